@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Benchmark of the hybrid symplectic N-body step on GB300.
+
+Workload: 16384 fully interacting equal-mass bodies (1e-3 Earth masses,
+a uniform in 0.5-3 au, e and i Rayleigh 0.01 / 0.005, radii from 2 g/cm^3),
+dt = 0.01 yr, critical radius 3 Hill radii; synthetic, seeded (opal_ic).
+A step is one full pass of the method: kick, jump, drift, encounter scan,
+Bulirsch-Stoer of the flagged groups, jump, kick.
+
+Prints one JSON line.  `value` is the mixed form's steps/s summed over
+ranks (each rank advances its own replica: independent systems, no
+collective on the data path); the FP64 form, interactions/s, |dE/E|, the
+kick's roofline, the end-to-end rate through the C ABI with host buffers,
+clocks and the oracle's CPU rate are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import opal_ic as ic  # noqa: E402
+
+METRIC = "steps/s and pair interactions/s at N=16384, mixed vs FP64 form, |dE/E| stated"
+UNIT = "steps/s"
+N_SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# algorithmic FP32 flops of one pair interaction of the kick (FMA = 2):
+# 3 subtractions, r^2 (1 mul + 2 fma = 5), rsqrt (1), m r^-3 (3 mul), 3 fma (6)
+FLOPS_PER_INTERACTION = 18
+# algorithmic bytes of the kick per launch: every body's float4 read once per
+# i-tile it meets plus the FP64 partial written per (i, j-chunk)
+KICK_KERNELS_PER_STEP = 8   # open, scan, confirm, group, bs, kick, close, finish
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------- ranks
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Largest value over ranks (the job's time is the slowest rank's)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [t.strip() for t in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("[N/A]", ""))}
+
+
+# ---------------------------------------------------------------- timing
+def time_steps(sim, steps: int, warmup: int, flush):
+    """Device time of each step (CUDA events on the simulation's stream,
+    L2 flushed before each step) and of its kick kernel (events captured in
+    the step graph on the same stream)."""
+    import torch
+    stream = torch.cuda.ExternalStream(sim.stream)
+    sim.step(warmup)
+    sim.time_kick(True)
+    step_ms, kick_ms = [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+        sim.step_async(1)
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+        kick_ms.append(sim.last_kick_ms())
+    sim.wait()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    sim.time_kick(False)
+    return step_ms, kick_ms
+
+
+def e2e_rate(system, steps: int, precision: int):
+    """Steps/s through the public API with host buffers: create from host
+    arrays (host->device), then every step opal_step and opal_get_state
+    (device->host of ids, masses, positions, velocities, radii)."""
+    from paper_2601_19654_gb300 import opal
+    n = system.n
+    t0 = time.perf_counter()
+    sim = opal.Simulation.from_system(system, precision=precision)
+    for _ in range(steps):
+        sim.step(1)
+        st = sim.state()
+    t1 = time.perf_counter()
+    sim.close()
+    assert st["x"].shape[0] > 0
+    h2d = n * 8 * (1 + 3 + 3 + 1)
+    d2h = n * (8 + 8 + 24 + 24 + 8)
+    return {"value": steps / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h, "note": "create (H2D, autotune, graph capture) inside the timed region, "
+                                              "amortised over the steps; state read back every step"}
+
+
+def oracle_rate(system, seconds: float, max_steps: int | None = None):
+    import oracle
+    oracle.build()
+    sim = oracle.Sim.from_system(system)
+    E0 = sim.energy()[0]
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        assert sim.step(1) == oracle.OK
+        done += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and done >= 2) or (max_steps and done >= max_steps):
+            break
+    dE = abs(sim.energy()[0] - E0) / abs(E0)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return done / el, done, el, threads, dE
+
+
+# ---------------------------------------------------------------- main
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    system = ic.equal_mass_disk(args.seed)
+    import oracle
+    oracle.build()
+    sim = oracle.Sim.from_system(system)
+    for _ in range(min(args.warmup, 1)):
+        sim.step(1)
+    budget = 120.0
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.steps and (time.perf_counter() - t0) < budget:
+        assert sim.step(1) == oracle.OK
+        done += 1
+    el = time.perf_counter() - t0
+    v = done / el
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": done, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": system.name, "bodies": system.n, "form": "FP64 serial oracle (C, OpenMP kick)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{done} full steps of the 16384-body system ({el:.1f} s)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "interactions_per_s": v * system.n * (system.n - 1)}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2601_19654_gb300 import opal
+    from paper_2601_19654_gb300.build import build
+    if local == 0:
+        build()
+    barrier(world)
+    system = ic.equal_mass_disk(args.seed + rank)
+    n = system.n
+    pairs = n * (n - 1)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    # mixed form (the headline)
+    sim = opal.Simulation.from_system(system, precision=1)
+    kick_cfg = sim.kick_config
+    E0 = sim.energy()[0]
+    barrier(world)
+    visible = [t for t in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if t.strip()]
+    gpu_id = visible[local] if local < len(visible) else str(local)
+    with ClockSampler(gpu_id) as clk:
+        step_ms, kick_ms = time_steps(sim, args.steps, args.warmup, flush)
+    total_ms = max_over_ranks(float(np.sum(step_ms)), world)
+    dE_mixed = abs(sim.energy()[0] - E0) / abs(E0)
+    last = sim.stats()
+    sim.close()
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms * 1e-3)
+
+    # FP64 form, same workload
+    sim64 = opal.Simulation.from_system(system, precision=0)
+    E064 = sim64.energy()[0]
+    s64, k64 = time_steps(sim64, args.fp64_steps, 3, flush)
+    dE_fp64 = abs(sim64.energy()[0] - E064) / abs(E064)
+    sim64.close()
+    ms64 = max_over_ranks(float(np.mean(s64)), world)
+
+    kick_avg = float(np.mean(kick_ms))
+    flops = FLOPS_PER_INTERACTION * pairs
+    peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (kick_avg * 1e-3) / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": system.name, "bodies": n, "form": "mixed (FP32 pair kick, FP64 drift/BS)",
+                   "dt_yr": 0.01, "rcrit_hill": 3.0, "l2": "flushed (256 MiB memset) before every timed step",
+                   "replicas": world, "kick": kick_cfg},
+        "interactions_per_s": value * pairs,
+        "dE_over_E": {"mixed": dE_mixed, "fp64": dE_fp64,
+                      "over_steps": {"mixed": args.warmup + args.steps, "fp64": 3 + args.fp64_steps}},
+        "fp64": {"value": world * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
+                 "interactions_per_s": world * 1e3 / ms64 * pairs, "kick_ms": float(np.mean(k64)),
+                 "steps": args.fp64_steps},
+        "mixed_over_fp64": ms64 / ms_per_step,
+        "encounters_last_step": last,
+        "roofline": {"bound": "alu", "kernel": "kick (mixed)", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "note": f"{FLOPS_PER_INTERACTION} FP32 flops per pair x N(N-1) pairs per launch; "
+                             "peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (of nominal max clock)",
+                     "kick_ms": kick_avg, "kick_share_of_step": kick_avg / float(np.mean(step_ms))},
+        "gpu_launches": KICK_KERNELS_PER_STEP * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        line["e2e"] = e2e_rate(system, max(5, min(args.steps, 50)), precision=1)
+        if not args.no_cpu_baseline:
+            v, done, el, threads, dE = oracle_rate(system, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                    "sample": f"{done} full steps of the {n}-body system ({el:.1f} s)",
+                                    "dE_over_E": dE}
+        print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

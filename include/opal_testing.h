@@ -1,0 +1,59 @@
+/*
+ * opal_testing.h -- test hooks of the GB300 hybrid symplectic step.
+ *
+ * Each hook runs one stage of the step on its own, through the same kernels
+ * opal_step launches, so the tests can compare a stage with the oracle on
+ * identical inputs.  Pointers are host memory, borrowed for the call; arrays
+ * of vectors are row-major n x 3; body order is the order given at create.
+ * The hooks overwrite parts of the simulation's state: use a simulation made
+ * for the test.  Same status codes as opal.h.
+ */
+#ifndef OPAL_TESTING_H
+#define OPAL_TESTING_H
+
+#include <stdint.h>
+
+#include "opal.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Kick accelerations at the simulation's current positions and masses
+ * (Sec. 3.1, force block, LOOP 2): a[3n] = G sum_j m_j K(r_ij; max(rc_i, rc_j))
+ * (x_j - x_i) / r_ij^3, in the simulation's precision and changeover form.
+ * rc[n] (may be NULL to keep the simulation's) replaces the critical radii.
+ * The result also becomes the simulation's stored accelerations. */
+opal_status opal_debug_accel(opal_sim* sim, const double* rc, double* a);
+
+/* Keplerian drift of n independent bodies about mu over dt (Sec. 3.1, third
+ * block), in place on x[3n], v[3n]; iters[n] gets the iteration count, or
+ * -1 where the solve did not converge within max_iter (0 = default 50), in
+ * which case that body is left unchanged. */
+opal_status opal_debug_drift(int64_t n, double mu, double dt, int32_t max_iter, double* x, double* v,
+                             int32_t* iters);
+
+/* Close-encounter scan of system 0 (Sec. 3.1, mce_snif block) on given
+ * start-of-drift (x0, V0) and after-drift (x1, V1) states and critical radii
+ * rc[n], with the simulation's dt.  Writes the flagged pairs, i < j, sorted,
+ * into pi[cap], pj[cap]; *count gets their number and *ncand (may be NULL)
+ * the pairs that reached the exact FP64 test.  The simulation's positions
+ * and velocities are overwritten. */
+opal_status opal_debug_scan(opal_sim* sim, const double* x0, const double* V0, const double* x1,
+                            const double* V1, const double* rc, int64_t cap, int32_t* pi, int32_t* pj,
+                            int64_t* count, int64_t* ncand);
+
+/* Bulirsch-Stoer integration over the simulation's dt of all bodies of a
+ * one-system simulation (at most 64) as a single encounter group, from
+ * (x0, V0), with critical radii rc, masses m, radii radius, flags alive
+ * (Sec. 2.1.1 footnote 2; mce_coll for mergers).  Outputs x, V and updates
+ * m, radius, alive in place; *E_lost gets the energy removed by mergers and
+ * *substeps the substeps used. */
+opal_status opal_debug_bs_group(opal_sim* sim, const double* x0, const double* V0, const double* rc, double* x,
+                                double* V, double* m, double* radius, int32_t* alive, double* E_lost,
+                                int64_t* substeps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

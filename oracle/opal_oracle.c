@@ -162,7 +162,8 @@ void orc_stumpff(double z, double c[4]) {
  *   F(chi) = r0 G1 + eta G2 + mu G3 - dt = 0,  F' = r = r0 G0 + eta G1 + mu G2.
  * F is increasing (F' = r > 0) and F' >= q, the pericentre distance, so the
  * root lies in [0, dt/q] (dt > 0; mirrored for dt < 0).  Newton from
- * chi = dt / r0 keeps that bracket up to date and bisects whenever a Newton
+ * chi = dt / r0 (bound orbits) or the logarithmic start of Vallado's
+ * Algorithm 8 (unbound orbits) keeps that bracket up to date and bisects whenever a Newton
  * step would leave it; converged when |dchi| <= 1e-15 |chi|, or when |dchi|
  * is below 1e-12 |chi| and no smaller than the step before.  A bound orbit
  * first drops whole periods P = 2 pi mu / beta^1.5 from dt (the state repeats).
@@ -192,6 +193,15 @@ int32_t orc_kepler_drift(double mu, double dt, double x[3], double v[3], int32_t
         hi = 0.0;
     }
     double chi = dt / r0, c[4];
+    if (beta < 0.0) {
+        /* unbound orbit: the logarithmic starting value of the universal
+         * variable (Vallado, Fundamentals of Astrodynamics, Algorithm 8),
+         * with a = mu / beta < 0; kept only when its logarithm is defined */
+        double a = mu / beta, sg = dt >= 0.0 ? 1.0 : -1.0;
+        double den = eta + sg * sqrt(-mu * a) * (1.0 - r0 / a);
+        double arg = -2.0 * beta * dt / den;
+        if (den != 0.0 && arg > 0.0 && isfinite(arg)) chi = sg * sqrt(-a / mu) * log(arg);
+    }
     if (chi < lo) chi = lo;
     if (chi > hi) chi = hi;
     int conv = 0, it;

@@ -1,0 +1,359 @@
+// Body-parallel kernels of the step: the opening half (kick, jump, save,
+// Keplerian drift, critical radii, float copies for the pair kernels), the
+// closing half (jump, kick, momentum partials for the next step), the undo
+// of a failed step, and the coordinate conversions at the boundary.
+//
+// Paper: Sec. 3.1, Hamiltonian block (LOOP 1 velocities, LOOP 2 momentum
+// reduction, LOOP 3 positions, LOOP 4 copy of x and v) and third block
+// (arxes_drift on every body, failure flag); Hill / critical radii from the
+// instantaneous heliocentric distance, Sec. 2.1.1 item (4) and footnotes.
+#include "opal_internal.cuh"
+
+namespace opal {
+
+// Sum of the system's momentum segments, in a fixed order, broadcast to the
+// block.  Every block of a system gets the same bits.
+__device__ void system_momentum(const Dev& d, const double* part, const SysInfo& si, double* P3) {
+    __shared__ double red[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        double px = 0.0, py = 0.0, pz = 0.0;
+        for (int64_t k = lane; k < si.nseg; k += 32) {
+            int64_t sg = si.seg0 + k;
+            px += part[sg];
+            py += part[d.nseg_tot + sg];
+            pz += part[2 * d.nseg_tot + sg];
+        }
+        red[0][lane] = px;
+        red[1][lane] = py;
+        red[2][lane] = pz;
+        __syncwarp();
+        if (lane < 3) {
+            double s = 0.0;
+            for (int k = 0; k < 32; k++) s += red[lane][k];
+            P3[lane] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Fixed-order reduction of 3 values over a block of kBodyThreads threads into
+// kBodyThreads / kSeg segments: out[c][seg] for each 64-body half.
+__device__ void segment_sums(const Dev& d, int64_t first_body, double vx, double vy, double vz, double* part) {
+    __shared__ double buf[3][kBodyThreads];
+    buf[0][threadIdx.x] = vx;
+    buf[1][threadIdx.x] = vy;
+    buf[2][threadIdx.x] = vz;
+    __syncthreads();
+    for (int w = kSeg / 2; w >= 1; w >>= 1) {
+        int t = threadIdx.x % kSeg;
+        if (t < w) {
+            buf[0][threadIdx.x] += buf[0][threadIdx.x + w];
+            buf[1][threadIdx.x] += buf[1][threadIdx.x + w];
+            buf[2][threadIdx.x] += buf[2][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x % kSeg == 0) {
+        int64_t sg = (first_body + threadIdx.x) / kSeg;
+        part[sg] = buf[0][threadIdx.x];
+        part[d.nseg_tot + sg] = buf[1][threadIdx.x];
+        part[2 * d.nseg_tot + sg] = buf[2][threadIdx.x];
+    }
+}
+
+__device__ __forceinline__ void note_rcmax(const Dev& d, int s, double rc) {
+    // rc >= 0: the order of non-negative floats matches the order of their bits
+    atomicMax(reinterpret_cast<int*>(d.rcmax) + s, __float_as_int(__double2float_ru(rc)));
+}
+
+// scan inputs of a live body: start-of-drift hi/lo, velocities, and the
+// radius s that bounds how far the body's Hermite path over the step strays
+// from its end point: |x0 - x1| + (4/27)|dt|(|V0| + |V1|), plus rc and margins.
+__device__ __forceinline__ void scan_floats(const Dev& d, int64_t b, double ox, double oy, double oz, double ovx,
+                                            double ovy, double ovz, double x, double y, double z, double vx,
+                                            double vy, double vz, double rc) {
+    double wx = ox - x, wy = oy - y, wz = oz - z;
+    double v0n = sqrt(dot3(ovx, ovy, ovz, ovx, ovy, ovz)), v1n = sqrt(dot3(vx, vy, vz, vx, vy, vz));
+    double rho = sqrt(dot3(wx, wy, wz, wx, wy, wz)) + (4.0 / 27.0) * fabs(d.p.dt) * (v0n + v1n);
+    double r1 = sqrt(dot3(x, y, z, x, y, z));
+    double sr = (rho + rc) * (1.0 + 1e-5) + 1e-6 * r1;
+    float hx, lx, hy, ly, hz, lz;
+    split_hl(ox, hx, lx);
+    split_hl(oy, hy, ly);
+    split_hl(oz, hz, lz);
+    d.sc0[b] = make_float4(hx, hy, hz, __double2float_ru(sr));
+    d.sc1[b] = make_float4(lx, ly, lz, 0.0f);
+    d.sv0[b] = make_float4((float)ovx, (float)ovy, (float)ovz, __double2float_ru(v0n));
+    d.sv1[b] = make_float4((float)vx, (float)vy, (float)vz, __double2float_ru(v1n));
+}
+
+// ---------------------------------------------------------------------------
+// create time: heliocentric -> democratic heliocentric velocities, one block
+// per system: V_i = v_i - sum_j m_j v_j / (M0 + sum_j m_j).
+__global__ void k_to_dh(Dev d) {
+    const SysInfo si = d.sys[blockIdx.x];
+    __shared__ double red[4][256];
+    double sx = 0, sy = 0, sz = 0, sm = 0;
+    for (int64_t k = threadIdx.x; k < si.cap; k += blockDim.x) {
+        int64_t b = si.off + k;
+        if (!d.alive[b]) continue;
+        sx += d.m[b] * d.vx[b];
+        sy += d.m[b] * d.vy[b];
+        sz += d.m[b] * d.vz[b];
+        sm += d.m[b];
+    }
+    red[0][threadIdx.x] = sx;
+    red[1][threadIdx.x] = sy;
+    red[2][threadIdx.x] = sz;
+    red[3][threadIdx.x] = sm;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w >= 1; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 4; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    double Mt = d.p.M0 + red[3][0];
+    double cx = red[0][0] / Mt, cy = red[1][0] / Mt, cz = red[2][0] / Mt;
+    for (int64_t k = threadIdx.x; k < si.cap; k += blockDim.x) {
+        int64_t b = si.off + k;
+        if (!d.alive[b]) continue;
+        d.vx[b] -= cx;
+        d.vy[b] -= cy;
+        d.vz[b] -= cz;
+    }
+}
+
+// create time: critical radii and float copies at the initial positions
+__global__ void k_prime(Dev d) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.ntot) return;
+    int s = d.body_sys[b];
+    if (!d.alive[b]) {
+        d.rc[b] = 0.0;
+        park_floats(d, b);
+        return;
+    }
+    double r = sqrt(dot3(d.x[b], d.y[b], d.z[b], d.x[b], d.y[b], d.z[b]));
+    double rc = d.p.rcrit_hill * r * cbrt(d.m[b] / (3.0 * d.p.M0));
+    d.rc[b] = rc;
+    kick_floats(d, b, d.x[b], d.y[b], d.z[b], d.m[b], rc);
+    note_rcmax(d, s, rc);
+}
+
+// ---------------------------------------------------------------------------
+// Opening half of a step, one thread per body.
+__global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
+    if (d.ctl->status) return;
+    const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
+    const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
+    const SysInfo si = d.sys[s];
+    __shared__ double P[3];
+    system_momentum(d, d.pP_open, si, P);
+    const double half = 0.5 * d.p.dt, M0 = d.p.M0;
+    // undo copy of the start of the step
+    double x = d.x[b], y = d.y[b], z = d.z[b], vx = d.vx[b], vy = d.vy[b], vz = d.vz[b];
+    d.xs[b] = x; d.ys[b] = y; d.zs[b] = z;
+    d.vxs[b] = vx; d.vys[b] = vy; d.vzs[b] = vz;
+    d.rcs[b] = d.rc[b];
+    int iters = 0;
+    if (d.alive[b]) {
+        // kick (LOOP 1), jump with the momentum sum (LOOPs 2-3), copy (LOOP 4)
+        vx += half * d.ax[b];
+        vy += half * d.ay[b];
+        vz += half * d.az[b];
+        x += half * P[0] / M0;
+        y += half * P[1] / M0;
+        z += half * P[2] / M0;
+        d.x0[b] = x; d.y0[b] = y; d.z0[b] = z;
+        d.vx0[b] = vx; d.vy0[b] = vy; d.vz0[b] = vz;
+        const double ox = x, oy = y, oz = z, ovx = vx, ovy = vy, ovz = vz;
+        iters = kepler_drift(d.p.G * M0, d.p.dt, d.p.kepler_max_iter, x, y, z, vx, vy, vz);
+        if (iters < 0) {
+            set_status(d.ctl, kEkepler, (int)b);
+            iters = d.p.kepler_max_iter;
+        }
+        d.x[b] = x; d.y[b] = y; d.z[b] = z;
+        d.vx[b] = vx; d.vy[b] = vy; d.vz[b] = vz;
+        double r1 = sqrt(dot3(x, y, z, x, y, z));
+        double rc = d.p.rcrit_hill * r1 * cbrt(d.m[b] / (3.0 * M0));
+        d.rc[b] = rc;
+        kick_floats(d, b, x, y, z, d.m[b], rc);
+        note_rcmax(d, s, rc);
+        scan_floats(d, b, ox, oy, oz, ovx, ovy, ovz, x, y, z, vx, vy, vz, rc);
+    } else {
+        park_floats(d, b);
+    }
+    // largest iteration count of the block
+    __shared__ int itmax;
+    if (threadIdx.x == 0) itmax = 0;
+    __syncthreads();
+    atomicMax(&itmax, iters);
+    __syncthreads();
+    if (threadIdx.x == 0 && itmax > 0) atomicMax(&d.ctl->kepler_max, itmax);
+}
+
+// ---------------------------------------------------------------------------
+// Closing half: reduce the kick partials into a, jump with the momentum of
+// the post-encounter state, kick, and the momentum partials the next
+// step's jump needs (of V + dt/2 a, the velocities after its opening kick).
+// first != 0 (create time): only a and the partials, no jump or kick.
+__global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
+    if (d.ctl->status) return;
+    const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
+    const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
+    const SysInfo si = d.sys[s];
+    __shared__ double P[3];
+    if (!first) system_momentum(d, d.pP_close, si, P);
+    const double half = 0.5 * d.p.dt, G = d.p.G;
+    const int64_t local = b - si.off;
+    double ax = 0, ay = 0, az = 0;
+    for (int c = 0; c < si.nchunk; c++) {
+        int64_t slot = si.slot0 + (int64_t)c * si.cap + local;
+        ax += d.pacc_x[slot];
+        ay += d.pacc_y[slot];
+        az += d.pacc_z[slot];
+    }
+    ax *= G;
+    ay *= G;
+    az *= G;
+    double px = 0, py = 0, pz = 0;
+    if (d.alive[b]) {
+        double x = d.x[b], y = d.y[b], z = d.z[b], vx = d.vx[b], vy = d.vy[b], vz = d.vz[b];
+        if (!first) {
+            x += half * P[0] / d.p.M0;
+            y += half * P[1] / d.p.M0;
+            z += half * P[2] / d.p.M0;
+            vx += half * ax;
+            vy += half * ay;
+            vz += half * az;
+            d.x[b] = x; d.y[b] = y; d.z[b] = z;
+            d.vx[b] = vx; d.vy[b] = vy; d.vz[b] = vz;
+        }
+        d.ax[b] = ax; d.ay[b] = ay; d.az[b] = az;
+        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz) &&
+              isfinite(ax) && isfinite(ay) && isfinite(az)))
+            set_status(d.ctl, kEnonfinite, (int)b);
+        double m = d.m[b];
+        px = m * (vx + half * ax);
+        py = m * (vy + half * ay);
+        pz = m * (vz + half * az);
+    } else {
+        d.ax[b] = 0.0; d.ay[b] = 0.0; d.az[b] = 0.0;
+    }
+    segment_sums(d, (int64_t)blockIdx.x * kBodyThreads, px, py, pz, d.pP_open);
+    if (!first && b == 0) {
+        // energy removed by this step's mergers, per system, in group order
+        int ng = d.ctl->ngroups;
+        for (int g = 0; g < ng; g++) {
+            double e = d.glost[g];
+            if (e != 0.0) d.E_lost[d.body_sys[d.members[d.goff[g]]]] += e;
+        }
+    }
+}
+
+// Undo of a failed step (runs every step; returns at once when all is well).
+__global__ void k_finish(Dev d) {
+    const Ctl* c = d.ctl;
+    if (!c->status) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) d.ctl->steps_done++;
+        return;
+    }
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < d.ntot;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        d.x[b] = d.xs[b]; d.y[b] = d.ys[b]; d.z[b] = d.zs[b];
+        d.vx[b] = d.vxs[b]; d.vy[b] = d.vys[b]; d.vz[b] = d.vzs[b];
+        d.rc[b] = d.rcs[b];
+    }
+    // masses, radii and flags of group members as they were before the BS
+    int nmem = c->ninvolved;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nmem; k += (int64_t)gridDim.x * blockDim.x) {
+        int b = d.members[k];
+        if (d.undo[3 * k + 2] >= 0.0) {   // slot written by the BS kernel
+            d.m[b] = d.undo[3 * k];
+            d.R[b] = d.undo[3 * k + 1];
+            d.alive[b] = (int)d.undo[3 * k + 2];
+        }
+        d.label[b] = -1;
+    }
+}
+
+// get_state: heliocentric velocities v = V + P / M0, one block per system
+__global__ void k_export(Dev d, double* vh) {
+    const SysInfo si = d.sys[blockIdx.x];
+    __shared__ double red[3][256];
+    double sx = 0, sy = 0, sz = 0;
+    for (int64_t k = threadIdx.x; k < si.cap; k += blockDim.x) {
+        int64_t b = si.off + k;
+        if (!d.alive[b]) continue;
+        sx += d.m[b] * d.vx[b];
+        sy += d.m[b] * d.vy[b];
+        sz += d.m[b] * d.vz[b];
+    }
+    red[0][threadIdx.x] = sx;
+    red[1][threadIdx.x] = sy;
+    red[2][threadIdx.x] = sz;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w >= 1; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    double cx = red[0][0] / d.p.M0, cy = red[1][0] / d.p.M0, cz = red[2][0] / d.p.M0;
+    for (int64_t k = threadIdx.x; k < si.cap; k += blockDim.x) {
+        int64_t b = si.off + k;
+        vh[3 * b] = d.vx[b] + cx;
+        vh[3 * b + 1] = d.vy[b] + cy;
+        vh[3 * b + 2] = d.vz[b] + cz;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// test hooks: the drift alone, and the scan inputs from a given x0, V0, x1, V1, rc
+__global__ void k_debug_drift(int n, double mu, double dt, int max_iter, double* x, double* v, int* iters) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    double px = x[3 * b], py = x[3 * b + 1], pz = x[3 * b + 2], vx = v[3 * b], vy = v[3 * b + 1], vz = v[3 * b + 2];
+    int it = kepler_drift(mu, dt, max_iter, px, py, pz, vx, vy, vz);
+    x[3 * b] = px; x[3 * b + 1] = py; x[3 * b + 2] = pz;
+    v[3 * b] = vx; v[3 * b + 1] = vy; v[3 * b + 2] = vz;
+    iters[b] = it;
+}
+
+__global__ void k_debug_scan_prep(Dev d) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= d.ntot) return;
+    if (!d.alive[b]) {
+        park_floats(d, b);
+        return;
+    }
+    kick_floats(d, b, d.x[b], d.y[b], d.z[b], d.m[b], d.rc[b]);
+    note_rcmax(d, d.body_sys[b], d.rc[b]);
+    scan_floats(d, b, d.x0[b], d.y0[b], d.z0[b], d.vx0[b], d.vy0[b], d.vz0[b], d.x[b], d.y[b], d.z[b], d.vx[b],
+                d.vy[b], d.vz[b], d.rc[b]);
+}
+
+// ---------------------------------------------------------------------------
+void launch_debug_drift(int n, double mu, double dt, int max_iter, double* x, double* v, int* iters, cudaStream_t s) {
+    k_debug_drift<<<(n + 127) / 128, 128, 0, s>>>(n, mu, dt, max_iter, x, v, iters);
+}
+void launch_debug_scan_prep(const Dev& d, cudaStream_t s) {
+    k_debug_scan_prep<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d);
+}
+void launch_to_dh(const Dev& d, cudaStream_t s) { k_to_dh<<<d.nsys, 256, 0, s>>>(d); }
+void launch_prime(const Dev& d, cudaStream_t s) {
+    k_prime<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d);
+}
+void launch_open(const Dev& d, cudaStream_t s) {
+    k_open<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d);
+}
+void launch_close(const Dev& d, cudaStream_t s) {
+    k_close<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d, 0);
+}
+void launch_first_accel_finish(const Dev& d, cudaStream_t s) {
+    k_close<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d, 1);
+}
+void launch_finish(const Dev& d, cudaStream_t s) { k_finish<<<152, 256, 0, s>>>(d); }
+void launch_export(const Dev& d, double* v_helio, cudaStream_t s) { k_export<<<d.nsys, 256, 0, s>>>(d, v_helio); }
+
+}  // namespace opal

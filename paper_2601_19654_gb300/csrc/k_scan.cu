@@ -1,0 +1,314 @@
+// Close-encounter scan (Sec. 3.1, mce_snif block): flag every pair i < j of
+// live bodies of a system whose minimum separation over the step is <= the
+// critical distance max(rc_i, rc_j); then gather the flagged pairs into
+// groups (connected components) for the encounter integrator.
+//
+// The minimum is taken over the cubic Hermite path of the relative motion
+// built from the saved start-of-drift state (x0, V0) and the state after
+// the drift (x1, V1).  Three stages, each a superset of the next:
+//   1. FP32, per pair, in the tile kernel: |d1| <= s_i + s_j, where s bounds
+//      how far a body's path strays from its end point (plus rc);
+//   2. FP32, on the pairs that pass: distance from the origin to the chord
+//      d0 -> d1 minus a bound on the path's deviation from the chord;
+//   3. FP64 exact minimum on the survivors, in the same arithmetic as the
+//      oracle (16 intervals, sign change of d.d', 48 bisections).
+// Stages 1-2 carry margins far above FP32 rounding, so they never drop a
+// pair stage 3 would flag; the flagged set is that of stage 3 alone.
+#include "opal_internal.cuh"
+
+namespace opal {
+
+// ---------------------------------------------------------------- stage 2
+__device__ __noinline__ bool chord_bound_passes(const Dev& d, int64_t i, int64_t j, float T) {
+    float4 a0 = d.sc0[i], b0 = d.sc0[j], a0l = d.sc1[i], b0l = d.sc1[j];
+    float4 a1 = d.kh[i], b1 = d.kh[j], a1l = d.kl[i], b1l = d.kl[j];
+    float4 av0 = d.sv0[i], bv0 = d.sv0[j], av1 = d.sv1[i], bv1 = d.sv1[j];
+    float d0x = (b0.x - a0.x) + (b0l.x - a0l.x), d0y = (b0.y - a0.y) + (b0l.y - a0l.y),
+          d0z = (b0.z - a0.z) + (b0l.z - a0l.z);
+    float d1x = (b1.x - a1.x) + (b1l.x - a1l.x), d1y = (b1.y - a1.y) + (b1l.y - a1l.y),
+          d1z = (b1.z - a1.z) + (b1l.z - a1l.z);
+    float u0x = bv0.x - av0.x, u0y = bv0.y - av0.y, u0z = bv0.z - av0.z;
+    float u1x = bv1.x - av1.x, u1y = bv1.y - av1.y, u1z = bv1.z - av1.z;
+    float wx = d1x - d0x, wy = d1y - d0y, wz = d1z - d0z;
+    float ww = wx * wx + wy * wy + wz * wz;
+    float t = 0.0f;
+    if (ww > 0.0f) t = fminf(fmaxf(-(d0x * wx + d0y * wy + d0z * wz) / ww, 0.0f), 1.0f);
+    float cx = d0x + t * wx, cy = d0y + t * wy, cz = d0z + t * wz;
+    float cd = sqrtf(cx * cx + cy * cy + cz * cz);
+    float nu0 = sqrtf(u0x * u0x + u0y * u0y + u0z * u0z), nu1 = sqrtf(u1x * u1x + u1y * u1y + u1z * u1z);
+    float aT = fabsf(T);
+    // |path - chord| <= (sqrt 3 / 18)|d1 - d0| + (4/27)|T|(|u0| + |u1|), constants rounded up
+    float E = 0.0962251f * sqrtf(ww) + 0.1481482f * aT * (nu0 + nu1);
+    float rcij = fmaxf(d.rcf[i], d.rcf[j]);
+    float n0 = sqrtf(d0x * d0x + d0y * d0y + d0z * d0z), n1 = sqrtf(d1x * d1x + d1y * d1y + d1z * d1z);
+    float margin = 1e-4f * (n0 + n1 + E + rcij) + 1e-6f * aT * (av0.w + bv0.w + av1.w + bv1.w);
+    return cd - E <= rcij + margin;
+}
+
+// ---------------------------------------------------------------- stage 1
+__global__ void __launch_bounds__(kSeg) k_scan(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
+    __shared__ float4 sj[kSeg];
+    if (d.ctl->status) return;
+    const float T = (float)d.p.dt;
+    const int lane = threadIdx.x & 31;
+    for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
+        const PairTile tl = tiles[it];
+        const int64_t i = tl.i0 + threadIdx.x;
+        const float4 hi = d.kh[i];
+        const float si = d.sc0[i].w;
+        __syncthreads();
+        {
+            int64_t j = tl.j0 + threadIdx.x;
+            float4 h = d.kh[j];
+            sj[threadIdx.x] = make_float4(h.x, h.y, h.z, d.sc0[j].w);
+        }
+        __syncthreads();
+        for (int jj = 0; jj < kSeg; jj++) {
+            const int64_t j = tl.j0 + jj;
+            const float4 pj = sj[jj];
+            float dx = pj.x - hi.x, dy = pj.y - hi.y, dz = pj.z - hi.z;
+            float r2 = dx * dx + dy * dy + dz * dz;
+            float Ts = si + pj.w;
+            bool pass = (j > i) && (r2 < Ts * Ts);
+            if (pass) pass = chord_bound_passes(d, i, j, T);
+            unsigned mask = __ballot_sync(0xffffffffu, pass);
+            if (mask) {
+                int leader = __ffs(mask) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&d.ctl->ncand, __popc(mask));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (pass) {
+                    int idx = base + __popc(mask & ((1u << lane) - 1u));
+                    if (idx < d.cand_cap) d.cand[idx] = make_int2((int)i, (int)j);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- stage 3
+// Relative position and its s-derivative on the cubic Hermite path,
+// s in [0, 1], T = dt (same operation order as the oracle).
+__device__ __forceinline__ void hermite_rel(double s, double T, const double* d0, const double* u0,
+                                            const double* d1, const double* u1, double* dd, double* dp) {
+    double s2 = s * s, s3 = s2 * s;
+    double h00 = 2.0 * s3 - 3.0 * s2 + 1.0, h10 = s3 - 2.0 * s2 + s;
+    double h01 = -2.0 * s3 + 3.0 * s2, h11 = s3 - s2;
+    double p00 = 6.0 * s2 - 6.0 * s, p10 = 3.0 * s2 - 4.0 * s + 1.0;
+    double p01 = -6.0 * s2 + 6.0 * s, p11 = 3.0 * s2 - 2.0 * s;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        dd[k] = h00 * d0[k] + h10 * T * u0[k] + h01 * d1[k] + h11 * T * u1[k];
+        dp[k] = p00 * d0[k] + p10 * T * u0[k] + p01 * d1[k] + p11 * T * u1[k];
+    }
+}
+
+// Same result as scanning the 16 intervals in order and bisecting each sign
+// change on the spot (the minimum over the intervals does not depend on the
+// order they are visited in), arranged so that the lanes of a warp bisect
+// together instead of one after another.
+__device__ double min_sep2(double T, const double* d0, const double* u0, const double* d1, const double* u1) {
+    double D = d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2];
+    double D1 = d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2];
+    if (D1 < D) D = D1;
+    double dd[3], dp[3];
+    hermite_rel(0.0, T, d0, u0, d1, u1, dd, dp);
+    double ga = dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2];
+    unsigned mask = 0;
+    for (int k = 0; k < 16; k++) {
+        double sb = (k + 1) / 16.0;
+        hermite_rel(sb, T, d0, u0, d1, u1, dd, dp);
+        double gb = dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2];
+        if (ga < 0.0 && gb >= 0.0) mask |= 1u << k;
+        ga = gb;
+    }
+    while (__any_sync(__activemask(), mask != 0)) {
+        if (mask) {
+            int k = __ffs(mask) - 1;
+            mask &= mask - 1;
+            double lo = k / 16.0, hi = (k + 1) / 16.0;
+            for (int b = 0; b < 48; b++) {
+                double mid = 0.5 * (lo + hi);
+                hermite_rel(mid, T, d0, u0, d1, u1, dd, dp);
+                if (dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2] < 0.0) lo = mid;
+                else hi = mid;
+            }
+            hermite_rel(0.5 * (lo + hi), T, d0, u0, d1, u1, dd, dp);
+            double Dm = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+            if (Dm < D) D = Dm;
+        }
+    }
+    return D;
+}
+
+__global__ void k_confirm(Dev d) {
+    if (d.ctl->status) return;
+    const int ncand = d.ctl->ncand;
+    if (ncand > d.cand_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.ctl, kEoverflow, -1);
+        return;
+    }
+    const double T = d.p.dt;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncand; k += gridDim.x * blockDim.x) {
+        const int2 pr = d.cand[k];
+        const int i = pr.x, j = pr.y;
+        if (!d.alive[i] || !d.alive[j]) continue;
+        double d0[3] = {d.x0[j] - d.x0[i], d.y0[j] - d.y0[i], d.z0[j] - d.z0[i]};
+        double u0[3] = {d.vx0[j] - d.vx0[i], d.vy0[j] - d.vy0[i], d.vz0[j] - d.vz0[i]};
+        double d1[3] = {d.x[j] - d.x[i], d.y[j] - d.y[i], d.z[j] - d.z[i]};
+        double u1[3] = {d.vx[j] - d.vx[i], d.vy[j] - d.vy[i], d.vz[j] - d.vz[i]};
+        double rcij = fmax(d.rc[i], d.rc[j]);
+        double D = min_sep2(T, d0, u0, d1, u1);
+        if (D <= rcij * rcij) {
+            int idx = atomicAdd(&d.ctl->nflag, 1);
+            if (idx < d.flag_cap) d.flag[idx] = pr;
+            else set_status(d.ctl, kEoverflow, -2);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- groups
+// One block: min-label propagation over the flagged pairs (label = lowest
+// body index of the component), then a bitonic sort of (label, body) keys
+// and two block scans give the members, grouped and ascending, and the
+// group offsets.
+constexpr int kGroupThreads = 1024;
+constexpr int kGroupMaxKeys = 2 * kGroupMaxBodies;   // two keys per flagged pair
+
+__device__ void block_exclusive_scan(int* v, int n, int* total, int* warp_buf) {
+    // each thread owns a contiguous run of ceil(n / blockDim) entries
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int a = min(n, (int)threadIdx.x * per), b = min(n, a + per);
+    int s = 0;
+    for (int k = a; k < b; k++) s += v[k];
+    // inclusive scan of the per-thread sums across the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_buf[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int wsum = (lane < (int)(blockDim.x >> 5)) ? warp_buf[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wsum, o);
+            if (lane >= o) wsum += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) warp_buf[lane] = wsum;
+    }
+    __syncthreads();
+    int base = x - s + (warp > 0 ? warp_buf[warp - 1] : 0);
+    for (int k = a; k < b; k++) {
+        int t = v[k];
+        v[k] = base;
+        base += t;
+    }
+    if (threadIdx.x == blockDim.x - 1) *total = base;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGroupThreads) k_group(Dev d) {
+    extern __shared__ unsigned char smem[];
+    long long* keys = reinterpret_cast<long long*>(smem);
+    int* uslot = reinterpret_cast<int*>(keys + kGroupMaxKeys);
+    int* gidx = uslot + kGroupMaxKeys;
+    __shared__ int changed, total_u, total_g, warp_buf[32];
+    if (d.ctl->status) return;
+    const int nf = d.ctl->nflag;
+    if (nf == 0) return;
+    if (nf > d.flag_cap || 2 * nf > kGroupMaxKeys) {
+        if (threadIdx.x == 0) set_status(d.ctl, kEoverflow, -3);
+        return;
+    }
+    for (int p = threadIdx.x; p < nf; p += blockDim.x) {
+        int2 pr = d.flag[p];
+        d.label[pr.x] = pr.x;
+        d.label[pr.y] = pr.y;
+    }
+    __syncthreads();
+    // min-label propagation; a component of k bodies settles within k rounds
+    for (int round = 0; round <= nf + 1; round++) {
+        if (threadIdx.x == 0) changed = 0;
+        __syncthreads();
+        for (int p = threadIdx.x; p < nf; p += blockDim.x) {
+            int2 pr = d.flag[p];
+            int li = atomicAdd(&d.label[pr.x], 0), lj = atomicAdd(&d.label[pr.y], 0);
+            if (li != lj) {
+                int l = min(li, lj);
+                atomicMin(&d.label[pr.x], l);
+                atomicMin(&d.label[pr.y], l);
+                changed = 1;
+            }
+        }
+        __syncthreads();
+        int c = changed;
+        __syncthreads();
+        if (!c) break;
+    }
+    // keys (label, body), padded to a power of two with the largest key
+    const int nk = 2 * nf;
+    int np2 = 1;
+    while (np2 < nk) np2 <<= 1;
+    for (int k = threadIdx.x; k < np2; k += blockDim.x) {
+        long long key = 0x7fffffffffffffffLL;
+        if (k < nk) {
+            int2 pr = d.flag[k >> 1];
+            int b = (k & 1) ? pr.y : pr.x;
+            key = ((long long)__ldcg(&d.label[b]) << 32) | (long long)(unsigned)b;
+        }
+        keys[k] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= np2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = threadIdx.x; k < np2; k += blockDim.x) {
+                int q = k ^ stride;
+                if (q > k) {
+                    bool up = (k & size) == 0;
+                    long long a = keys[k], b = keys[q];
+                    if ((a > b) == up) {
+                        keys[k] = b;
+                        keys[q] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // member slot of each distinct key, and group index of each label run
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        uslot[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1 : 0;
+        gidx[k] = (k == 0 || (keys[k] >> 32) != (keys[k - 1] >> 32)) ? 1 : 0;
+    }
+    __syncthreads();
+    block_exclusive_scan(uslot, nk, &total_u, warp_buf);
+    block_exclusive_scan(gidx, nk, &total_g, warp_buf);
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        if (k == 0 || keys[k] != keys[k - 1]) d.members[uslot[k]] = (int)(keys[k] & 0xffffffffLL);
+        if (k == 0 || (keys[k] >> 32) != (keys[k - 1] >> 32)) d.goff[gidx[k]] = uslot[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d.goff[total_g] = total_u;
+        d.ctl->ngroups = total_g;
+        d.ctl->ninvolved = total_u;
+    }
+    for (int k = threadIdx.x; k < total_u; k += blockDim.x) d.undo[3 * k + 2] = -1.0;
+}
+
+void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s) {
+    k_scan<<<grid, kSeg, 0, s>>>(d, tiles, ntiles);
+}
+void launch_confirm(const Dev& d, int grid, cudaStream_t s) { k_confirm<<<grid, 256, 0, s>>>(d); }
+
+size_t group_smem() { return (size_t)kGroupMaxKeys * (sizeof(long long) + 2 * sizeof(int)); }
+void launch_group(const Dev& d, cudaStream_t s) {
+    k_group<<<1, kGroupThreads, group_smem(), s>>>(d);
+}
+cudaError_t group_setup() {
+    return cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem());
+}
+
+}  // namespace opal

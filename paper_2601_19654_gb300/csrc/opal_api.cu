@@ -1,0 +1,869 @@
+// Host side of the C ABI (include/opal.h): validation, device layout, work
+// lists, the per-step CUDA graph, and the copies across the boundary.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <cstdlib>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/opal.h"
+#include "../../include/opal_testing.h"
+#include "opal_internal.cuh"
+
+using namespace opal;
+
+namespace {
+
+thread_local char g_err[512];
+
+void set_err(char* buf, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    if (buf != g_err) std::memcpy(g_err, buf, 512);
+}
+
+const char* status_name(int s) {
+    switch (s) {
+        case kOk: return "ok";
+        case kEinval: return "invalid argument";
+        case kEnomem: return "out of memory";
+        case kEcuda: return "CUDA error";
+        case kEkepler: return "Kepler drift did not converge";
+        case kEbs: return "Bulirsch-Stoer substep cap reached";
+        case kEoverflow: return "encounter list or group capacity exceeded";
+        case kEnonfinite: return "non-finite value in the state";
+    }
+    return "unknown";
+}
+
+}  // namespace
+
+struct opal_sim {
+    Dev d{};
+    int dev = 0;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<SysInfo> sys;
+    std::vector<int64_t> n_per_sys;
+    std::vector<KickItem> items;
+    std::vector<PairTile> tiles;
+    std::vector<int64_t> tile_off;
+    KickItem* d_items = nullptr;
+    PairTile* d_tiles = nullptr;
+    int64_t* d_tile_off = nullptr;
+    int kick_grid = 1, scan_grid = 1, confirm_grid = 1, bs_grid = 1, energy_grid = 1;
+    int kick_variant = 0;
+    char kick_desc[256] = {0};
+    int time_kick = 0;                       // graph records events around the kick
+    cudaEvent_t kick_ev[2] = {nullptr, nullptr};
+    double* d_vh = nullptr;        // heliocentric velocities for get_state
+    double* d_en_body = nullptr;
+    double* d_en_pair = nullptr;
+    double* d_en_out = nullptr;
+    std::vector<void*> allocs;
+    char err[512] = {0};
+    int64_t n_total = 0;
+};
+
+namespace {
+
+template <class T>
+opal_status dalloc(opal_sim* s, T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        set_err(s->err, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? OPAL_ENOMEM : OPAL_ECUDA;
+    }
+    s->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return OPAL_OK;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            set_err(s->err, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return OPAL_ECUDA;                                                                \
+        }                                                                                     \
+    } while (0)
+
+#define TRY(call)                          \
+    do {                                   \
+        opal_status st_ = (call);          \
+        if (st_ != OPAL_OK) return st_;    \
+    } while (0)
+
+bool finite_all(const double* a, int64_t n) {
+    for (int64_t i = 0; i < n; i++)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+// The kick's work list: 128-body i-tiles against j-chunks of the real bodies,
+// chunk counts chosen so the items fill the persistent grid evenly.
+void build_kick_items(opal_sim* s, int slots) {
+    double work = 0;
+    for (auto& si : s->sys) work += (double)si.cap * (double)si.n;
+    const double target = std::max(1.0, work / std::max(1, slots));
+    s->items.clear();
+    int64_t slot = 0;
+    for (size_t k = 0; k < s->sys.size(); k++) {
+        SysInfo& si = s->sys[k];
+        const int64_t itiles = si.cap / kPad;
+        const double w_tile = (double)kPad * (double)si.n;
+        int64_t nchunk = (int64_t)std::llround(w_tile / target);
+        // a single system: make the item count a whole multiple of the grid
+        if (s->sys.size() == 1) nchunk = std::max<int64_t>(1, (slots + itiles - 1) / itiles);
+        nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, std::max<int64_t>(1, si.n / 64)));
+        si.nchunk = (int32_t)nchunk;
+        si.slot0 = slot;
+        slot += nchunk * si.cap;
+        for (int64_t c = 0; c < nchunk; c++) {
+            int64_t j0 = si.off + (si.n * c) / nchunk, j1 = si.off + (si.n * (c + 1)) / nchunk;
+            for (int64_t t = 0; t < itiles; t++) {
+                KickItem it{};
+                it.sys = (int32_t)k;
+                it.chunk = (int32_t)c;
+                it.i0 = si.off + t * kPad;
+                it.j0 = j0;
+                it.j1 = j1;
+                s->items.push_back(it);
+            }
+        }
+    }
+    std::stable_sort(s->items.begin(), s->items.end(),
+                     [](const KickItem& a, const KickItem& b) { return (a.j1 - a.j0) > (b.j1 - b.j0); });
+}
+
+void build_pair_tiles(opal_sim* s) {
+    s->tiles.clear();
+    s->tile_off.assign(1, 0);
+    for (size_t k = 0; k < s->sys.size(); k++) {
+        const SysInfo& si = s->sys[k];
+        const int64_t nt = (si.n + kSeg - 1) / kSeg;
+        for (int64_t a = 0; a < nt; a++)
+            for (int64_t b = a; b < nt; b++) {
+                PairTile t{};
+                t.sys = (int32_t)k;
+                t.i0 = si.off + a * kSeg;
+                t.j0 = si.off + b * kSeg;
+                s->tiles.push_back(t);
+            }
+        s->tile_off.push_back((int64_t)s->tiles.size());
+    }
+}
+
+opal_status validate(const opal_params* p, char* err) {
+    if (!p) return set_err(err, "params is NULL"), OPAL_EINVAL;
+    if (!(std::isfinite(p->G) && p->G > 0)) return set_err(err, "G must be finite and > 0"), OPAL_EINVAL;
+    if (!(std::isfinite(p->M0) && p->M0 > 0)) return set_err(err, "M0 must be finite and > 0"), OPAL_EINVAL;
+    if (!(std::isfinite(p->dt) && p->dt != 0)) return set_err(err, "dt must be finite and nonzero"), OPAL_EINVAL;
+    if (!(std::isfinite(p->rcrit_hill) && p->rcrit_hill >= 0))
+        return set_err(err, "rcrit_hill must be finite and >= 0"), OPAL_EINVAL;
+    if (!(std::isfinite(p->bs_tol) && p->bs_tol > 0)) return set_err(err, "bs_tol must be > 0"), OPAL_EINVAL;
+    if (p->precision != 0 && p->precision != 1) return set_err(err, "precision must be 0 or 1"), OPAL_EINVAL;
+    if (p->changeover != 0 && p->changeover != 1) return set_err(err, "changeover must be 0 or 1"), OPAL_EINVAL;
+    if (p->kepler_max_iter < 0 || p->bs_max_substeps < 0 || p->encounter_capacity < 0)
+        return set_err(err, "caps must be >= 0"), OPAL_EINVAL;
+    return OPAL_OK;
+}
+
+opal_status capture_graph(opal_sim* s);
+
+opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, const double* m, const double* x,
+                        const double* v, const double* R, opal_sim** out) {
+    if (!out) return set_err(g_err, "out is NULL"), OPAL_EINVAL;
+    *out = nullptr;
+    TRY(validate(p, g_err));
+    if (nsys <= 0 || !nps) return set_err(g_err, "need at least one system"), OPAL_EINVAL;
+    int64_t ntot = 0;
+    for (int32_t k = 0; k < nsys; k++) {
+        if (nps[k] <= 0) return set_err(g_err, "system %d has n = %lld <= 0", k, (long long)nps[k]), OPAL_EINVAL;
+        ntot += nps[k];
+    }
+    if (ntot > (int64_t)1 << 30) return set_err(g_err, "too many bodies"), OPAL_EINVAL;
+    if (!m || !x || !v || !R) return set_err(g_err, "NULL body array"), OPAL_EINVAL;
+    if (!finite_all(m, ntot) || !finite_all(x, 3 * ntot) || !finite_all(v, 3 * ntot) || !finite_all(R, ntot))
+        return set_err(g_err, "non-finite value in the bodies"), OPAL_EINVAL;
+    for (int64_t i = 0; i < ntot; i++) {
+        if (m[i] < 0) return set_err(g_err, "body %lld has negative mass", (long long)i), OPAL_EINVAL;
+        if (R[i] < 0) return set_err(g_err, "body %lld has negative radius", (long long)i), OPAL_EINVAL;
+        if (x[3 * i] == 0 && x[3 * i + 1] == 0 && x[3 * i + 2] == 0)
+            return set_err(g_err, "body %lld sits on the star", (long long)i), OPAL_EINVAL;
+    }
+    opal_sim* s = new (std::nothrow) opal_sim();
+    if (!s) return set_err(g_err, "host allocation failed"), OPAL_ENOMEM;
+    opal_status st = OPAL_OK;
+    auto fail = [&](opal_status code) {
+        std::memcpy(g_err, s->err, sizeof(g_err));
+        opal_destroy(s);
+        return code;
+    };
+#define CKF(call)                                                                               \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            set_err(s->err, "%s failed: %s", #call, cudaGetErrorString(e_));                    \
+            return fail(OPAL_ECUDA);                                                            \
+        }                                                                                       \
+    } while (0)
+#define TRYF(call)                        \
+    do {                                  \
+        opal_status st_ = (call);         \
+        if (st_ != OPAL_OK) return fail(st_); \
+    } while (0)
+    CKF(cudaGetDevice(&s->dev));
+    CKF(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
+    CKF(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    CKF(group_setup());
+
+    // parameters
+    Params& P = s->d.p;
+    P.G = p->G; P.M0 = p->M0; P.dt = p->dt; P.rcrit_hill = p->rcrit_hill; P.bs_tol = p->bs_tol;
+    P.precision = p->precision; P.changeover = p->changeover;
+    P.kepler_max_iter = p->kepler_max_iter > 0 ? p->kepler_max_iter : 50;
+    P.bs_max_substeps = p->bs_max_substeps > 0 ? p->bs_max_substeps : (1 << 20);
+    P.encounter_capacity = p->encounter_capacity > 0 ? p->encounter_capacity : std::max<int64_t>(4096, 4 * ntot);
+
+    // layout
+    int64_t off = 0;
+    for (int32_t k = 0; k < nsys; k++) {
+        SysInfo si{};
+        si.off = off;
+        si.n = nps[k];
+        si.cap = (nps[k] + kPad - 1) / kPad * kPad;
+        si.seg0 = off / kSeg;
+        si.nseg = si.cap / kSeg;
+        s->sys.push_back(si);
+        s->n_per_sys.push_back(nps[k]);
+        off += si.cap;
+    }
+    const int64_t N = off;
+    s->n_total = ntot;
+    Dev& d = s->d;
+    d.ntot = N;
+    d.nsys = nsys;
+    d.nseg_tot = N / kSeg;
+    // kick variants: the work list of each, and the largest partial buffer any needs
+    const int nvar = kick_num_variants(p->precision);
+    std::vector<std::vector<KickItem>> var_items(nvar);
+    std::vector<std::vector<SysInfo>> var_sys(nvar);
+    std::vector<int> var_grid(nvar);
+    int64_t max_slots = 0;
+    for (int v = 0; v < nvar; v++) {
+        int occ = std::max(1, kick_occupancy(p->precision, v));
+        build_kick_items(s, s->nsm * occ);
+        var_items[v] = s->items;
+        var_sys[v] = s->sys;
+        var_grid[v] = (int)std::min<int64_t>((int64_t)s->items.size(), (int64_t)s->nsm * occ);
+        int64_t sl = 0;
+        for (auto& si : s->sys) sl += (int64_t)si.nchunk * si.cap;
+        max_slots = std::max(max_slots, sl);
+    }
+    build_pair_tiles(s);
+    s->scan_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (int64_t)s->tiles.size()), (int64_t)s->nsm * 16);
+    s->energy_grid = s->scan_grid;
+    s->confirm_grid = s->nsm * 2;
+    s->bs_grid = s->nsm * 4;
+    const int64_t slots = max_slots;
+
+    double** f64[] = {&d.x, &d.y, &d.z, &d.vx, &d.vy, &d.vz, &d.ax, &d.ay, &d.az, &d.x0, &d.y0, &d.z0,
+                      &d.vx0, &d.vy0, &d.vz0, &d.xs, &d.ys, &d.zs, &d.vxs, &d.vys, &d.vzs, &d.rcs,
+                      &d.m, &d.R, &d.rc};
+    for (auto pp : f64) TRYF(dalloc(s, pp, N));
+    TRYF(dalloc(s, &d.alive, N));
+    TRYF(dalloc(s, &d.body_sys, N));
+    TRYF(dalloc(s, &d.label, N));
+    float4** f4[] = {&d.kh, &d.kl, &d.sc0, &d.sc1, &d.sv0, &d.sv1};
+    for (auto pp : f4) TRYF(dalloc(s, pp, N));
+    TRYF(dalloc(s, &d.rcf, N));
+    TRYF(dalloc(s, &d.rcmax, nsys));
+    TRYF(dalloc(s, &d.pacc_x, slots));
+    TRYF(dalloc(s, &d.pacc_y, slots));
+    TRYF(dalloc(s, &d.pacc_z, slots));
+    TRYF(dalloc(s, &d.pP_close, 3 * d.nseg_tot));
+    TRYF(dalloc(s, &d.pP_open, 3 * d.nseg_tot));
+    d.flag_cap = P.encounter_capacity;
+    d.cand_cap = std::max<int64_t>(1 << 16, 8 * d.flag_cap);
+    TRYF(dalloc(s, &d.cand, d.cand_cap));
+    TRYF(dalloc(s, &d.flag, d.flag_cap));
+    TRYF(dalloc(s, &d.members, 2 * d.flag_cap + 2));
+    TRYF(dalloc(s, &d.goff, 2 * d.flag_cap + 2));
+    TRYF(dalloc(s, &d.glost, 2 * d.flag_cap + 2));
+    TRYF(dalloc(s, &d.undo, 3 * (2 * d.flag_cap + 2)));
+    TRYF(dalloc(s, &d.E_lost, nsys));
+    TRYF(dalloc(s, &d.ctl, 1));
+    TRYF(dalloc(s, &d.sys, nsys));
+    size_t max_items = 0;
+    for (auto& it : var_items) max_items = std::max(max_items, it.size());
+    TRYF(dalloc(s, &s->d_items, max_items));
+    TRYF(dalloc(s, &s->d_tiles, s->tiles.size()));
+    TRYF(dalloc(s, &s->d_tile_off, s->tile_off.size()));
+    TRYF(dalloc(s, &s->d_vh, 3 * N));
+    TRYF(dalloc(s, &s->d_en_body, 7 * (N / 128)));
+    TRYF(dalloc(s, &s->d_en_pair, s->tiles.size()));
+    TRYF(dalloc(s, &s->d_en_out, 8 * nsys));
+
+    // host staging in the padded SoA layout
+    std::vector<double> hx(N), hy(N), hz(N), hvx(N, 0.0), hvy(N, 0.0), hvz(N, 0.0), hm(N, 0.0), hR(N, 0.0);
+    std::vector<int32_t> halive(N, 0), hsys(N, 0), hlabel(N, -1);
+    int64_t src = 0;
+    for (int32_t k = 0; k < nsys; k++) {
+        const SysInfo& si = s->sys[k];
+        for (int64_t t = 0; t < si.cap; t++) {
+            int64_t b = si.off + t;
+            hsys[b] = k;
+            if (t < si.n) {
+                hx[b] = x[3 * src]; hy[b] = x[3 * src + 1]; hz[b] = x[3 * src + 2];
+                hvx[b] = v[3 * src]; hvy[b] = v[3 * src + 1]; hvz[b] = v[3 * src + 2];
+                hm[b] = m[src];
+                hR[b] = R[src];
+                halive[b] = 1;
+                src++;
+            } else {   // ghost: massless, parked far away
+                hx[b] = 1.0e6 + (double)b; hy[b] = 0.0; hz[b] = 0.0;
+            }
+        }
+    }
+    auto up = [&](void* dst, const void* srcp, size_t bytes) {
+        return cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyHostToDevice, s->stream);
+    };
+    CKF(up(d.x, hx.data(), N * 8)); CKF(up(d.y, hy.data(), N * 8)); CKF(up(d.z, hz.data(), N * 8));
+    CKF(up(d.vx, hvx.data(), N * 8)); CKF(up(d.vy, hvy.data(), N * 8)); CKF(up(d.vz, hvz.data(), N * 8));
+    CKF(up(d.m, hm.data(), N * 8)); CKF(up(d.R, hR.data(), N * 8));
+    CKF(up(d.alive, halive.data(), N * 4)); CKF(up(d.body_sys, hsys.data(), N * 4));
+    CKF(up(d.label, hlabel.data(), N * 4));
+    CKF(up(s->d_tiles, s->tiles.data(), s->tiles.size() * sizeof(PairTile)));
+    CKF(up(s->d_tile_off, s->tile_off.data(), s->tile_off.size() * sizeof(int64_t)));
+    CKF(cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), s->stream));
+    CKF(cudaMemsetAsync(d.E_lost, 0, nsys * 8, s->stream));
+    CKF(cudaMemsetAsync(d.ax, 0, N * 8, s->stream));
+    CKF(cudaMemsetAsync(d.ay, 0, N * 8, s->stream));
+    CKF(cudaMemsetAsync(d.az, 0, N * 8, s->stream));
+    CKF(cudaMemsetAsync(d.rcmax, 0, nsys * 4, s->stream));
+    // democratic heliocentric velocities, critical radii (offsets and
+    // capacities are the same in every variant's system table)
+    CKF(up(d.sys, var_sys[0].data(), nsys * sizeof(SysInfo)));
+    launch_to_dh(d, s->stream);
+    launch_prime(d, s->stream);
+    // pick the kick variant: timed on this simulation's own positions
+    {
+        int best = p->precision == 1 ? 1 : 0;
+        const char* force = getenv("OPAL_KICK_VARIANT");
+        double work = 0;
+        for (auto& si : s->sys) work += (double)si.cap * (double)si.n;
+        double best_ms = -1;
+        if (force) {
+            best = std::max(0, std::min(nvar - 1, atoi(force)));
+        } else if (nvar > 1 && work >= 4.0e6) {
+            cudaEvent_t e0, e1;
+            CKF(cudaEventCreate(&e0));
+            CKF(cudaEventCreate(&e1));
+            for (int v = 0; v < nvar; v++) {
+                CKF(up(d.sys, var_sys[v].data(), nsys * sizeof(SysInfo)));
+                CKF(up(s->d_items, var_items[v].data(), var_items[v].size() * sizeof(KickItem)));
+                const int reps = work >= 1e8 ? 3 : 10;
+                launch_kick(d, s->d_items, (int64_t)var_items[v].size(), var_grid[v], P.precision, v, s->stream);
+                CKF(cudaEventRecord(e0, s->stream));
+                for (int r = 0; r < reps; r++)
+                    launch_kick(d, s->d_items, (int64_t)var_items[v].size(), var_grid[v], P.precision, v, s->stream);
+                CKF(cudaEventRecord(e1, s->stream));
+                CKF(cudaEventSynchronize(e1));
+                float ms = 0;
+                CKF(cudaEventElapsedTime(&ms, e0, e1));
+                if (best_ms < 0 || ms / reps < best_ms) {
+                    best_ms = ms / reps;
+                    best = v;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        s->kick_variant = best;
+        s->items = var_items[best];
+        s->sys = var_sys[best];
+        s->kick_grid = var_grid[best];
+        snprintf(s->kick_desc, sizeof(s->kick_desc), "%s, grid %d, %zu items, %d j-chunks (system 0)%s",
+                 kick_variant_name(p->precision, best), s->kick_grid, s->items.size(), s->sys[0].nchunk,
+                 force ? ", forced" : (best_ms >= 0 ? ", autotuned" : ""));
+        CKF(up(d.sys, s->sys.data(), nsys * sizeof(SysInfo)));
+        CKF(up(s->d_items, s->items.data(), s->items.size() * sizeof(KickItem)));
+    }
+    launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, P.precision, s->kick_variant, s->stream);
+    launch_first_accel_finish(d, s->stream);
+    CKF(cudaGetLastError());
+    CKF(cudaStreamSynchronize(s->stream));
+    Ctl c{};
+    CKF(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (c.status) {
+        set_err(s->err, "initial accelerations: %s (body %d)", status_name(c.status), c.detail);
+        return fail((opal_status)c.status);
+    }
+    st = capture_graph(s);
+    if (st != OPAL_OK) return fail(st);
+    *out = s;
+    return OPAL_OK;
+#undef CKF
+#undef TRYF
+}
+
+// the kernels of one step, in order; names for profiling
+const char* kKernelNames[] = {"counters", "open(kick+jump+drift)", "scan", "confirm", "group", "bs", "kick",
+                              "close(jump+kick)", "finish"};
+constexpr int kNumKernels = 9;
+
+void launch_stage(opal_sim* s, int k) {
+    const Dev& d = s->d;
+    switch (k) {
+        case 0:
+            cudaMemsetAsync(reinterpret_cast<char*>(d.ctl) + offsetof(Ctl, ncand), 0,
+                            offsetof(Ctl, steps_done) - offsetof(Ctl, ncand), s->stream);
+            cudaMemsetAsync(d.rcmax, 0, d.nsys * sizeof(float), s->stream);
+            break;
+        case 1: launch_open(d, s->stream); break;
+        case 2: launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, s->stream); break;
+        case 3: launch_confirm(d, s->confirm_grid, s->stream); break;
+        case 4: launch_group(d, s->stream); break;
+        case 5: launch_bs(d, s->bs_grid, s->stream); break;
+        case 6:
+            launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant,
+                        s->stream);
+            break;
+        case 7: launch_close(d, s->stream); break;
+        case 8: launch_finish(d, s->stream); break;
+    }
+}
+
+opal_status capture_graph(opal_sim* s) {
+    if (s->exec) {
+        CK(cudaGraphExecDestroy(s->exec));
+        s->exec = nullptr;
+    }
+    if (s->graph) {
+        CK(cudaGraphDestroy(s->graph));
+        s->graph = nullptr;
+    }
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < kNumKernels; k++) {
+        if (s->time_kick && k == 6) cudaEventRecordWithFlags(s->kick_ev[0], s->stream, cudaEventRecordExternal);
+        launch_stage(s, k);
+        if (s->time_kick && k == 6) cudaEventRecordWithFlags(s->kick_ev[1], s->stream, cudaEventRecordExternal);
+    }
+    cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
+    if (e != cudaSuccess) {
+        set_err(s->err, "graph capture failed: %s", cudaGetErrorString(e));
+        return OPAL_ECUDA;
+    }
+    CK(cudaGraphInstantiate(&s->exec, s->graph, 0));
+    return OPAL_OK;
+}
+
+opal_status finish_steps(opal_sim* s, int64_t before) {
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    Ctl c{};
+    CK(cudaMemcpy(&c, s->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (c.status) {
+        set_err(s->err, "step %lld: %s (detail %d)", (long long)(c.steps_done + 1), status_name(c.status),
+                c.detail);
+        int zero[2] = {0, 0};
+        CK(cudaMemcpy(s->d.ctl, zero, sizeof(zero), cudaMemcpyHostToDevice));
+        return (opal_status)c.status;
+    }
+    (void)before;
+    return OPAL_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void opal_default_params(opal_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->G = 1.0;
+    p->M0 = 1.0;
+    p->dt = 2.0 * M_PI * 0.01;
+    p->rcrit_hill = 3.0;
+    p->bs_tol = 1e-12;
+    p->precision = 1;
+    p->changeover = 0;
+}
+
+opal_status opal_create(const opal_params* p, int64_t n, const double* m, const double* x, const double* v,
+                        const double* radius, opal_sim** out) {
+    return create_impl(p, 1, &n, m, x, v, radius, out);
+}
+
+opal_status opal_ensemble_create(const opal_params* p, int32_t nsys, const int64_t* n_per_sys, const double* m,
+                                 const double* x, const double* v, const double* radius, opal_sim** out) {
+    return create_impl(p, nsys, n_per_sys, m, x, v, radius, out);
+}
+
+opal_status opal_step(opal_sim* s, int64_t nsteps) {
+    if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
+    if (nsteps < 0) return set_err(s->err, "nsteps < 0"), OPAL_EINVAL;
+    for (int64_t k = 0; k < nsteps; k++) CK(cudaGraphLaunch(s->exec, s->stream));
+    return finish_steps(s, 0);
+}
+
+opal_status opal_step_async(opal_sim* s, int64_t nsteps) {
+    if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
+    if (nsteps < 0) return set_err(s->err, "nsteps < 0"), OPAL_EINVAL;
+    for (int64_t k = 0; k < nsteps; k++) CK(cudaGraphLaunch(s->exec, s->stream));
+    return OPAL_OK;
+}
+
+opal_status opal_wait(opal_sim* s) {
+    if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
+    return finish_steps(s, 0);
+}
+
+int32_t opal_num_systems(const opal_sim* s) { return s ? s->d.nsys : 0; }
+int64_t opal_num_bodies(const opal_sim* s) { return s ? s->n_total : 0; }
+
+int64_t opal_steps_done(const opal_sim* s) {
+    if (!s) return -1;
+    long long v = 0;
+    cudaStreamSynchronize(s->stream);
+    cudaMemcpy(&v, reinterpret_cast<char*>(s->d.ctl) + offsetof(Ctl, steps_done), sizeof(v),
+               cudaMemcpyDeviceToHost);
+    return v;
+}
+
+opal_status opal_get_state(const opal_sim* cs, int32_t sys, int64_t* n_alive, int64_t* ids, double* m, double* x,
+                           double* v, double* radius) {
+    opal_sim* s = const_cast<opal_sim*>(cs);
+    if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
+    if (sys < 0 || sys >= s->d.nsys) return set_err(s->err, "no system %d", sys), OPAL_EINVAL;
+    const SysInfo si = s->sys[sys];
+    const int64_t n = si.n;
+    launch_export(s->d, s->d_vh, s->stream);
+    CK(cudaGetLastError());
+    std::vector<double> hx(n), hy(n), hz(n), hm(n), hR(n), hv(3 * n);
+    std::vector<int32_t> ha(n);
+    auto dn = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream);
+    };
+    CK(dn(hx.data(), s->d.x + si.off, n * 8)); CK(dn(hy.data(), s->d.y + si.off, n * 8));
+    CK(dn(hz.data(), s->d.z + si.off, n * 8)); CK(dn(hm.data(), s->d.m + si.off, n * 8));
+    CK(dn(hR.data(), s->d.R + si.off, n * 8)); CK(dn(ha.data(), s->d.alive + si.off, n * 4));
+    CK(dn(hv.data(), s->d_vh + 3 * si.off, 3 * n * 8));
+    CK(cudaStreamSynchronize(s->stream));
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (!ha[i]) continue;
+        if (ids) ids[k] = i;
+        if (m) m[k] = hm[i];
+        if (radius) radius[k] = hR[i];
+        if (x) { x[3 * k] = hx[i]; x[3 * k + 1] = hy[i]; x[3 * k + 2] = hz[i]; }
+        if (v) { v[3 * k] = hv[3 * i]; v[3 * k + 1] = hv[3 * i + 1]; v[3 * k + 2] = hv[3 * i + 2]; }
+        k++;
+    }
+    if (n_alive) *n_alive = k;
+    return OPAL_OK;
+}
+
+opal_status opal_energy_momentum(const opal_sim* cs, int32_t sys, double* E, double L[3], double P[3],
+                                 double* E_merged_lost) {
+    opal_sim* s = const_cast<opal_sim*>(cs);
+    if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
+    if (sys < 0 || sys >= s->d.nsys) return set_err(s->err, "no system %d", sys), OPAL_EINVAL;
+    launch_energy(s->d, s->d_tiles, (int64_t)s->tiles.size(), s->d_tile_off, s->d_en_pair, s->d_en_body,
+                  s->d_en_out, s->energy_grid, s->stream);
+    CK(cudaGetLastError());
+    double o[8];
+    CK(cudaMemcpyAsync(o, s->d_en_out + 8 * sys, sizeof(o), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (E) *E = o[0];
+    if (L) { L[0] = o[1]; L[1] = o[2]; L[2] = o[3]; }
+    if (P) { P[0] = o[4]; P[1] = o[5]; P[2] = o[6]; }
+    if (E_merged_lost) *E_merged_lost = o[7];
+    return OPAL_OK;
+}
+
+opal_status opal_last_step_stats(const opal_sim* cs, int64_t out[6]) {
+    opal_sim* s = const_cast<opal_sim*>(cs);
+    if (!s || !out) return set_err(g_err, "NULL argument"), OPAL_EINVAL;
+    Ctl c{};
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(&c, s->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    out[0] = c.nflag;
+    out[1] = c.ngroups;
+    out[2] = c.nmerge;
+    out[3] = (int64_t)c.nsub;
+    out[4] = c.ncand;
+    out[5] = c.kepler_max;
+    return OPAL_OK;
+}
+
+void* opal_stream(const opal_sim* s) { return s ? (void*)s->stream : nullptr; }
+
+opal_status opal_profile_steps(opal_sim* s, int64_t nsteps, int32_t cap, int32_t* nk, double* ms,
+                               const char** names) {
+    if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
+    const int K = kNumKernels;
+    if (nk) *nk = K;
+    std::vector<cudaEvent_t> ev(K + 1);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    std::vector<double> acc(K, 0.0);
+    for (int64_t t = 0; t < nsteps; t++) {
+        for (int k = 0; k < K; k++) {
+            CK(cudaEventRecord(ev[k], s->stream));
+            launch_stage(s, k);
+        }
+        CK(cudaEventRecord(ev[K], s->stream));
+        CK(cudaEventSynchronize(ev[K]));
+        for (int k = 0; k < K; k++) {
+            float f = 0;
+            CK(cudaEventElapsedTime(&f, ev[k], ev[k + 1]));
+            acc[k] += f;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < K && k < cap; k++) {
+        if (ms) ms[k] = nsteps > 0 ? acc[k] / (double)nsteps : 0.0;
+        if (names) names[k] = kKernelNames[k];
+    }
+    return finish_steps(s, 0);
+}
+
+const char* opal_last_error(const opal_sim* s) { return s ? s->err : g_err; }
+
+const char* opal_kick_config(const opal_sim* s) { return s ? s->kick_desc : ""; }
+
+opal_status opal_time_kick(opal_sim* s, int32_t enable) {
+    if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
+    if (enable && !s->kick_ev[0]) {
+        CK(cudaEventCreate(&s->kick_ev[0]));
+        CK(cudaEventCreate(&s->kick_ev[1]));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    s->time_kick = enable ? 1 : 0;
+    return capture_graph(s);
+}
+
+double opal_last_kick_ms(const opal_sim* cs) {
+    opal_sim* s = const_cast<opal_sim*>(cs);
+    if (!s || !s->time_kick) return -1.0;
+    if (cudaEventSynchronize(s->kick_ev[1]) != cudaSuccess) return -1.0;
+    float ms = -1.0f;
+    if (cudaEventElapsedTime(&ms, s->kick_ev[0], s->kick_ev[1]) != cudaSuccess) return -1.0;
+    return ms;
+}
+
+void opal_destroy(opal_sim* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    for (auto e : s->kick_ev)
+        if (e) cudaEventDestroy(e);
+    for (void* p : s->allocs) cudaFree(p);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+// ---------------------------------------------------------------------------
+// test hooks (include/opal_testing.h)
+
+opal_status opal_debug_accel(opal_sim* s, const double* rc, double* a) {
+    if (!s || !a) return set_err(g_err, "NULL argument"), OPAL_EINVAL;
+    Dev& d = s->d;
+    const int64_t N = d.ntot;
+    if (rc) {
+        std::vector<double> h(N, 0.0);
+        int64_t src = 0;
+        for (auto& si : s->sys)
+            for (int64_t t = 0; t < si.n; t++) h[si.off + t] = rc[src++];
+        CK(cudaMemcpyAsync(d.rc, h.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    // float copies of the current positions with these rc, then the kick
+    CK(cudaMemsetAsync(d.rcmax, 0, d.nsys * 4, s->stream));
+    launch_debug_scan_prep(d, s->stream);
+    launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, s->stream);
+    launch_first_accel_finish(d, s->stream);
+    CK(cudaGetLastError());
+    std::vector<double> ax(N), ay(N), az(N);
+    CK(cudaMemcpyAsync(ax.data(), d.ax, N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(ay.data(), d.ay, N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(az.data(), d.az, N * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    int64_t dst = 0;
+    for (auto& si : s->sys)
+        for (int64_t t = 0; t < si.n; t++, dst++) {
+            a[3 * dst] = ax[si.off + t];
+            a[3 * dst + 1] = ay[si.off + t];
+            a[3 * dst + 2] = az[si.off + t];
+        }
+    return OPAL_OK;
+}
+
+opal_status opal_debug_drift(int64_t n, double mu, double dt, int32_t max_iter, double* x, double* v,
+                             int32_t* iters) {
+    if (n <= 0 || !x || !v || !iters) return set_err(g_err, "bad argument"), OPAL_EINVAL;
+    double *dx = nullptr, *dv = nullptr;
+    int* di = nullptr;
+    cudaError_t e = cudaMalloc(&dx, n * 24);
+    if (e == cudaSuccess) e = cudaMalloc(&dv, n * 24);
+    if (e == cudaSuccess) e = cudaMalloc(&di, n * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x, n * 24, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dv, v, n * 24, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_debug_drift((int)n, mu, dt, max_iter > 0 ? max_iter : 50, dx, dv, di, 0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(x, dx, n * 24, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(v, dv, n * 24, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(iters, di, n * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dv);
+    cudaFree(di);
+    if (e != cudaSuccess) return set_err(g_err, "drift test hook: %s", cudaGetErrorString(e)), OPAL_ECUDA;
+    return OPAL_OK;
+}
+
+static opal_status upload_soa(opal_sim* s, const double* src, double* dx, double* dy, double* dz) {
+    const int64_t N = s->d.ntot;
+    std::vector<double> a(N, 0.0), b(N, 0.0), c(N, 0.0);
+    int64_t k = 0;
+    for (auto& si : s->sys)
+        for (int64_t t = 0; t < si.n; t++, k++) {
+            a[si.off + t] = src[3 * k];
+            b[si.off + t] = src[3 * k + 1];
+            c[si.off + t] = src[3 * k + 2];
+        }
+    CK(cudaMemcpyAsync(dx, a.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(dy, b.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(dz, c.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return OPAL_OK;
+}
+
+opal_status opal_debug_scan(opal_sim* s, const double* x0, const double* V0, const double* x1, const double* V1,
+                            const double* rc, int64_t cap, int32_t* pi, int32_t* pj, int64_t* count,
+                            int64_t* ncand) {
+    if (!s || !x0 || !V0 || !x1 || !V1 || !rc || !count) return set_err(g_err, "NULL argument"), OPAL_EINVAL;
+    Dev& d = s->d;
+    TRY(upload_soa(s, x0, d.x0, d.y0, d.z0));
+    TRY(upload_soa(s, V0, d.vx0, d.vy0, d.vz0));
+    TRY(upload_soa(s, x1, d.x, d.y, d.z));
+    TRY(upload_soa(s, V1, d.vx, d.vy, d.vz));
+    {
+        const int64_t N = d.ntot;
+        std::vector<double> h(N, 0.0);
+        int64_t k = 0;
+        for (auto& si : s->sys)
+            for (int64_t t = 0; t < si.n; t++) h[si.off + t] = rc[k++];
+        CK(cudaMemcpyAsync(d.rc, h.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
+    }
+    CK(cudaMemsetAsync(reinterpret_cast<char*>(d.ctl) + offsetof(Ctl, ncand), 0,
+                       offsetof(Ctl, steps_done) - offsetof(Ctl, ncand), s->stream));
+    launch_debug_scan_prep(d, s->stream);
+    launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, s->stream);
+    launch_confirm(d, s->confirm_grid, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    Ctl c{};
+    CK(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (ncand) *ncand = c.ncand;
+    if (c.status) {
+        int zero[2] = {0, 0};
+        cudaMemcpy(d.ctl, zero, sizeof(zero), cudaMemcpyHostToDevice);
+        set_err(s->err, "scan: %s", status_name(c.status));
+        return (opal_status)c.status;
+    }
+    std::vector<int2> fl(std::min<int64_t>(c.nflag, d.flag_cap));
+    if (!fl.empty()) CK(cudaMemcpy(fl.data(), d.flag, fl.size() * sizeof(int2), cudaMemcpyDeviceToHost));
+    // report in body order of the input (system-local indices are global input order)
+    std::vector<int64_t> map(d.ntot, -1);
+    int64_t k = 0;
+    for (auto& si : s->sys)
+        for (int64_t t = 0; t < si.n; t++) map[si.off + t] = k++;
+    std::vector<std::pair<int64_t, int64_t>> pr;
+    for (auto& f : fl) pr.push_back({map[f.x], map[f.y]});
+    std::sort(pr.begin(), pr.end());
+    *count = (int64_t)pr.size();
+    for (int64_t q = 0; q < (int64_t)pr.size() && q < cap; q++) {
+        pi[q] = (int32_t)pr[q].first;
+        pj[q] = (int32_t)pr[q].second;
+    }
+    return OPAL_OK;
+}
+
+opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0, const double* rc, double* x,
+                                double* V, double* m, double* radius, int32_t* alive, double* E_lost,
+                                int64_t* substeps) {
+    if (!s || !x0 || !V0 || !rc || !x || !V || !m || !radius || !alive)
+        return set_err(g_err, "NULL argument"), OPAL_EINVAL;
+    if (s->d.nsys != 1) return set_err(s->err, "one system only"), OPAL_EINVAL;
+    Dev& d = s->d;
+    const SysInfo si = s->sys[0];
+    const int64_t n = si.n;
+    if (n > kBsMaxMembers) return set_err(s->err, "group larger than %d", kBsMaxMembers), OPAL_EINVAL;
+    TRY(upload_soa(s, x0, d.x0, d.y0, d.z0));
+    TRY(upload_soa(s, V0, d.vx0, d.vy0, d.vz0));
+    std::vector<double> h(d.ntot, 0.0), hm(d.ntot, 0.0), hR(d.ntot, 0.0);
+    std::vector<int32_t> ha(d.ntot, 0), mem(n), goff = {0, (int32_t)n};
+    for (int64_t t = 0; t < n; t++) {
+        h[t] = rc[t];
+        hm[t] = m[t];
+        hR[t] = radius[t];
+        ha[t] = alive[t];
+        mem[t] = (int32_t)t;
+    }
+    CK(cudaMemcpy(d.rc, h.data(), d.ntot * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.m, hm.data(), d.ntot * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.R, hR.data(), d.ntot * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.alive, ha.data(), d.ntot * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.members, mem.data(), n * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.goff, goff.data(), 8, cudaMemcpyHostToDevice));
+    Ctl c{};
+    c.ngroups = 1;
+    c.ninvolved = (int)n;
+    CK(cudaMemcpy(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+    launch_bs(d, 1, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    int zero[2] = {0, 0};
+    CK(cudaMemcpy(d.ctl, zero, sizeof(zero), cudaMemcpyHostToDevice));
+    if (substeps) *substeps = (int64_t)c.nsub;
+    if (c.status) {
+        set_err(s->err, "bs: %s", status_name(c.status));
+        return (opal_status)c.status;
+    }
+    std::vector<double> a(n), b(n), cc(n), va(n), vb(n), vc(n), gl(1);
+    CK(cudaMemcpy(a.data(), d.x, n * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(b.data(), d.y, n * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cc.data(), d.z, n * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(va.data(), d.vx, n * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vb.data(), d.vy, n * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(vc.data(), d.vz, n * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(m, d.m, n * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(radius, d.R, n * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(alive, d.alive, n * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(gl.data(), d.glost, 8, cudaMemcpyDeviceToHost));
+    for (int64_t t = 0; t < n; t++) {
+        x[3 * t] = a[t]; x[3 * t + 1] = b[t]; x[3 * t + 2] = cc[t];
+        V[3 * t] = va[t]; V[3 * t + 1] = vb[t]; V[3 * t + 2] = vc[t];
+    }
+    if (E_lost) *E_lost = gl[0];
+    return OPAL_OK;
+}
+
+}  // extern "C"

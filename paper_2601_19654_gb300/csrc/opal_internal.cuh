@@ -1,0 +1,302 @@
+// Internal layout and device helpers of the GB300 hybrid symplectic step.
+//
+// Body arrays are structure-of-arrays in HBM, systems packed one after
+// another, each padded to a multiple of kPad bodies (ghost bodies: m = 0,
+// alive = 0, parked far away).  All FP64 state stays resident on the device
+// for the lifetime of a simulation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/opal.h"
+
+namespace opal {
+
+constexpr int kPad = 128;        // body padding of every system (block of the body kernels)
+constexpr int kSeg = 64;         // bodies per partial-sum segment
+constexpr int kBodyThreads = 128;
+constexpr int kBsMaxMembers = 64;   // bodies per encounter group
+constexpr int kBsWarps = 4;         // warps per BS group (two midpoint sequences each)
+constexpr int kBsRows = 8;          // extrapolation rows: n_k = 2, 4, ..., 16
+constexpr int kGroupMaxBodies = 4096;   // flagged pairs the grouping kernel takes per step
+constexpr float kFar = 1.0e18f;     // parking coordinate of ghost and dead bodies (float copies)
+
+// status codes mirror opal_status
+enum : int { kOk = 0, kEinval = 1, kEnomem = 2, kEcuda = 3, kEkepler = 4, kEbs = 5, kEoverflow = 6,
+             kEnonfinite = 7 };
+
+// four doubles, 32-byte aligned (one shared-memory slot of a j-body)
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+
+// Device control block: status word and per-step counters.
+struct Ctl {
+    int status;          // first error of the current opal_step call (0 = ok)
+    int detail;          // body or group index that raised it
+    int ncand;           // pairs passing the FP32 bounds (this step)
+    int nflag;           // flagged pairs (this step)
+    int ngroups;         // encounter groups (this step)
+    int ninvolved;       // bodies in groups (this step)
+    int nmerge;          // mergers (this step)
+    int kepler_max;      // largest drift iteration count (this step)
+    unsigned long long nsub;  // BS substeps (this step)
+    long long steps_done;
+    int cand_overflow;   // candidates lost to a full candidate list (forces a status)
+    int pad;
+};
+
+// Per-system constants.
+struct SysInfo {
+    int64_t off;      // first body
+    int64_t cap;      // padded body count (multiple of kPad)
+    int64_t n;        // bodies given at create
+    int64_t seg0;     // first partial-sum segment (off / kSeg)
+    int64_t nseg;     // cap / kSeg
+    int64_t slot0;    // first row of the kick's partial-acceleration buffer
+    int32_t nchunk;   // j-chunks of the kick for this system
+    int32_t pad;
+};
+
+// One unit of kick work: an i-tile against a j-range of the same system.
+struct KickItem {
+    int32_t sys;
+    int32_t chunk;    // index of the j-range within the system
+    int64_t i0;       // first body of the i-tile (global)
+    int64_t j0, j1;   // j-range (global, half-open)
+};
+
+// One unit of scan / energy work: an i-tile against a j-tile at or above it.
+struct PairTile {
+    int32_t sys;
+    int32_t pad;
+    int64_t i0, j0;   // tile starts (global); tiles are kSeg bodies
+};
+
+struct Params {
+    double G, M0, dt, rcrit_hill, bs_tol;
+    int precision, changeover, kepler_max_iter, bs_max_substeps;
+    int64_t encounter_capacity;
+};
+
+// All device pointers of one simulation (passed by value to kernels).
+struct Dev {
+    int64_t ntot;
+    int nsys;
+    Params p;
+    SysInfo* sys;
+    int32_t* body_sys;
+    // FP64 state
+    double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az;
+    double *x0, *y0, *z0, *vx0, *vy0, *vz0;      // start of drift
+    double *xs, *ys, *zs, *vxs, *vys, *vzs, *rcs; // start of step (undo)
+    double *m, *R, *rc;
+    int32_t* alive;
+    // float copies for the pair kernels
+    float4* kh;    // (x_hi, y_hi, z_hi, m) after drift / BS
+    float4* kl;    // (x_lo, y_lo, z_lo, max(4 rc^2, tiny))
+    float* rcf;    // rc as float (rounded up)
+    float* rcmax;  // per system: largest rc of the step (rounded up)
+    float4* sc0;   // (x0_hi, y0_hi, z0_hi, s = prefilter radius)
+    float4* sc1;   // (x0_lo, y0_lo, z0_lo, 0)
+    float4* sv0;   // (V0, |V0|)
+    float4* sv1;   // (V1, |V1|)
+    // partial sums
+    double *pacc_x, *pacc_y, *pacc_z;   // kick partials [slot rows]
+    double *pP_close;                   // [3][nseg_tot] momentum before the closing jump
+    double *pP_open;                    // [3][nseg_tot] momentum before the opening jump
+    int64_t nseg_tot;
+    // encounter pipeline
+    int2* cand;  int64_t cand_cap;      // FP32-bound candidates
+    int2* flag;  int64_t flag_cap;      // flagged pairs
+    int32_t* label;                     // per body; -1 when not in a group
+    int32_t* members;                   // group members, grouped, ascending
+    int32_t* goff;                      // [ngroups + 1] member offsets
+    double* glost;                      // per group energy lost to mergers
+    double* undo;                       // per member slot: m, R, alive (3 doubles)
+    double* E_lost;                     // per system running sum
+    Ctl* ctl;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+
+__device__ __forceinline__ void set_status(Ctl* c, int code, int detail) {
+    if (atomicCAS(&c->status, 0, code) == 0) c->detail = detail;
+}
+
+__device__ __forceinline__ double dot3(double ax, double ay, double az, double bx, double by, double bz) {
+    return ax * bx + ay * by + az * bz;
+}
+
+// Changeover weight K(r; rc): the rational form y^2/(2y^2-2y+1) or the
+// quintic 10y^3-15y^4+6y^5, y = (r - 0.1 rc)/(0.9 rc); 1 beyond rc, 0 below 0.1 rc.
+__device__ __forceinline__ double changeover(double r, double rc, int form) {
+    if (r >= rc) return 1.0;
+    double y = (r - 0.1 * rc) / (0.9 * rc);
+    if (y <= 0.0) return 0.0;
+    if (form == 0) return y * y / (2.0 * y * y - 2.0 * y + 1.0);
+    return y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
+}
+
+__device__ __forceinline__ float changeover_f(float r, float rc, int form) {
+    if (r >= rc) return 1.0f;
+    float y = (r - 0.1f * rc) / (0.9f * rc);
+    if (y <= 0.0f) return 0.0f;
+    if (form == 0) return y * y / (2.0f * y * y - 2.0f * y + 1.0f);
+    return y * y * y * (10.0f - 15.0f * y + 6.0f * y * y);
+}
+
+// Stumpff functions c0..c3 by their series at an argument quartered until
+// |z| <= 0.1, then the double-angle relations undo the quartering.
+__device__ __forceinline__ void stumpff(double z, double& c0, double& c1, double& c2, double& c3) {
+    int nq = 0;
+    while (fabs(z) > 0.1) {
+        z *= 0.25;
+        nq++;
+    }
+    double s[4];
+    const double inv_fact[4] = {1.0, 1.0, 0.5, 1.0 / 6.0};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        double t = 1.0;
+#pragma unroll
+        for (int j = 10; j >= 1; j--) t = 1.0 - z * t / (double)((k + 2 * j - 1) * (k + 2 * j));
+        s[k] = t * inv_fact[k];
+    }
+    c0 = s[0]; c1 = s[1]; c2 = s[2]; c3 = s[3];
+    for (; nq > 0; nq--) {
+        c3 = (c2 + c0 * c3) * 0.25;
+        c2 = c1 * c1 * 0.5;
+        c1 = c0 * c1;
+        c0 = 2.0 * c0 * c0 - 1.0;
+    }
+}
+
+// Universal-variable Kepler drift over dt (mu = G M0).  Bracketed Newton on
+// F(chi) = r0 G1 + eta G2 + mu G3 - dt (F increasing, root in [0, dt/q] with q
+// the pericentre distance), bisecting when a Newton step leaves the bracket;
+// bound orbits first drop whole periods from dt and start from dt / r0,
+// unbound ones start from the logarithmic value of Vallado's Algorithm 8.  Returns iterations used, or
+// -1 on non-convergence (state untouched).
+__device__ __forceinline__ int kepler_drift(double mu, double dt, int max_iter, double& x, double& y, double& z,
+                                            double& vx, double& vy, double& vz) {
+    double r0 = sqrt(dot3(x, y, z, x, y, z));
+    double v2 = dot3(vx, vy, vz, vx, vy, vz);
+    double eta = dot3(x, y, z, vx, vy, vz);
+    double beta = 2.0 * mu / r0 - v2;
+    if (beta > 0.0) {
+        double period = 2.0 * 3.14159265358979323846 * mu / (beta * sqrt(beta));
+        if (fabs(dt) > period) dt = fmod(dt, period);
+    }
+    double hx = y * vz - z * vy, hy = z * vx - x * vz, hz = x * vy - y * vx;
+    double p = dot3(hx, hy, hz, hx, hy, hz) / mu;
+    double ecc2 = 1.0 - p * beta / mu;
+    double q = p / (1.0 + sqrt(ecc2 > 0.0 ? ecc2 : 0.0));
+    double lo, hi;
+    if (dt >= 0.0) {
+        lo = 0.0;
+        hi = q > 0.0 ? dt / q : HUGE_VAL;
+    } else {
+        lo = q > 0.0 ? dt / q : -HUGE_VAL;
+        hi = 0.0;
+    }
+    double chi = dt / r0;
+    if (beta < 0.0) {
+        // unbound orbit: logarithmic starting value (Vallado, Algorithm 8)
+        double a = mu / beta, sg = dt >= 0.0 ? 1.0 : -1.0;
+        double den = eta + sg * sqrt(-mu * a) * (1.0 - r0 / a);
+        double arg = -2.0 * beta * dt / den;
+        if (den != 0.0 && arg > 0.0 && isfinite(arg)) chi = sg * sqrt(-a / mu) * log(arg);
+    }
+    if (chi < lo) chi = lo;
+    if (chi > hi) chi = hi;
+    double c0, c1, c2, c3;
+    int conv = 0, it;
+    double dchi_prev = HUGE_VAL;
+    for (it = 1; it <= max_iter; it++) {
+        stumpff(beta * chi * chi, c0, c1, c2, c3);
+        double G0 = c0, G1 = chi * c1, G2 = chi * chi * c2, G3 = chi * chi * chi * c3;
+        double F = r0 * G1 + eta * G2 + mu * G3 - dt;
+        double dF = r0 * G0 + eta * G1 + mu * G2;
+        if (F < 0.0) lo = chi;
+        else hi = chi;
+        double chin = chi - F / dF;
+        if (!(chin >= lo && chin <= hi)) chin = 0.5 * (lo + hi);
+        double dchi = chin - chi;
+        chi = chin;
+        if (fabs(dchi) <= 1e-15 * fabs(chi) || (fabs(dchi) <= 1e-12 * fabs(chi) && fabs(dchi) >= dchi_prev)) {
+            conv = 1;
+            break;
+        }
+        dchi_prev = fabs(dchi);
+    }
+    if (!conv) return -1;
+    stumpff(beta * chi * chi, c0, c1, c2, c3);
+    double G0 = c0, G1 = chi * c1, G2 = chi * chi * c2, G3 = chi * chi * chi * c3;
+    double r = r0 * G0 + eta * G1 + mu * G2;
+    double f = 1.0 - mu * G2 / r0, g = dt - mu * G3;
+    double fd = -mu * G1 / (r * r0), gd = 1.0 - mu * G2 / r;
+    double nx = f * x + g * vx, ny = f * y + g * vy, nz = f * z + g * vz;
+    double nvx = fd * x + gd * vx, nvy = fd * y + gd * vy, nvz = fd * z + gd * vz;
+    x = nx; y = ny; z = nz;
+    vx = nvx; vy = nvy; vz = nvz;
+    return it;
+}
+
+// float hi/lo split of a double: hi = rn(x), lo = rn(x - hi)
+__device__ __forceinline__ void split_hl(double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+}
+
+// float copies of a live body for the pair kernels, and parking of a dead one
+__device__ __forceinline__ void park_floats(const Dev& d, int64_t b) {
+    float far = kFar * (1.0f + (float)(b & 1023) * (1.0f / 1024.0f));
+    d.kh[b] = make_float4(far, far, far, 0.0f);
+    d.kl[b] = make_float4(0.0f, 0.0f, 0.0f, 1e-30f);
+    d.rcf[b] = 0.0f;
+    d.sc0[b] = make_float4(far, far, far, 0.0f);
+    d.sc1[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    d.sv0[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    d.sv1[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void kick_floats(const Dev& d, int64_t b, double x, double y, double z, double m,
+                                            double rc) {
+    float hx, lx, hy, ly, hz, lz;
+    split_hl(x, hx, lx);
+    split_hl(y, hy, ly);
+    split_hl(z, hz, lz);
+    d.kh[b] = make_float4(hx, hy, hz, (float)m);
+    d.kl[b] = make_float4(lx, ly, lz, 0.0f);
+    d.rcf[b] = __double2float_ru(rc);
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the kernel translation units)
+
+void launch_to_dh(const Dev& d, cudaStream_t s);
+void launch_prime(const Dev& d, cudaStream_t s);
+void launch_open(const Dev& d, cudaStream_t s);
+void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s);
+void launch_confirm(const Dev& d, int grid, cudaStream_t s);
+void launch_group(const Dev& d, cudaStream_t s);
+cudaError_t group_setup();
+void launch_bs(const Dev& d, int grid, cudaStream_t s);
+void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int variant,
+                 cudaStream_t s);
+int kick_num_variants(int precision);
+const char* kick_variant_name(int precision, int variant);
+int kick_occupancy(int precision, int variant);
+void launch_close(const Dev& d, cudaStream_t s);
+void launch_first_accel_finish(const Dev& d, cudaStream_t s);
+void launch_finish(const Dev& d, cudaStream_t s);
+void launch_energy(const Dev& d, const PairTile* tiles, int64_t ntiles, const int64_t* tile_off,
+                   double* pair_part, double* body_part, double* out, int grid, cudaStream_t s);
+void launch_export(const Dev& d, double* v_helio, cudaStream_t s);
+void launch_debug_drift(int n, double mu, double dt, int max_iter, double* x, double* v, int* iters, cudaStream_t s);
+void launch_debug_scan_prep(const Dev& d, cudaStream_t s);
+
+}  // namespace opal

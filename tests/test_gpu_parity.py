@@ -1,0 +1,373 @@
+"""GPU parity: every stage of the CUDA path, and whole steps, against the oracle.
+
+All calls go through the C ABI (include/opal.h, include/opal_testing.h).
+Tolerances:
+  - FP64 form: 1e-12 relative position error after 100 steps (1e-13 for
+    a single stage); the two sides differ only in summation order and fused
+    multiply-adds, except where a Bulirsch-Stoer accept/reject decision sits
+    within rounding of the tolerance.
+  - mixed form: 1e-6 relative position error after 100 steps, and |dE/E|
+    within 2x the oracle's (plus 1e-14 absolute slack for round-off).
+  - flagged pair sets: identical, except pairs whose exact minimum sits
+    within 1e-9 relative of the critical distance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import opal_ic as ic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def opal():
+    from paper_2601_19654_gb300.build import build
+    build()
+    oracle.build()
+    from paper_2601_19654_gb300 import opal as o
+    return o
+
+
+def relpos(a, b):
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
+
+
+def drifted(s, dt):
+    """(x0, V0) at the start of a drift and (x1, V1) after it, by the oracle."""
+    V0 = oracle.helio_to_dh(s.M0, s.m, s.v)
+    x0 = s.x.copy()
+    x1, V1 = x0.copy(), V0.copy()
+    for i in range(s.n):
+        st, x1[i], V1[i], _ = oracle.kepler_drift(s.G * s.M0, dt, x0[i], V0[i])
+        assert st == oracle.OK
+    return x0, V0, x1, V1
+
+
+# ---------------------------------------------------------------- drift
+def test_drift_matches_oracle(opal):
+    rng = np.random.default_rng(11)
+    cases = []
+    for k in range(300):
+        if k % 10 == 9:
+            a, e = -rng.uniform(0.5, 3), rng.uniform(1.1, 3)
+            f = rng.uniform(-0.8, 0.8) * np.arccos(-1 / e)
+        else:
+            a, e, f = rng.uniform(0.3, 10), rng.uniform(0, 0.95), rng.uniform(0, 2 * np.pi)
+        x, v = ic.elements_to_state(1.0, a, e, rng.uniform(0, 1), rng.uniform(0, 6), rng.uniform(0, 6), f)
+        cases.append((x, v))
+    x = np.array([c[0] for c in cases])
+    v = np.array([c[1] for c in cases])
+    for dt in (0.0628, -0.3, 7.7):
+        xg, vg, itg = opal.debug_drift(1.0, dt, x, v)
+        for i in range(len(x)):
+            st, xo, vo, ito = oracle.kepler_drift(1.0, dt, x[i], v[i])
+            assert st == oracle.OK and itg[i] > 0
+            assert np.linalg.norm(xg[i] - xo) <= 1e-13 * np.linalg.norm(xo) * max(1.0, abs(dt))
+            assert np.linalg.norm(vg[i] - vo) <= 1e-13 * np.linalg.norm(vo) * max(1.0, abs(dt))
+            # iteration counts may differ where both sides stop at the round-off floor
+            assert abs(int(itg[i]) - ito) <= 3
+
+
+def test_drift_reports_nonconvergence(opal):
+    x, v = ic.elements_to_state(1.0, 1.0, 0.3, 0.0, 0.0, 0.0, 1.0)
+    xg, vg, it = opal.debug_drift(1.0, 0.5, x[None], v[None], max_iter=1)
+    assert it[0] == -1
+    assert np.array_equal(xg[0], x) and np.array_equal(vg[0], v)
+
+
+# ---------------------------------------------------------------- kick
+def _accel_case(name):
+    if name == "tiny":
+        return ic.tiny(0), None
+    if name == "cluster":
+        s = ic.random_cluster(seed=2, n=40, spread=0.01)
+        return s, oracle.hill_rcrit(1.0, 20.0, s.m, s.x)      # many pairs inside rc
+    if name == "planetesimals":
+        return ic.planetesimals_jupiter(0, n=1000), None
+    if name == "ragged":
+        s = ic.random_cluster(seed=5, n=333, spread=0.05)
+        return s, oracle.hill_rcrit(1.0, 10.0, s.m, s.x)
+    raise KeyError(name)
+
+
+def _accel_err(a, ao):
+    """Per-body error relative to the body's |a| (to the largest |a| for a
+    body whose every partner sits inside 0.1 rc, where the kick's share is 0)."""
+    scale = np.maximum(np.linalg.norm(ao, axis=1), 1e-3 * np.linalg.norm(ao, axis=1).max())
+    return np.linalg.norm(a - ao, axis=1) / scale
+
+
+@pytest.mark.parametrize("name", ["tiny", "cluster", "planetesimals", "ragged"])
+@pytest.mark.parametrize("form", [0, 1])
+def test_accel_fp64_matches_oracle(opal, name, form):
+    s, rc = _accel_case(name)
+    if rc is None:
+        rc = oracle.hill_rcrit(1.0, 3.0, s.m, s.x)
+    with opal.Simulation.from_system(s, precision=0, changeover=form) as sim:
+        a = sim.debug_accel(rc)
+    ao = oracle.accel(1.0, s.m, s.x, rc, form=form)
+    err = _accel_err(a, ao)
+    assert err.max() <= 1e-12, err.max()
+
+
+@pytest.mark.parametrize("name", ["tiny", "cluster", "planetesimals", "ragged"])
+def test_accel_mixed_matches_oracle(opal, name):
+    s, rc = _accel_case(name)
+    if rc is None:
+        rc = oracle.hill_rcrit(1.0, 3.0, s.m, s.x)
+    with opal.Simulation.from_system(s, precision=1) as sim:
+        a = sim.debug_accel(rc)
+    ao = oracle.accel(1.0, s.m, s.x, rc)
+    err = _accel_err(a, ao)
+    assert np.median(err) <= 1e-6 and err.max() <= 1e-4, (np.median(err), err.max())
+
+
+# ---------------------------------------------------------------- scan
+def _scan_compare(opal, s, dt, f_hill):
+    x0, V0, x1, V1 = drifted(s, dt)
+    rc = oracle.hill_rcrit(s.M0, f_hill, s.m, x1)
+    with opal.Simulation.from_system(s, dt=dt) as sim:
+        gi, gj, gcand = sim.debug_scan(x0, V0, x1, V1, rc)
+    oi, oj, ocand = oracle.scan(dt, x0, V0, x1, V1, rc)
+    got, ref = set(zip(gi.tolist(), gj.tolist())), set(zip(oi.tolist(), oj.tolist()))
+    for (i, j) in got ^ ref:
+        D = oracle.min_sep2(dt, x0[j] - x0[i], V0[j] - V0[i], x1[j] - x1[i], V1[j] - V1[i])
+        r2 = max(rc[i], rc[j]) ** 2
+        assert abs(D - r2) <= 1e-9 * r2, (i, j, D, r2)
+    return len(ref), gcand
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("f_hill", [0.5, 2.0, 8.0])
+def test_scan_matches_oracle_on_clusters(opal, seed, f_hill):
+    s = ic.random_cluster(seed=seed, n=70, spread=0.02, vspread=0.05)
+    nflag, ncand = _scan_compare(opal, s, 0.05, f_hill)
+    assert ncand >= nflag
+
+
+def test_scan_matches_oracle_on_planetesimal_disk(opal):
+    s = ic.planetesimals_jupiter(0, n=1000)
+    nflag, _ = _scan_compare(opal, s, s.dt, 3.0)
+    assert nflag > 0
+
+
+def test_scan_backwards_in_time(opal):
+    s = ic.random_cluster(seed=9, n=50, spread=0.02, vspread=0.05)
+    _scan_compare(opal, s, -0.05, 2.0)
+
+
+# ---------------------------------------------------------------- BS
+def _bs_compare(opal, X0, V0, m, R, rc, dt):
+    n = len(m)
+    p = oracle.make_params(dt=dt)
+    mo, Ro, rco = m.copy(), R.copy(), rc.copy()
+    alive = np.ones(n, np.int32)
+    Xo, Vo = X0.copy(), V0.copy()
+    st, El, nmg, sub = oracle.bs_group(p, np.arange(n, dtype=np.int32), mo, Ro, rco, alive, Xo, Vo)
+    assert st == oracle.OK
+    sys_bodies = ic.System("g", m.copy(), X0.copy(), V0.copy(), R.copy(), dt=dt, nsteps=1)
+    with opal.Simulation.from_system(sys_bodies, precision=0) as sim:
+        gst, out = sim.debug_bs_group(X0, V0, rc, m, R)
+    assert gst == opal.OK
+    assert out["alive"].tolist() == alive.tolist()
+    assert np.array_equal(out["m"], mo)
+    live = alive > 0
+    assert relpos(out["x"][live], Xo[live]) <= 1e-12
+    assert np.abs(out["V"][live] - Vo[live]).max() <= 1e-12 * np.abs(Vo[live]).max()
+    assert out["substeps"] == sub
+    if nmg:
+        assert abs(out["E_lost"] - El) <= 1e-12 * abs(El)
+    return nmg, sub
+
+
+def test_bs_single_body_matches_oracle(opal):
+    x, v = ic.elements_to_state(1.0, 1.2, 0.3, 0.1, 0.2, 0.3, 2.0)
+    _bs_compare(opal, x[None], v[None], np.array([1e-9]), np.array([1e-9]), np.array([1e-9]), 0.3)
+
+
+def test_bs_close_encounter_matches_oracle(opal):
+    x1, v1 = ic.elements_to_state(1.0, 1.0, 0.02, 0.0, 0.0, 0.0, 0.0)
+    X0 = np.array([x1, x1 + [0.0, 0.004, 0.0002], x1 + [0.003, -0.002, 0.0]])
+    V0 = np.array([v1, v1 + [0.01, -0.02, 0.0], v1 + [-0.01, 0.0, 0.001]])
+    m = np.array([3e-6, 2e-6, 1e-6])
+    nmg, sub = _bs_compare(opal, X0, V0, m, np.full(3, 1e-8), np.array([0.02, 0.01, 0.01]), 0.0628)
+    assert sub >= 1
+
+
+def test_bs_merger_matches_oracle(opal):
+    x1, v1 = ic.elements_to_state(1.0, 1.0, 0.02, 0.0, 0.0, 0.0, 0.0)
+    X0 = np.array([x1, x1 + [0.0, 0.004, 0.0002]])
+    V0 = np.array([v1, v1 + [0.0, -0.08, -0.004]])
+    m = np.array([3e-6, 2e-6])
+    nmg, sub = _bs_compare(opal, X0, V0, m, np.array([3e-4, 2e-4]), np.array([1.0, 1.0]), 0.0628)
+    assert nmg == 1
+
+
+# ---------------------------------------------------------------- whole steps
+def _run_pair(opal, s, nsteps, precision, block=10, **kw):
+    sim = opal.Simulation.from_system(s, precision=precision, **kw)
+    osim = oracle.Sim.from_system(s, **{k: v for k, v in kw.items() if k in ("dt", "changeover", "bs_max_substeps")})
+    E0g, E0o = sim.energy()[0], osim.energy()[0]
+    done = 0
+    while done < nsteps:
+        k = min(block, nsteps - done)
+        sim.step(k)
+        assert osim.step(k) == oracle.OK
+        done += k
+    st = sim.state()
+    dEg = abs(sim.energy()[0] - E0g) / abs(E0g)
+    dEo = abs(osim.energy()[0] - E0o) / abs(E0o)
+    out = dict(sim=sim, osim=osim, st=st, dEg=dEg, dEo=dEo)
+    return out
+
+
+def _alive_parity(out):
+    st, osim = out["st"], out["osim"]
+    alive = np.nonzero(osim.alive)[0]
+    assert st["ids"].tolist() == alive.tolist()
+    return relpos(st["x"], osim.x[alive])
+
+
+@pytest.mark.parametrize("name,nsteps", [("tiny", 100), ("planetesimals", 100)])
+def test_step_fp64_matches_oracle(opal, name, nsteps):
+    s = ic.tiny(0) if name == "tiny" else ic.planetesimals_jupiter(0, n=1000)
+    out = _run_pair(opal, s, nsteps, 0)
+    err = _alive_parity(out)
+    assert err <= 1e-12, err
+    E, L, P, El = out["sim"].energy()
+    Eo, Lo, Po, Elo = out["osim"].energy()
+    assert abs(E - Eo) <= 1e-13 * abs(Eo)
+    assert np.abs(L - Lo).max() <= 1e-13 * np.linalg.norm(Lo)
+
+
+@pytest.mark.parametrize("name,nsteps", [("tiny", 100), ("planetesimals", 100)])
+def test_step_mixed_matches_oracle(opal, name, nsteps):
+    s = ic.tiny(0) if name == "tiny" else ic.planetesimals_jupiter(0, n=1000)
+    out = _run_pair(opal, s, nsteps, 1)
+    err = _alive_parity(out)
+    assert err <= 1e-6, err
+    assert out["dEg"] <= 2 * out["dEo"] + 1e-14, (out["dEg"], out["dEo"])
+
+
+def test_step_with_mergers_matches_oracle(opal):
+    s = ic.random_cluster(seed=11, n=24, spread=0.02, vspread=0.01, mass=3e-7)
+    s.R = s.R * 30.0
+    out = _run_pair(opal, s, 60, 0, block=1)
+    st, osim = out["st"], out["osim"]
+    assert osim.alive.sum() < s.n                         # mergers happened
+    err = _alive_parity(out)
+    assert err <= 1e-9, err
+    assert np.allclose(st["m"], osim.m[osim.alive > 0], rtol=1e-15, atol=0)
+    El, Elo = out["sim"].energy()[3], out["osim"].energy()[3]
+    assert abs(El - Elo) <= 1e-9 * abs(Elo)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_equal_mass_disk_two_steps(opal, precision):
+    """The 16384-body workload in the benchmark's launch configuration."""
+    s = ic.equal_mass_disk(0)
+    out = _run_pair(opal, s, 2, precision, block=1)
+    err = _alive_parity(out)
+    assert err <= (1e-12 if precision == 0 else 1e-6), err
+    assert out["sim"].stats()["n_pairs"] == out["osim"].stats.n_pairs
+
+
+def test_backward_steps_retrace_forward_steps(opal):
+    s = ic.tiny(0)
+    with opal.Simulation.from_system(s, precision=0) as sim:
+        x0 = sim.state()["x"]
+        sim.step(100)
+        st = sim.state()
+    with opal.Simulation(st["m"], st["x"], st["v"], st["R"], precision=0, dt=-s.dt) as back:
+        back.step(100)
+        assert relpos(back.state()["x"], x0) <= 1e-12
+
+
+def test_ensemble_matches_each_system(opal):
+    systems = [ic.tiny(seed=3, n=70), ic.tiny(seed=4, n=130), ic.planetesimals_jupiter(1, n=200)]
+    for s in systems:
+        s.dt = systems[0].dt
+    with opal.Simulation.ensemble(systems, precision=0) as sim:
+        sim.step(20)
+        for k, s in enumerate(systems):
+            osim = oracle.Sim.from_system(s, dt=systems[0].dt)
+            assert osim.step(20) == oracle.OK
+            st = sim.state(k)
+            assert relpos(st["x"], osim.x[osim.alive > 0]) <= 1e-12
+
+
+def test_get_state_roundtrip_continues_the_run(opal):
+    s = ic.tiny(1)
+    with opal.Simulation.from_system(s, precision=0) as a:
+        a.step(30)
+        st = a.state()
+        with opal.Simulation(st["m"], st["x"], st["v"], st["R"], precision=0, dt=s.dt) as b:
+            a.step(30)
+            b.step(30)
+            assert relpos(b.state()["x"], a.state()["x"]) <= 1e-13
+
+
+def test_runs_are_deterministic(opal):
+    s = ic.planetesimals_jupiter(2, n=600)
+    out = []
+    for _ in range(2):
+        with opal.Simulation.from_system(s, precision=1) as sim:
+            sim.step(40)
+            out.append(sim.state()["x"])
+    assert np.array_equal(out[0], out[1])
+
+
+def test_profiled_steps_equal_graph_steps(opal):
+    s = ic.planetesimals_jupiter(3, n=500)
+    with opal.Simulation.from_system(s, precision=0) as a, opal.Simulation.from_system(s, precision=0) as b:
+        a.step(5)
+        prof = b.profile(5)
+        assert np.array_equal(a.state()["x"], b.state()["x"])
+        assert "kick" in prof and prof["kick"] > 0
+
+
+def test_energy_matches_oracle_before_any_step(opal):
+    s = ic.planetesimals_jupiter(0, n=1000)
+    with opal.Simulation.from_system(s) as sim:
+        E, L, P, El = sim.energy()
+    Eo, Lo, Po = oracle.energy(1.0, 1.0, s.m, s.x, oracle.helio_to_dh(1.0, s.m, s.v))
+    assert abs(E - Eo) <= 1e-14 * abs(Eo)
+    assert np.abs(L - Lo).max() <= 1e-14 * np.linalg.norm(Lo)
+    assert np.abs(P - Po).max() <= 1e-14 * np.abs(s.m[:, None] * s.v).sum()
+    assert El == 0.0
+
+
+# ---------------------------------------------------------------- failures
+def test_kepler_failure_undoes_the_step(opal):
+    s = ic.tiny(0)
+    with opal.Simulation.from_system(s, precision=0, kepler_max_iter=1) as sim:
+        before = sim.state()
+        st = sim.try_step(3)
+        assert st == opal.EKEPLER
+        after = sim.state()
+        assert sim.steps_done == 0
+        for k in ("x", "v", "m", "R"):
+            assert np.array_equal(before[k], after[k]), k
+        assert "Kepler" in opal.lib().opal_last_error(sim.ptr).decode()
+
+
+def test_bs_failure_undoes_the_step(opal):
+    s = ic.random_cluster(seed=3, n=12, spread=0.004, vspread=0.01, mass=3e-6)
+    with opal.Simulation.from_system(s, precision=0, bs_max_substeps=1, dt=0.3) as sim:
+        before = sim.state()
+        assert sim.try_step(1) == opal.EBS
+        after = sim.state()
+        for k in ("x", "v", "m", "R", "ids"):
+            assert np.array_equal(before[k], after[k]), k
+
+
+def test_encounter_overflow_is_reported_and_a_larger_list_succeeds(opal):
+    s = ic.random_cluster(seed=4, n=40, spread=0.01, vspread=0.02, mass=3e-6)
+    with opal.Simulation.from_system(s, precision=0, encounter_capacity=1) as sim:
+        before = sim.state()
+        assert sim.try_step(1) == opal.EOVERFLOW
+        assert np.array_equal(before["x"], sim.state()["x"])
+    with opal.Simulation.from_system(s, precision=0, encounter_capacity=4096) as sim:
+        sim.step(1)
+        assert sim.stats()["n_pairs"] > 1
