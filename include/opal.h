@@ -144,6 +144,9 @@ const char* opal_kick_config(const opal_sim* sim);
 opal_status opal_time_kick(opal_sim* sim, int32_t enable);
 double opal_last_kick_ms(const opal_sim* sim);
 
+/* Number of kernel launches in one step (kernel nodes of the step graph). */
+int32_t opal_graph_kernels(const opal_sim* sim);
+
 /* Reason for the last error on sim (or on the calling thread when sim is NULL). */
 const char* opal_last_error(const opal_sim* sim);
 

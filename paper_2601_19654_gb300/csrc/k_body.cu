@@ -62,27 +62,68 @@ __device__ void segment_sums(const Dev& d, int64_t first_body, double vx, double
     }
 }
 
+// box of the path midpoints of the system's live bodies (block-reduced,
+// then one atomic per block and bound)
+__device__ void note_box(const Dev& d, int s, int64_t b) {
+    __shared__ int red[6][kBodyThreads / 32];
+    float v[6];
+    if (d.alive[b]) {
+        float4 c = d.cen[b];
+        v[0] = v[3] = c.x;
+        v[1] = v[4] = c.y;
+        v[2] = v[5] = c.z;
+    } else {
+        v[0] = v[1] = v[2] = 3.0e38f;
+        v[3] = v[4] = v[5] = -3.0e38f;
+    }
+    for (int k = 0; k < 6; k++) {
+        float x = v[k];
+        for (int o = 16; o >= 1; o >>= 1) {
+            float y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = k < 3 ? fminf(x, y) : fmaxf(x, y);
+        }
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = ford(x);
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        int x = red[k][0];
+        for (int w = 1; w < kBodyThreads / 32; w++) x = k < 3 ? min(x, red[k][w]) : max(x, red[k][w]);
+        if (k < 3) atomicMin(&d.sbox[3 * s + k], x);
+        else atomicMax(&d.sbox[3 * d.nsys + 3 * s + k - 3], x);
+    }
+}
+
 __device__ __forceinline__ void note_rcmax(const Dev& d, int s, double rc) {
     // rc >= 0: the order of non-negative floats matches the order of their bits
     atomicMax(reinterpret_cast<int*>(d.rcmax) + s, __float_as_int(__double2float_ru(rc)));
 }
 
 // scan inputs of a live body: start-of-drift hi/lo, velocities, and the
-// radius s that bounds how far the body's Hermite path over the step strays
-// from its end point: |x0 - x1| + (4/27)|dt|(|V0| + |V1|), plus rc and margins.
+// midpoint c = (x0 + x1)/2 + dt (V0 - V1)/8 of its Hermite path over the
+// step with the radius s around c that holds the whole path:
+// |x1 - x0|/2 + (sqrt 3/18)|x0 - x1 + dt V1| + (4/27 + 1/8)|dt||V0 - V1|,
+// plus rc, and margins far above FP32 rounding.
 __device__ __forceinline__ void scan_floats(const Dev& d, int64_t b, double ox, double oy, double oz, double ovx,
                                             double ovy, double ovz, double x, double y, double z, double vx,
                                             double vy, double vz, double rc) {
-    double wx = ox - x, wy = oy - y, wz = oz - z;
+    const double T = d.p.dt;
+    double wx = x - ox, wy = y - oy, wz = z - oz;
+    double ex = -wx + T * vx, ey = -wy + T * vy, ez = -wz + T * vz;
+    double dvx = ovx - vx, dvy = ovy - vy, dvz = ovz - vz;
+    double cx = 0.5 * (ox + x) + 0.125 * T * dvx, cy = 0.5 * (oy + y) + 0.125 * T * dvy,
+           cz = 0.5 * (oz + z) + 0.125 * T * dvz;
+    double rho = 0.5 * sqrt(dot3(wx, wy, wz, wx, wy, wz)) + 0.09622504486493763 * sqrt(dot3(ex, ey, ez, ex, ey, ez)) +
+                 (4.0 / 27.0 + 0.125) * fabs(T) * sqrt(dot3(dvx, dvy, dvz, dvx, dvy, dvz));
+    double sr = (rho + rc) * (1.0 + 1e-5) + 1e-6 * sqrt(dot3(cx, cy, cz, cx, cy, cz));
+    float srf = __double2float_ru(sr);
+    d.cen[b] = make_float4((float)cx, (float)cy, (float)cz, srf);
     double v0n = sqrt(dot3(ovx, ovy, ovz, ovx, ovy, ovz)), v1n = sqrt(dot3(vx, vy, vz, vx, vy, vz));
-    double rho = sqrt(dot3(wx, wy, wz, wx, wy, wz)) + (4.0 / 27.0) * fabs(d.p.dt) * (v0n + v1n);
-    double r1 = sqrt(dot3(x, y, z, x, y, z));
-    double sr = (rho + rc) * (1.0 + 1e-5) + 1e-6 * r1;
     float hx, lx, hy, ly, hz, lz;
     split_hl(ox, hx, lx);
     split_hl(oy, hy, ly);
     split_hl(oz, hz, lz);
-    d.sc0[b] = make_float4(hx, hy, hz, __double2float_ru(sr));
+    d.sc0[b] = make_float4(hx, hy, hz, srf);
     d.sc1[b] = make_float4(lx, ly, lz, 0.0f);
     d.sv0[b] = make_float4((float)ovx, (float)ovy, (float)ovz, __double2float_ru(v0n));
     d.sv1[b] = make_float4((float)vx, (float)vy, (float)vz, __double2float_ru(v1n));
@@ -184,13 +225,14 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
     } else {
         park_floats(d, b);
     }
-    // largest iteration count of the block
+    // largest iteration count of the block, and the box of the midpoints
     __shared__ int itmax;
     if (threadIdx.x == 0) itmax = 0;
     __syncthreads();
     atomicMax(&itmax, iters);
     __syncthreads();
     if (threadIdx.x == 0 && itmax > 0) atomicMax(&d.ctl->kepler_max, itmax);
+    note_box(d, s, b);
 }
 
 // ---------------------------------------------------------------------------
@@ -320,17 +362,18 @@ __global__ void k_debug_drift(int n, double mu, double dt, int max_iter, double*
     iters[b] = it;
 }
 
-__global__ void k_debug_scan_prep(Dev d) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= d.ntot) return;
-    if (!d.alive[b]) {
+__global__ void __launch_bounds__(kBodyThreads) k_debug_scan_prep(Dev d) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
+    if (d.alive[b]) {
+        kick_floats(d, b, d.x[b], d.y[b], d.z[b], d.m[b], d.rc[b]);
+        note_rcmax(d, s, d.rc[b]);
+        scan_floats(d, b, d.x0[b], d.y0[b], d.z0[b], d.vx0[b], d.vy0[b], d.vz0[b], d.x[b], d.y[b], d.z[b],
+                    d.vx[b], d.vy[b], d.vz[b], d.rc[b]);
+    } else {
         park_floats(d, b);
-        return;
     }
-    kick_floats(d, b, d.x[b], d.y[b], d.z[b], d.m[b], d.rc[b]);
-    note_rcmax(d, d.body_sys[b], d.rc[b]);
-    scan_floats(d, b, d.x0[b], d.y0[b], d.z0[b], d.vx0[b], d.vy0[b], d.vz0[b], d.x[b], d.y[b], d.z[b], d.vx[b],
-                d.vy[b], d.vz[b], d.rc[b]);
+    note_box(d, s, b);   // every thread of the block, from this one call site
 }
 
 // ---------------------------------------------------------------------------
@@ -346,14 +389,19 @@ void launch_prime(const Dev& d, cudaStream_t s) {
 }
 void launch_open(const Dev& d, cudaStream_t s) {
     k_open<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d);
+    prof_mark("open: kick+jump+drift");
 }
 void launch_close(const Dev& d, cudaStream_t s) {
     k_close<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d, 0);
+    prof_mark("close: jump+kick");
 }
 void launch_first_accel_finish(const Dev& d, cudaStream_t s) {
     k_close<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d, 1);
 }
-void launch_finish(const Dev& d, cudaStream_t s) { k_finish<<<152, 256, 0, s>>>(d); }
+void launch_finish(const Dev& d, cudaStream_t s) {
+    k_finish<<<152, 256, 0, s>>>(d);
+    prof_mark("finish");
+}
 void launch_export(const Dev& d, double* v_helio, cudaStream_t s) { k_export<<<d.nsys, 256, 0, s>>>(d, v_helio); }
 
 }  // namespace opal

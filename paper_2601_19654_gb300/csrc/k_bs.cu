@@ -13,119 +13,52 @@
 // k <= 2 -> double, at k >= 6 -> halve; not accepted by k = 7 -> retry at
 // half length; the substep count is capped.
 //
-// One block of four warps per group.  Warp w runs the two midpoint
-// sequences n = 2(w+1) and n = 16 - 2w (20 derivative evaluations each, so
-// the warps finish together) with one member per lane; then one thread per
-// (member, position-or-velocity) extrapolates its three components.  Every
-// row the sequential method would compute is computed (the extra rows are
-// unused), so the accepted values are those of the sequential method.
+// Layout: one thread per (sequence k, member b); all eight midpoint
+// sequences advance in lockstep, one derivative evaluation per round.
+// Sequence k finishes at round n_k = 2k + 2, its thread extrapolates row k
+// for its member at once (row k - 1 is two rounds old), and the group stops
+// at the first row that passes the test, as the sequential method does.  On
+// this chip a warp instruction costs the FP64 pipe the same whatever the
+// number of active lanes, so the rounds of a group cost what one sequence
+// would, and groups of up to 4 members fit one warp.  Four such warps (on
+// the four schedulers of an SM) try the step sizes H, H/2, H/4, H/8 at once:
+// the first one accepted in that order is the one the sequential method
+// would reach after its rejections, so only the cost of rejections changes.
 #include "opal_internal.cuh"
 
 namespace opal {
 
-constexpr int kM = kBsMaxMembers;
-constexpr int kBsThreads = 32 * kBsWarps;
-
-struct BsShared {
-    double y[6][kM];               // current state, component-major: X, Y, Z, VX, VY, VZ
-    double T0[kBsRows][6][kM];     // midpoint results; overwritten by the diagonal T[k][k]
-    double pos[kBsWarps][3][kM];   // positions of the evaluation in progress, per warp
-    double m[kM], R[kM], rc[kM];
-    int alive[kM], gid[kM];
-    double errk[kBsWarps][kBsRows];
-    int kacc, collide;
-    double El;
-    int nmerge;
+// Neville coefficients 1 / ((n_k / n_{k-j})^2 - 1) with n_k = 2(k+1): exact
+// rationals (k-j+1)^2 / ((k+1)^2 - (k-j+1)^2), rounded once.
+__constant__ double kNeville[kBsRows][kBsRows] = {
+    {0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 1.0 / 3.0, 0, 0, 0, 0, 0, 0},
+    {0, 4.0 / 5.0, 1.0 / 8.0, 0, 0, 0, 0, 0},
+    {0, 9.0 / 7.0, 4.0 / 12.0, 1.0 / 15.0, 0, 0, 0, 0},
+    {0, 16.0 / 9.0, 9.0 / 16.0, 4.0 / 21.0, 1.0 / 24.0, 0, 0, 0},
+    {0, 25.0 / 11.0, 16.0 / 20.0, 9.0 / 27.0, 4.0 / 32.0, 1.0 / 35.0, 0, 0},
+    {0, 36.0 / 13.0, 25.0 / 24.0, 16.0 / 33.0, 9.0 / 40.0, 4.0 / 45.0, 1.0 / 48.0, 0},
+    {0, 49.0 / 15.0, 36.0 / 28.0, 25.0 / 39.0, 16.0 / 48.0, 9.0 / 55.0, 4.0 / 60.0, 1.0 / 63.0},
 };
 
-// derivative of the members a lane owns (q = 0, 1 -> member lane + 32 q)
-__device__ __forceinline__ void bs_deriv(BsShared& S, const Params& p, int w, int nm, const double (&z)[2][6],
-                                         double (&f)[2][6]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-        int b = lane + 32 * q;
-        if (b < nm) {
-            S.pos[w][0][b] = z[q][0];
-            S.pos[w][1][b] = z[q][1];
-            S.pos[w][2][b] = z[q][2];
-        }
-    }
-    __syncwarp();
-    const double G = p.G, M0 = p.M0;
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-        int b = lane + 32 * q;
-        if (b >= nm) continue;
-        if (!S.alive[b]) {
-#pragma unroll
-            for (int c = 0; c < 6; c++) f[q][c] = 0.0;
-            continue;
-        }
-        const double xb = z[q][0], yb = z[q][1], zb = z[q][2];
-        double r2 = xb * xb + yb * yb + zb * zb, r = sqrt(r2);
-        double s = -G * M0 / (r2 * r);
-        double ax = s * xb, ay = s * yb, az = s * zb;
-        for (int o = 0; o < nm; o++) {
-            if (o == b || !S.alive[o]) continue;
-            double dx = S.pos[w][0][o] - xb, dy = S.pos[w][1][o] - yb, dz = S.pos[w][2][o] - zb;
-            double dr2 = dx * dx + dy * dy + dz * dz, dr = sqrt(dr2);
-            double rcbo = S.rc[b] > S.rc[o] ? S.rc[b] : S.rc[o];
-            double wgt = 1.0 - changeover(dr, rcbo, p.changeover);
-            if (wgt == 0.0) continue;
-            double t = G * S.m[o] * wgt / (dr2 * dr);
-            ax += t * dx;
-            ay += t * dy;
-            az += t * dz;
-        }
-        f[q][0] = z[q][3];
-        f[q][1] = z[q][4];
-        f[q][2] = z[q][5];
-        f[q][3] = ax;
-        f[q][4] = ay;
-        f[q][5] = az;
-    }
-    __syncwarp();
-}
+// NT threads hold A attempts (step sizes H, H/2, ..., H/2^(A-1)) of one group
+// of up to M members, one thread per (attempt, sequence, member).
+template <int NT, int A>
+struct BsSh {
+    static constexpr int M = NT / (A * kBsRows);
+    double y[6][M];                     // current state, component-major: X, Y, Z, VX, VY, VZ
+    double pos[A][kBsRows][3][M];       // positions of each sequence's evaluation in progress
+    double row[A][kBsRows][6][M];       // the last extrapolated row of each member
+    double err[A][kBsRows][M];          // squared error ratio of each member, per finished row
+    double m[M], R[M], rc[M];
+    int alive[M], gid[M];
+    int kacc[A];                        // accepted row of each attempt, -1 while none
+    int decision, collide, nmerge;
+    double El;
+};
 
-// modified midpoint with n steps over H from S.y, result into S.T0[row]
-__device__ void bs_mmid(BsShared& S, const Params& p, int w, int nm, double H, int n, int row) {
-    const int lane = threadIdx.x & 31;
-    double za[2][6], zb[2][6], f[2][6];
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-        int b = lane + 32 * q;
-#pragma unroll
-        for (int c = 0; c < 6; c++) za[q][c] = (b < nm) ? S.y[c][b] : 0.0;
-    }
-    const double h = H / n;
-    bs_deriv(S, p, w, nm, za, f);
-#pragma unroll
-    for (int q = 0; q < 2; q++)
-#pragma unroll
-        for (int c = 0; c < 6; c++) zb[q][c] = za[q][c] + h * f[q][c];
-    for (int st = 1; st < n; st++) {
-        bs_deriv(S, p, w, nm, zb, f);
-#pragma unroll
-        for (int q = 0; q < 2; q++)
-#pragma unroll
-            for (int c = 0; c < 6; c++) {
-                double znew = za[q][c] + 2.0 * h * f[q][c];
-                za[q][c] = zb[q][c];
-                zb[q][c] = znew;
-            }
-    }
-    bs_deriv(S, p, w, nm, zb, f);
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-        int b = lane + 32 * q;
-        if (b < nm)
-#pragma unroll
-            for (int c = 0; c < 6; c++) S.T0[row][c][b] = 0.5 * (zb[q][c] + za[q][c] + h * f[q][c]);
-    }
-}
-
-__device__ void bs_merge(BsShared& S, const Params& p, int b, int q) {
+template <int NT, int A>
+__device__ void bs_merge(BsSh<NT, A>& S, const Params& p, int b, int q) {
     const double G = p.G, M0 = p.M0;
     double mb = S.m[b], mq = S.m[q], M = mb + mq;
     double d[3] = {S.y[0][q] - S.y[0][b], S.y[1][q] - S.y[1][b], S.y[2][q] - S.y[2][b]};
@@ -160,19 +93,55 @@ __device__ void bs_merge(BsShared& S, const Params& p, int b, int q) {
     S.nmerge++;
 }
 
-__global__ void __launch_bounds__(kBsThreads) k_bs(Dev d) {
-    __shared__ BsShared S;
+// acceleration of member b of sequence k at its position (x, y, z)
+template <int NT, int A>
+__device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, int nm, int a, int k, int b,
+                                         double xb, double yb, double zb, double& ax, double& ay, double& az) {
+    const double G = p.G, M0 = p.M0;
+    double r2 = xb * xb + yb * yb + zb * zb, ri = rsqrt(r2);
+    double s = -G * M0 * (ri * ri * ri);
+    ax = s * xb;
+    ay = s * yb;
+    az = s * zb;
+    for (int o = 0; o < nm; o++) {
+        if (o == b || !S.alive[o]) continue;
+        double dx = S.pos[a][k][0][o] - xb, dy = S.pos[a][k][1][o] - yb, dz = S.pos[a][k][2][o] - zb;
+        double dr2 = dx * dx + dy * dy + dz * dz;
+        double rcbo = S.rc[b] > S.rc[o] ? S.rc[b] : S.rc[o];
+        if (dr2 >= rcbo * rcbo) continue;   // 1 - K = 0 at or beyond rc
+        double dri = rsqrt(dr2), dr = dr2 * dri;
+        double wgt = 1.0 - changeover(dr, rcbo, p.changeover);
+        if (wgt == 0.0) continue;
+        double t = G * S.m[o] * wgt * (dri * dri * dri);
+        ax += t * dx;
+        ay += t * dy;
+        az += t * dz;
+    }
+}
+
+template <int NT, int A>
+__global__ void __launch_bounds__(NT, 1) k_bs(Dev d, int small) {
+    using Sh = BsSh<NT, A>;
+    constexpr int M = Sh::M;
+    constexpr int TA = NT / A;            // threads per attempt
+    __shared__ Sh S;
     if (d.ctl->status) return;
     const Params p = d.p;
-    const int ng = d.ctl->ngroups;
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int ng = small ? d.ctl->ngroups : d.ctl->nlarge;
+    const int tid = threadIdx.x;
+    const int a = tid / TA, lt = tid % TA;
     const int cap = p.bs_max_substeps;
-    for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+    const double tol2 = p.bs_tol * p.bs_tol;
+    for (int gi = blockIdx.x; gi < ng; gi += gridDim.x) {
+        const int g = small ? gi : d.glarge[gi];
         const int mb = d.goff[g], nm = d.goff[g + 1] - mb;
-        if (nm > kM) {
+        if (small && nm > M) continue;      // handled by the large-group kernel
+        if (nm > M) {
             if (tid == 0) set_status(d.ctl, kEoverflow, 1000000 + g);
             return;
         }
+        const int k = lt / nm, b = lt % nm;       // sequence and member of this thread
+        const bool act = k < kBsRows;
         if (tid < nm) {
             int gb = d.members[mb + tid];
             S.gid[tid] = gb;
@@ -195,116 +164,165 @@ __global__ void __launch_bounds__(kBsThreads) k_bs(Dev d) {
             S.nmerge = 0;
         }
         __syncthreads();
-        const double dt = p.dt, tol = p.bs_tol;
+        const double dt = p.dt;
+        const int n = 2 * (k + 1);
         double t = 0.0, H = dt;
-        int nsub = 0, failed = 0;
-        for (;;) {
+        int nsub = 0, failed = 0, finished = 0;
+        while (!finished && !failed) {
+            // attempt 0 takes min(H, what remains); attempt j takes half of attempt j-1,
+            // exactly the step sizes the sequential method would try after rejections
             double rem = dt - t;
-            int last = 0;
+            int last0 = 0;
             if (fabs(H) >= fabs(rem)) {
                 H = rem;
-                last = 1;
+                last0 = 1;
             }
-            // all eight midpoint sequences, two per warp
-            bs_mmid(S, p, w, nm, H, 2 * (w + 1), w);
-            bs_mmid(S, p, w, nm, H, 2 * (kBsRows - w), kBsRows - 1 - w);
+            const double Ha = ldexp(H, -a);
+            const double h = Ha / n;
+            double za[6], zb[6], diag[6];
+            if (act)
+                for (int c = 0; c < 6; c++) za[c] = zb[c] = S.y[c][b];
+            if (lt == 0) S.kacc[a] = -1;
+            if (tid == 0) S.decision = -1;
             __syncthreads();
-            // extrapolation: thread (member b, part pp) owns components 3pp..3pp+2
-            double ek[kBsRows];
-#pragma unroll
-            for (int k = 0; k < kBsRows; k++) ek[k] = 0.0;
-            if (tid < 2 * nm) {
-                const int b = tid >> 1, pp = tid & 1;
-                double dsq[kBsRows], nrm[kBsRows];
-#pragma unroll
-                for (int k = 0; k < kBsRows; k++) dsq[k] = nrm[k] = 0.0;
-                for (int c = 3 * pp; c < 3 * pp + 3; c++) {
-                    double prev[kBsRows], cur[kBsRows];
-#pragma unroll
-                    for (int k = 0; k < kBsRows; k++) {
-                        cur[0] = S.T0[k][c][b];
-#pragma unroll
-                        for (int j = 1; j <= k; j++) {
-                            double ratio = (double)(k + 1) / (double)(k - j + 1);
-                            double den = ratio * ratio - 1.0;
-                            cur[j] = cur[j - 1] + (cur[j - 1] - prev[j - 1]) / den;
-                        }
-                        if (k >= 1) {
-                            double df = cur[k] - cur[k - 1];
-                            dsq[k] += df * df;
-                        }
-                        nrm[k] += cur[k] * cur[k];
-                        S.T0[k][c][b] = cur[k];
-#pragma unroll
-                        for (int j = 0; j <= k; j++) prev[j] = cur[j];
-                    }
+            for (int r = 0; r <= 2 * kBsRows; r++) {
+                const bool live = act && r <= n;
+                if (live) {
+                    const double* zp = (r == 0) ? za : zb;
+                    S.pos[a][k][0][b] = zp[0];
+                    S.pos[a][k][1][b] = zp[1];
+                    S.pos[a][k][2][b] = zp[2];
                 }
-                if (S.alive[b]) {
-#pragma unroll
-                    for (int k = 1; k < kBsRows; k++) {
-                        double sc = sqrt(nrm[k]);
-                        if (sc < 1e-300) sc = 1e-300;
-                        double e = sqrt(dsq[k]) / sc;
-                        ek[k] = (e <= 1.7e308) ? e : HUGE_VAL;   // NaN counts as not converged
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 1; k < kBsRows; k++) {
-                double v = ek[k];
-                for (int o = 16; o >= 1; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-                if (lane == 0) S.errk[w][k] = v;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int kacc = -1;
-                for (int k = 1; k < kBsRows && kacc < 0; k++) {
-                    double e = S.errk[0][k];
-                    for (int ww = 1; ww < kBsWarps; ww++) e = fmax(e, S.errk[ww][k]);
-                    if (e <= tol) kacc = k;
-                }
-                S.kacc = kacc;
-            }
-            __syncthreads();
-            const int kacc = S.kacc;
-            nsub++;
-            if (kacc >= 0) {
-                for (int e = tid; e < 6 * nm; e += kBsThreads) {
-                    int c = e / nm, b = e % nm;
-                    S.y[c][b] = S.T0[kacc][c][b];
-                }
-                t = last ? dt : t + H;
-                if (tid == 0) S.collide = 0;
                 __syncthreads();
-                // any pair in contact?  (exact sequential resolution only if so)
-                for (int e = tid; e < nm * nm; e += kBsThreads) {
-                    int b = e / nm, q = e % nm;
-                    if (q > b && S.alive[b] && S.alive[q]) {
-                        double dx = S.y[0][q] - S.y[0][b], dy = S.y[1][q] - S.y[1][b], dz = S.y[2][q] - S.y[2][b];
-                        if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[b] + S.R[q]) S.collide = 1;
+                if (live) {
+                    double f[6];
+                    const double* zp = (r == 0) ? za : zb;
+                    if (S.alive[b]) {
+                        f[0] = zp[3];
+                        f[1] = zp[4];
+                        f[2] = zp[5];
+                        bs_accel<NT, A>(S, p, nm, a, k, b, zp[0], zp[1], zp[2], f[3], f[4], f[5]);
+                    } else {
+                        for (int c = 0; c < 6; c++) f[c] = 0.0;
+                    }
+                    if (r == 0) {
+                        for (int c = 0; c < 6; c++) zb[c] = za[c] + h * f[c];
+                    } else if (r < n) {
+                        for (int c = 0; c < 6; c++) {
+                            double znew = za[c] + 2.0 * h * f[c];
+                            za[c] = zb[c];
+                            zb[c] = znew;
+                        }
+                    } else {
+                        // sequence k done: raw value, then row k of the tableau
+                        double dsq_x = 0.0, dsq_v = 0.0, nx = 0.0, nv = 0.0;
+                        for (int c = 0; c < 6; c++) {
+                            double cur = 0.5 * (zb[c] + za[c] + h * f[c]);
+                            double prev_col = 0.0;
+                            for (int j = 1; j <= k; j++) {
+                                double up = S.row[a][j - 1][c][b];
+                                S.row[a][j - 1][c][b] = cur;
+                                prev_col = cur;
+                                cur = cur + (cur - up) * kNeville[k][j];
+                            }
+                            S.row[a][k][c][b] = cur;
+                            diag[c] = cur;
+                            if (k >= 1) {
+                                double df = cur - prev_col;
+                                if (c < 3) {
+                                    dsq_x += df * df;
+                                    nx += cur * cur;
+                                } else {
+                                    dsq_v += df * df;
+                                    nv += cur * cur;
+                                }
+                            }
+                        }
+                        // squared error ratio: (|dX|/|X|)^2 vs (|dV|/|V|)^2, larger one
+                        double e2 = 0.0;
+                        if (k >= 1 && S.alive[b]) {
+                            double ex = dsq_x / fmax(nx, 2.3e-308), ev = dsq_v / fmax(nv, 2.3e-308);
+                            e2 = ex > ev ? ex : ev;
+                            if (!(e2 <= 1.7e308)) e2 = HUGE_VAL;   // NaN counts as not converged
+                        }
+                        S.err[a][k][b] = e2;
                     }
                 }
                 __syncthreads();
-                if (S.collide && tid == 0) {
-                    for (int b = 0; b < nm; b++)
-                        for (int q = b + 1; q < nm && S.alive[b]; q++) {
-                            if (!S.alive[q]) continue;
-                            double dx = S.y[0][q] - S.y[0][b], dy = S.y[1][q] - S.y[1][b],
-                                   dz = S.y[2][q] - S.y[2][b];
-                            if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[b] + S.R[q]) bs_merge(S, p, b, q);
+                if (r >= 4 && (r & 1) == 0) {
+                    const int kr = r / 2 - 1;           // row finished this round
+                    if (lt == 0 && S.kacc[a] < 0) {
+                        double e2 = 0.0;
+                        for (int q = 0; q < nm; q++) e2 = fmax(e2, S.err[a][kr][q]);
+                        if (e2 <= tol2) S.kacc[a] = kr;
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        // attempt 0 accepted: done; at the last round every attempt has
+                        // decided and the first accepted one (in halving order) is taken
+                        if (S.kacc[0] >= 0) S.decision = 0;
+                        else if (r == 2 * kBsRows) {
+                            int dcs = A;
+                            for (int q = A - 1; q >= 0; q--)
+                                if (S.kacc[q] >= 0) dcs = q;
+                            S.decision = dcs;
                         }
+                    }
+                    __syncthreads();
+                    if (S.decision >= 0) break;
                 }
-                __syncthreads();
-                if (last) break;
-                if (kacc <= 2) H *= 2.0;
-                else if (kacc >= 6) H *= 0.5;
-            } else {
-                H *= 0.5;
             }
-            if (nsub >= cap) {
-                failed = 1;
-                break;
+            const int dec = S.decision;
+            // replay the sequential control flow over the attempts just made
+            for (int q = 0; q < A; q++) {
+                nsub++;
+                const double Hq = ldexp(H, -q);
+                if (q == dec) {
+                    const int kacc = S.kacc[q];
+                    if (act && a == q && k == kacc)
+                        for (int c = 0; c < 6; c++) S.y[c][b] = diag[c];
+                    const int lastq = (q == 0) ? last0 : 0;
+                    t = lastq ? dt : t + Hq;
+                    if (tid == 0) S.collide = 0;
+                    __syncthreads();
+                    // any pair in contact?  (exact sequential resolution only if so)
+                    for (int e = tid; e < nm * nm; e += NT) {
+                        int u = e / nm, w = e % nm;
+                        if (w > u && S.alive[u] && S.alive[w]) {
+                            double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
+                                   dz = S.y[2][w] - S.y[2][u];
+                            if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w]) S.collide = 1;
+                        }
+                    }
+                    __syncthreads();
+                    if (S.collide && tid == 0) {
+                        for (int u = 0; u < nm; u++)
+                            for (int w = u + 1; w < nm && S.alive[u]; w++) {
+                                if (!S.alive[w]) continue;
+                                double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
+                                       dz = S.y[2][w] - S.y[2][u];
+                                if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w])
+                                    bs_merge<NT, A>(S, p, u, w);
+                            }
+                    }
+                    __syncthreads();
+                    if (lastq) {
+                        finished = 1;
+                        break;
+                    }
+                    H = Hq;
+                    if (kacc <= 2) H *= 2.0;
+                    else if (kacc >= 6) H *= 0.5;
+                    if (nsub >= cap) failed = 1;
+                    break;
+                }
+                if (nsub >= cap) {   // attempt q rejected
+                    failed = 1;
+                    break;
+                }
             }
+            if (dec == A && !failed) H = ldexp(H, -A);   // every attempt rejected
+            __syncthreads();
         }
         if (failed) {
             if (tid == 0) set_status(d.ctl, kEbs, g);
@@ -331,6 +349,14 @@ __global__ void __launch_bounds__(kBsThreads) k_bs(Dev d) {
     }
 }
 
-void launch_bs(const Dev& d, int grid, cudaStream_t s) { k_bs<<<grid, kBsThreads, 0, s>>>(d); }
+constexpr int kBsSmallThreads = 128;   // groups of up to 4 members: 4 attempts, one warp each
+constexpr int kBsLargeThreads = 512;   // groups of up to 64 members: one attempt
+
+void launch_bs(const Dev& d, int grid, cudaStream_t s) {
+    k_bs<kBsSmallThreads, 4><<<grid, kBsSmallThreads, 0, s>>>(d, 1);
+    prof_mark("bs: groups <= 4");
+    k_bs<kBsLargeThreads, 1><<<(grid + 15) / 16, kBsLargeThreads, 0, s>>>(d, 0);
+    prof_mark("bs: groups > 4");
+}
 
 }  // namespace opal

@@ -253,6 +253,7 @@ void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, 
                  cudaStream_t s) {
     if (precision == 1) kMixed[v].launch(d, items, nitems, grid, s);
     else kFp64[v].launch(d, items, nitems, grid, s);
+    prof_mark("kick");
 }
 
 }  // namespace opal

@@ -6,12 +6,13 @@
 // The minimum is taken over the cubic Hermite path of the relative motion
 // built from the saved start-of-drift state (x0, V0) and the state after
 // the drift (x1, V1).  Three stages, each a superset of the next:
-//   1. FP32, per pair, in the tile kernel: |d1| <= s_i + s_j, where s bounds
-//      how far a body's path strays from its end point (plus rc);
+//   1. FP32, on bodies sorted by the cell of their path midpoint c and tile
+//      pairs culled by boxes: |c_j - c_i| < s_i + s_j, where s bounds how far
+//      a body's path strays from its midpoint (plus rc);
 //   2. FP32, on the pairs that pass: distance from the origin to the chord
 //      d0 -> d1 minus a bound on the path's deviation from the chord;
 //   3. FP64 exact minimum on the survivors, in the same arithmetic as the
-//      oracle (16 intervals, sign change of d.d', 48 bisections).
+//      oracle (16 intervals, sign change of d.d', bracketed Newton).
 // Stages 1-2 carry margins far above FP32 rounding, so they never drop a
 // pair stage 3 would flag; the flagged set is that of stage 3 alone.
 #include "opal_internal.cuh"
@@ -46,31 +47,191 @@ __device__ __noinline__ bool chord_bound_passes(const Dev& d, int64_t i, int64_t
 }
 
 // ---------------------------------------------------------------- stage 1
-__global__ void __launch_bounds__(kSeg) k_scan(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
+// A body's Hermite path stays within s of its midpoint c, so a pair can come
+// within the critical distance only if |c_j - c_i| < s_i + s_j.  Each step
+// the bodies of a system are counting-sorted by the row-major cell of c on a
+// grid fitted to the system's box of midpoints (a few bodies per cell), so
+// that 64 consecutive bodies of the sorted order lie close together; a tile
+// of 64 gets the box of its intervals c +- s, and only tile pairs whose boxes
+// overlap are tested pair by pair (a pair passing the test has overlapping
+// intervals on every axis, so no such pair is skipped).
+
+struct SortGrid {
+    float lo[3];
+    double inv_h;
+    int nx, ny, nz;
+};
+
+// grid of the system: cells of side h with the system's bodies over at most
+// 2 cap - 1 cells, about 8 live bodies per cell in the two widest directions
+__device__ SortGrid sort_grid(const Dev& d, int sys, const SysInfo& si) {
+    __shared__ SortGrid g;
+    if (threadIdx.x == 0) {
+        float lo[3], hi[3];
+        for (int k = 0; k < 3; k++) {
+            lo[k] = fordinv(d.sbox[3 * sys + k]);
+            hi[k] = fordinv(d.sbox[3 * d.nsys + 3 * sys + k]);
+            if (!(hi[k] >= lo[k])) lo[k] = hi[k] = 0.0f;   // no live body
+            g.lo[k] = lo[k];
+        }
+        double W[3];
+        for (int k = 0; k < 3; k++) W[k] = fmax((double)hi[k] - (double)lo[k], 1e-30);
+        double a = fmax(W[0], W[1]), b = fmin(W[0], W[1]);
+        double wmax = fmax(a, W[2]), wmid = W[2] > a ? a : (W[2] > b ? W[2] : b);
+        double cells = fmax(1.0, (double)si.n / 8.0);
+        double h = sqrt(wmax * wmid / cells);
+        const double nb = (double)(2 * si.cap - 1);
+        for (int it = 0; it < 200; it++) {
+            double n3 = (floor(W[0] / h) + 1) * (floor(W[1] / h) + 1) * (floor(W[2] / h) + 1);
+            if (n3 <= nb) break;
+            h *= 1.25;
+        }
+        g.inv_h = 1.0 / h;
+        g.nx = (int)(W[0] * g.inv_h) + 1;
+        g.ny = (int)(W[1] * g.inv_h) + 1;
+        g.nz = (int)(W[2] * g.inv_h) + 1;
+    }
+    __syncthreads();
+    return g;
+}
+
+__device__ __forceinline__ int grid_index(float c, float lo, double inv_h, int n) {
+    double q = floor(((double)c - (double)lo) * inv_h);
+    q = fmin(fmax(q, 0.0), (double)(n - 1));
+    return (int)q;
+}
+
+__global__ void __launch_bounds__(kBodyThreads) k_sort_count(Dev d) {
+    if (d.ctl->status) return;
+    const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
+    const int sys = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
+    const SysInfo si = d.sys[sys];
+    const SortGrid g = sort_grid(d, sys, si);
+    const int64_t base = 2 * si.off;               // the system's buckets: [2 off, 2 off + 2 cap)
+    int key;
+    if (d.alive[b]) {
+        const float4 c = d.cen[b];
+        int ix = grid_index(c.x, g.lo[0], g.inv_h, g.nx), iy = grid_index(c.y, g.lo[1], g.inv_h, g.ny),
+            iz = grid_index(c.z, g.lo[2], g.inv_h, g.nz);
+        if (iy & 1) ix = g.nx - 1 - ix;            // serpentine rows keep row ends together
+        key = (int)(base + ((int64_t)iz * g.ny + iy) * g.nx + ix);
+    } else {
+        key = (int)(base + 2 * si.cap - 1);        // dead and padding bodies last
+    }
+    d.ckey[b] = key;
+    atomicAdd(&d.cstart[key], 1);
+}
+
+// exclusive prefix sum of the bucket counts (one block)
+__global__ void __launch_bounds__(1024) k_sort_prefix(Dev d) {
+    __shared__ int warp_sum[32];
+    __shared__ int carry;
+    if (d.ctl->status) return;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < d.ncell; base += 1024) {
+        const int k = base + threadIdx.x;
+        int v = k < d.ncell ? d.cstart[k] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = warp_sum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sum[lane] = w;
+        }
+        __syncthreads();
+        const int excl = carry + x - v + (warp > 0 ? warp_sum[warp - 1] : 0);
+        if (k < d.ncell) d.ccursor[k] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+}
+
+// scatter into sorted order and copy each body's midpoint record beside it
+__global__ void __launch_bounds__(kBodyThreads) k_sort_scatter(Dev d) {
+    if (d.ctl->status) return;
+    const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
+    const int pos = atomicAdd(&d.ccursor[d.ckey[b]], 1);
+    d.csorted[pos] = (int)b;
+    d.cen_sorted[pos] = d.cen[b];
+}
+
+// box of c +- s over the live bodies of each 64-body tile of the sorted order
+__global__ void __launch_bounds__(kSeg) k_tile_box(Dev d) {
+    if (d.ctl->status) return;
+    const int64_t t = blockIdx.x;
+    const int64_t pos = t * kSeg + threadIdx.x;
+    const float4 c = d.cen_sorted[pos];
+    const bool live = d.alive[d.csorted[pos]] != 0;
+    float v[6];
+    v[0] = live ? __fsub_rd(c.x, c.w) : 3.0e38f;
+    v[1] = live ? __fsub_rd(c.y, c.w) : 3.0e38f;
+    v[2] = live ? __fsub_rd(c.z, c.w) : 3.0e38f;
+    v[3] = live ? __fadd_ru(c.x, c.w) : -3.0e38f;
+    v[4] = live ? __fadd_ru(c.y, c.w) : -3.0e38f;
+    v[5] = live ? __fadd_ru(c.z, c.w) : -3.0e38f;
+    __shared__ float red[2][6];
+    for (int k = 0; k < 6; k++) {
+        float x = v[k];
+        for (int o = 16; o >= 1; o >>= 1) {
+            float y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = k < 3 ? fminf(x, y) : fmaxf(x, y);
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        d.tbox[6 * t + k] = k < 3 ? fminf(red[0][k], red[1][k]) : fmaxf(red[0][k], red[1][k]);
+    }
+}
+
+__device__ __forceinline__ bool boxes_overlap(const float* a, const float* b) {
+    return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
+}
+
+// tile pairs (A, B >= A) of the sorted order whose boxes overlap
+__global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
     __shared__ float4 sj[kSeg];
+    __shared__ int gj[kSeg];
     if (d.ctl->status) return;
     const float T = (float)d.p.dt;
     const int lane = threadIdx.x & 31;
     for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
         const PairTile tl = tiles[it];
-        const int64_t i = tl.i0 + threadIdx.x;
-        const float4 hi = d.kh[i];
-        const float si = d.sc0[i].w;
+        const float* ba = d.tbox + 6 * (tl.i0 / kSeg);
+        const float* bb = d.tbox + 6 * (tl.j0 / kSeg);
+        if (!boxes_overlap(ba, bb)) continue;       // the same for the whole block
+        const int64_t pi = tl.i0 + threadIdx.x;
+        const float4 ci = d.cen_sorted[pi];
+        const int gi = d.csorted[pi];
         __syncthreads();
-        {
-            int64_t j = tl.j0 + threadIdx.x;
-            float4 h = d.kh[j];
-            sj[threadIdx.x] = make_float4(h.x, h.y, h.z, d.sc0[j].w);
-        }
+        sj[threadIdx.x] = d.cen_sorted[tl.j0 + threadIdx.x];
+        gj[threadIdx.x] = d.csorted[tl.j0 + threadIdx.x];
         __syncthreads();
+        const bool diag = tl.i0 == tl.j0;
         for (int jj = 0; jj < kSeg; jj++) {
-            const int64_t j = tl.j0 + jj;
-            const float4 pj = sj[jj];
-            float dx = pj.x - hi.x, dy = pj.y - hi.y, dz = pj.z - hi.z;
+            const float4 cj = sj[jj];
+            float dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
             float r2 = dx * dx + dy * dy + dz * dz;
-            float Ts = si + pj.w;
-            bool pass = (j > i) && (r2 < Ts * Ts);
-            if (pass) pass = chord_bound_passes(d, i, j, T);
+            float Ts = ci.w + cj.w;
+            bool pass = (!diag || jj > (int)threadIdx.x) && (r2 < Ts * Ts);
+            int a = 0, b = 0;
+            if (pass) {
+                a = min(gi, gj[jj]);
+                b = max(gi, gj[jj]);
+                pass = d.alive[a] && d.alive[b] && chord_bound_passes(d, a, b, T);
+            }
             unsigned mask = __ballot_sync(0xffffffffu, pass);
             if (mask) {
                 int leader = __ffs(mask) - 1;
@@ -79,7 +240,7 @@ __global__ void __launch_bounds__(kSeg) k_scan(Dev d, const PairTile* __restrict
                 base = __shfl_sync(0xffffffffu, base, leader);
                 if (pass) {
                     int idx = base + __popc(mask & ((1u << lane) - 1u));
-                    if (idx < d.cand_cap) d.cand[idx] = make_int2((int)i, (int)j);
+                    if (idx < d.cand_cap) d.cand[idx] = make_int2(a, b);
                 }
             }
         }
@@ -87,38 +248,45 @@ __global__ void __launch_bounds__(kSeg) k_scan(Dev d, const PairTile* __restrict
 }
 
 // ---------------------------------------------------------------- stage 3
-// Relative position and its s-derivative on the cubic Hermite path,
-// s in [0, 1], T = dt (same operation order as the oracle).
+// Relative position and its first and second s-derivatives on the cubic
+// Hermite path, s in [0, 1], T = dt (same operation order as the oracle).
 __device__ __forceinline__ void hermite_rel(double s, double T, const double* d0, const double* u0,
-                                            const double* d1, const double* u1, double* dd, double* dp) {
+                                            const double* d1, const double* u1, double* dd, double* dp,
+                                            double* d2) {
     double s2 = s * s, s3 = s2 * s;
     double h00 = 2.0 * s3 - 3.0 * s2 + 1.0, h10 = s3 - 2.0 * s2 + s;
     double h01 = -2.0 * s3 + 3.0 * s2, h11 = s3 - s2;
     double p00 = 6.0 * s2 - 6.0 * s, p10 = 3.0 * s2 - 4.0 * s + 1.0;
     double p01 = -6.0 * s2 + 6.0 * s, p11 = 3.0 * s2 - 2.0 * s;
+    double q00 = 12.0 * s - 6.0, q10 = 6.0 * s - 4.0, q01 = -12.0 * s + 6.0, q11 = 6.0 * s - 2.0;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         dd[k] = h00 * d0[k] + h10 * T * u0[k] + h01 * d1[k] + h11 * T * u1[k];
         dp[k] = p00 * d0[k] + p10 * T * u0[k] + p01 * d1[k] + p11 * T * u1[k];
+        d2[k] = q00 * d0[k] + q10 * T * u0[k] + q01 * d1[k] + q11 * T * u1[k];
     }
 }
 
-// Same result as scanning the 16 intervals in order and bisecting each sign
-// change on the spot (the minimum over the intervals does not depend on the
-// order they are visited in), arranged so that the lanes of a warp bisect
-// together instead of one after another.
+__device__ __forceinline__ double dot3p(const double* a, const double* b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Minimum of |d(s)|^2: the ends and every local minimum inside (a - to +
+// sign change of g = d.d' on 16 intervals, refined by bracketed Newton on g).
+// The minimum over the intervals does not depend on the order they are
+// visited in; the lanes of a warp refine their intervals together.
 __device__ double min_sep2(double T, const double* d0, const double* u0, const double* d1, const double* u1) {
-    double D = d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2];
-    double D1 = d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2];
+    double D = dot3p(d0, d0);
+    double D1 = dot3p(d1, d1);
     if (D1 < D) D = D1;
-    double dd[3], dp[3];
-    hermite_rel(0.0, T, d0, u0, d1, u1, dd, dp);
-    double ga = dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2];
+    double dd[3], dp[3], d2[3];
+    hermite_rel(0.0, T, d0, u0, d1, u1, dd, dp, d2);
+    double ga = dot3p(dd, dp);
     unsigned mask = 0;
     for (int k = 0; k < 16; k++) {
         double sb = (k + 1) / 16.0;
-        hermite_rel(sb, T, d0, u0, d1, u1, dd, dp);
-        double gb = dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2];
+        hermite_rel(sb, T, d0, u0, d1, u1, dd, dp, d2);
+        double gb = dot3p(dd, dp);
         if (ga < 0.0 && gb >= 0.0) mask |= 1u << k;
         ga = gb;
     }
@@ -126,15 +294,20 @@ __device__ double min_sep2(double T, const double* d0, const double* u0, const d
         if (mask) {
             int k = __ffs(mask) - 1;
             mask &= mask - 1;
-            double lo = k / 16.0, hi = (k + 1) / 16.0;
-            for (int b = 0; b < 48; b++) {
-                double mid = 0.5 * (lo + hi);
-                hermite_rel(mid, T, d0, u0, d1, u1, dd, dp);
-                if (dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2] < 0.0) lo = mid;
-                else hi = mid;
+            double lo = k / 16.0, hi = (k + 1) / 16.0, s = 0.5 * (lo + hi);
+            for (int it = 0; it < 60; it++) {
+                hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
+                double g = dot3p(dd, dp), gp = dot3p(dp, dp) + dot3p(dd, d2);
+                if (g < 0.0) lo = s;
+                else hi = s;
+                double sn = s - g / gp;
+                if (!(gp > 0.0 && sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+                double step = sn - s;
+                s = sn;
+                if (fabs(step) <= 1e-12) break;
             }
-            hermite_rel(0.5 * (lo + hi), T, d0, u0, d1, u1, dd, dp);
-            double Dm = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+            hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
+            double Dm = dot3p(dd, dd);
             if (Dm < D) D = Dm;
         }
     }
@@ -295,17 +468,35 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(Dev d) {
         d.ctl->ngroups = total_g;
         d.ctl->ninvolved = total_u;
     }
+    __syncthreads();
+    // groups too large for the one-warp encounter kernel
+    for (int g = threadIdx.x; g < total_g; g += blockDim.x)
+        if (d.goff[g + 1] - d.goff[g] > 4) d.glarge[atomicAdd(&d.ctl->nlarge, 1)] = g;
     for (int k = threadIdx.x; k < total_u; k += blockDim.x) d.undo[3 * k + 2] = -1.0;
 }
 
 void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s) {
-    k_scan<<<grid, kSeg, 0, s>>>(d, tiles, ntiles);
+    const unsigned nb = (unsigned)(d.ntot / kBodyThreads);
+    k_sort_count<<<nb, kBodyThreads, 0, s>>>(d);
+    prof_mark("scan: sort count");
+    k_sort_prefix<<<1, 1024, 0, s>>>(d);
+    prof_mark("scan: sort prefix");
+    k_sort_scatter<<<nb, kBodyThreads, 0, s>>>(d);
+    prof_mark("scan: sort scatter");
+    k_tile_box<<<(unsigned)(d.ntot / kSeg), kSeg, 0, s>>>(d);
+    prof_mark("scan: tile boxes");
+    k_scan_tiles<<<grid, kSeg, 0, s>>>(d, tiles, ntiles);
+    prof_mark("scan: tile pairs");
 }
-void launch_confirm(const Dev& d, int grid, cudaStream_t s) { k_confirm<<<grid, 256, 0, s>>>(d); }
+void launch_confirm(const Dev& d, int grid, cudaStream_t s) {
+    k_confirm<<<grid, 256, 0, s>>>(d);
+    prof_mark("confirm (FP64)");
+}
 
 size_t group_smem() { return (size_t)kGroupMaxKeys * (sizeof(long long) + 2 * sizeof(int)); }
 void launch_group(const Dev& d, cudaStream_t s) {
     k_group<<<1, kGroupThreads, group_smem(), s>>>(d);
+    prof_mark("group");
 }
 cudaError_t group_setup() {
     return cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem());

@@ -21,6 +21,14 @@ namespace {
 
 thread_local char g_err[512];
 
+}  // namespace
+
+namespace opal {
+thread_local ProfRec* g_prof = nullptr;
+}
+
+namespace {
+
 void set_err(char* buf, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -286,9 +294,17 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.alive, N));
     TRYF(dalloc(s, &d.body_sys, N));
     TRYF(dalloc(s, &d.label, N));
-    float4** f4[] = {&d.kh, &d.kl, &d.sc0, &d.sc1, &d.sv0, &d.sv1};
+    float4** f4[] = {&d.kh, &d.kl, &d.cen, &d.sc0, &d.sc1, &d.sv0, &d.sv1};
     for (auto pp : f4) TRYF(dalloc(s, pp, N));
     TRYF(dalloc(s, &d.rcf, N));
+    d.ncell = (int)(2 * N);
+    TRYF(dalloc(s, &d.sbox, 6 * nsys));
+    TRYF(dalloc(s, &d.ckey, N));
+    TRYF(dalloc(s, &d.cstart, d.ncell));
+    TRYF(dalloc(s, &d.ccursor, d.ncell));
+    TRYF(dalloc(s, &d.csorted, N));
+    TRYF(dalloc(s, &d.cen_sorted, N));
+    TRYF(dalloc(s, &d.tbox, 6 * (N / kSeg)));
     TRYF(dalloc(s, &d.rcmax, nsys));
     TRYF(dalloc(s, &d.pacc_x, slots));
     TRYF(dalloc(s, &d.pacc_y, slots));
@@ -301,6 +317,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.flag, d.flag_cap));
     TRYF(dalloc(s, &d.members, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.goff, 2 * d.flag_cap + 2));
+    TRYF(dalloc(s, &d.glarge, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.glost, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.undo, 3 * (2 * d.flag_cap + 2)));
     TRYF(dalloc(s, &d.E_lost, nsys));
@@ -419,6 +436,14 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
 #undef TRYF
 }
 
+// bucket counts to zero; midpoint boxes to (+huge, -huge) in the order map
+void reset_scan_order(opal_sim* s) {
+    const Dev& d = s->d;
+    cudaMemsetAsync(d.cstart, 0, (size_t)d.ncell * sizeof(int), s->stream);
+    cudaMemsetAsync(d.sbox, 0x7f, 3 * d.nsys * sizeof(int), s->stream);
+    cudaMemsetAsync(d.sbox + 3 * d.nsys, 0x80, 3 * d.nsys * sizeof(int), s->stream);
+}
+
 // the kernels of one step, in order; names for profiling
 const char* kKernelNames[] = {"counters", "open(kick+jump+drift)", "scan", "confirm", "group", "bs", "kick",
                               "close(jump+kick)", "finish"};
@@ -431,6 +456,8 @@ void launch_stage(opal_sim* s, int k) {
             cudaMemsetAsync(reinterpret_cast<char*>(d.ctl) + offsetof(Ctl, ncand), 0,
                             offsetof(Ctl, steps_done) - offsetof(Ctl, ncand), s->stream);
             cudaMemsetAsync(d.rcmax, 0, d.nsys * sizeof(float), s->stream);
+            reset_scan_order(s);
+            prof_mark("memsets");
             break;
         case 1: launch_open(d, s->stream); break;
         case 2: launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, s->stream); break;
@@ -615,28 +642,39 @@ void* opal_stream(const opal_sim* s) { return s ? (void*)s->stream : nullptr; }
 opal_status opal_profile_steps(opal_sim* s, int64_t nsteps, int32_t cap, int32_t* nk, double* ms,
                                const char** names) {
     if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
-    const int K = kNumKernels;
-    if (nk) *nk = K;
-    std::vector<cudaEvent_t> ev(K + 1);
-    for (auto& e : ev) CK(cudaEventCreate(&e));
-    std::vector<double> acc(K, 0.0);
+    ProfRec rec{};
+    rec.stream = s->stream;
+    rec.cap = 64;
+    for (int k = 0; k < rec.cap; k++) CK(cudaEventCreate(&rec.ev[k]));
+    cudaEvent_t start;
+    CK(cudaEventCreate(&start));
+    std::vector<const char*> order;
+    std::vector<double> acc;
     for (int64_t t = 0; t < nsteps; t++) {
-        for (int k = 0; k < K; k++) {
-            CK(cudaEventRecord(ev[k], s->stream));
-            launch_stage(s, k);
-        }
-        CK(cudaEventRecord(ev[K], s->stream));
-        CK(cudaEventSynchronize(ev[K]));
-        for (int k = 0; k < K; k++) {
+        rec.n = 0;
+        g_prof = &rec;
+        CK(cudaEventRecord(start, s->stream));
+        for (int k = 0; k < kNumKernels; k++) launch_stage(s, k);
+        g_prof = nullptr;
+        CK(cudaEventSynchronize(rec.ev[rec.n - 1]));
+        for (int k = 0; k < rec.n; k++) {
             float f = 0;
-            CK(cudaEventElapsedTime(&f, ev[k], ev[k + 1]));
-            acc[k] += f;
+            CK(cudaEventElapsedTime(&f, k == 0 ? start : rec.ev[k - 1], rec.ev[k]));
+            size_t q = 0;
+            while (q < order.size() && std::strcmp(order[q], rec.names[k]) != 0) q++;
+            if (q == order.size()) {
+                order.push_back(rec.names[k]);
+                acc.push_back(0.0);
+            }
+            acc[q] += f;
         }
     }
-    for (auto& e : ev) cudaEventDestroy(e);
-    for (int k = 0; k < K && k < cap; k++) {
+    for (int k = 0; k < rec.cap; k++) cudaEventDestroy(rec.ev[k]);
+    cudaEventDestroy(start);
+    if (nk) *nk = (int32_t)order.size();
+    for (size_t k = 0; k < order.size() && (int32_t)k < cap; k++) {
         if (ms) ms[k] = nsteps > 0 ? acc[k] / (double)nsteps : 0.0;
-        if (names) names[k] = kKernelNames[k];
+        if (names) names[k] = order[k];
     }
     return finish_steps(s, 0);
 }
@@ -644,6 +682,20 @@ opal_status opal_profile_steps(opal_sim* s, int64_t nsteps, int32_t cap, int32_t
 const char* opal_last_error(const opal_sim* s) { return s ? s->err : g_err; }
 
 const char* opal_kick_config(const opal_sim* s) { return s ? s->kick_desc : ""; }
+
+int32_t opal_graph_kernels(const opal_sim* s) {
+    if (!s || !s->graph) return -1;
+    size_t n = 0;
+    if (cudaGraphGetNodes(s->graph, nullptr, &n) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(s->graph, nodes.data(), &n) != cudaSuccess) return -1;
+    int32_t k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) k++;
+    }
+    return k;
+}
 
 opal_status opal_time_kick(opal_sim* s, int32_t enable) {
     if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
@@ -694,6 +746,7 @@ opal_status opal_debug_accel(opal_sim* s, const double* rc, double* a) {
     }
     // float copies of the current positions with these rc, then the kick
     CK(cudaMemsetAsync(d.rcmax, 0, d.nsys * 4, s->stream));
+    reset_scan_order(s);
     launch_debug_scan_prep(d, s->stream);
     launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, s->stream);
     launch_first_accel_finish(d, s->stream);
@@ -773,6 +826,7 @@ opal_status opal_debug_scan(opal_sim* s, const double* x0, const double* V0, con
     }
     CK(cudaMemsetAsync(reinterpret_cast<char*>(d.ctl) + offsetof(Ctl, ncand), 0,
                        offsetof(Ctl, steps_done) - offsetof(Ctl, ncand), s->stream));
+    reset_scan_order(s);
     launch_debug_scan_prep(d, s->stream);
     launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, s->stream);
     launch_confirm(d, s->confirm_grid, s->stream);
@@ -835,6 +889,11 @@ opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0,
     Ctl c{};
     c.ngroups = 1;
     c.ninvolved = (int)n;
+    if (n > 4) {
+        int zero = 0;
+        c.nlarge = 1;
+        CK(cudaMemcpy(d.glarge, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    }
     CK(cudaMemcpy(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
     launch_bs(d, 1, s->stream);
     CK(cudaGetLastError());

@@ -17,10 +17,10 @@ constexpr int kPad = 128;        // body padding of every system (block of the b
 constexpr int kSeg = 64;         // bodies per partial-sum segment
 constexpr int kBodyThreads = 128;
 constexpr int kBsMaxMembers = 64;   // bodies per encounter group
-constexpr int kBsWarps = 4;         // warps per BS group (two midpoint sequences each)
 constexpr int kBsRows = 8;          // extrapolation rows: n_k = 2, 4, ..., 16
 constexpr int kGroupMaxBodies = 4096;   // flagged pairs the grouping kernel takes per step
 constexpr float kFar = 1.0e18f;     // parking coordinate of ghost and dead bodies (float copies)
+
 
 // status codes mirror opal_status
 enum : int { kOk = 0, kEinval = 1, kEnomem = 2, kEcuda = 3, kEkepler = 4, kEbs = 5, kEoverflow = 6,
@@ -41,6 +41,8 @@ struct Ctl {
     int ninvolved;       // bodies in groups (this step)
     int nmerge;          // mergers (this step)
     int kepler_max;      // largest drift iteration count (this step)
+    int nlarge;          // groups too large for one warp (this step)
+    int pad0;
     unsigned long long nsub;  // BS substeps (this step)
     long long steps_done;
     int cand_overflow;   // candidates lost to a full candidate list (forces a status)
@@ -98,7 +100,9 @@ struct Dev {
     float4* kl;    // (x_lo, y_lo, z_lo, max(4 rc^2, tiny))
     float* rcf;    // rc as float (rounded up)
     float* rcmax;  // per system: largest rc of the step (rounded up)
-    float4* sc0;   // (x0_hi, y0_hi, z0_hi, s = prefilter radius)
+    float4* cen;   // (c_hi, s): midpoint of the body's path over the step and the radius
+                   // s bounding the path's distance from it (plus rc and margins)
+    float4* sc0;   // (x0_hi, y0_hi, z0_hi, s)
     float4* sc1;   // (x0_lo, y0_lo, z0_lo, 0)
     float4* sv0;   // (V0, |V0|)
     float4* sv1;   // (V1, |V1|)
@@ -107,12 +111,23 @@ struct Dev {
     double *pP_close;                   // [3][nseg_tot] momentum before the closing jump
     double *pP_open;                    // [3][nseg_tot] momentum before the opening jump
     int64_t nseg_tot;
+    // spatial order of the scan: each system's bodies counting-sorted by the
+    // cell of their path midpoint, and the box of every 64-body tile
+    int* sbox;                          // [2][nsys][3] order-mapped min, then max, of the midpoints
+    int* ckey;                          // per body: its bucket
+    int* cstart;                        // [ncell] bucket counts
+    int* ccursor;                       // [ncell] scatter cursors
+    int* csorted;                       // bodies in sorted order
+    float4* cen_sorted;                 // their midpoint records, in sorted order
+    float* tbox;                        // [ntot / 64][6] tile boxes of c +- s
+    int ncell;                          // buckets: 2 per body slot
     // encounter pipeline
     int2* cand;  int64_t cand_cap;      // FP32-bound candidates
     int2* flag;  int64_t flag_cap;      // flagged pairs
     int32_t* label;                     // per body; -1 when not in a group
     int32_t* members;                   // group members, grouped, ascending
     int32_t* goff;                      // [ngroups + 1] member offsets
+    int32_t* glarge;                    // groups of more than 4 members
     double* glost;                      // per group energy lost to mergers
     double* undo;                       // per member slot: m, R, alive (3 doubles)
     double* E_lost;                     // per system running sum
@@ -148,24 +163,26 @@ __device__ __forceinline__ float changeover_f(float r, float rc, int form) {
     return y * y * y * (10.0f - 15.0f * y + 6.0f * y * y);
 }
 
-// Stumpff functions c0..c3 by their series at an argument quartered until
-// |z| <= 0.1, then the double-angle relations undo the quartering.
+// Stumpff functions c0..c3: at an argument quartered until |z| <= 0.1, c2 and
+// c3 by ten nested series terms (multiplying by the reciprocal of
+// (k+2j-1)(k+2j)), c0 = 1 - z c2 and c1 = 1 - z c3; then the double-angle
+// relations undo the quartering.
 __device__ __forceinline__ void stumpff(double z, double& c0, double& c1, double& c2, double& c3) {
     int nq = 0;
     while (fabs(z) > 0.1) {
         z *= 0.25;
         nq++;
     }
-    double s[4];
-    const double inv_fact[4] = {1.0, 1.0, 0.5, 1.0 / 6.0};
+    double s2 = 1.0, s3 = 1.0;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        double t = 1.0;
-#pragma unroll
-        for (int j = 10; j >= 1; j--) t = 1.0 - z * t / (double)((k + 2 * j - 1) * (k + 2 * j));
-        s[k] = t * inv_fact[k];
+    for (int j = 10; j >= 1; j--) {
+        s2 = 1.0 - z * s2 * (1.0 / (double)((2 * j + 1) * (2 * j + 2)));
+        s3 = 1.0 - z * s3 * (1.0 / (double)((2 * j + 2) * (2 * j + 3)));
     }
-    c0 = s[0]; c1 = s[1]; c2 = s[2]; c3 = s[3];
+    c2 = s2 * 0.5;
+    c3 = s3 * (1.0 / 6.0);
+    c0 = 1.0 - z * c2;
+    c1 = 1.0 - z * c3;
     for (; nq > 0; nq--) {
         c3 = (c2 + c0 * c3) * 0.25;
         c2 = c1 * c1 * 0.5;
@@ -258,6 +275,7 @@ __device__ __forceinline__ void park_floats(const Dev& d, int64_t b) {
     d.kl[b] = make_float4(0.0f, 0.0f, 0.0f, 1e-30f);
     d.rcf[b] = 0.0f;
     d.sc0[b] = make_float4(far, far, far, 0.0f);
+    d.cen[b] = make_float4(far, far, far, 0.0f);
     d.sc1[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     d.sv0[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     d.sv1[b] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -272,6 +290,30 @@ __device__ __forceinline__ void kick_floats(const Dev& d, int64_t b, double x, d
     d.kh[b] = make_float4(hx, hy, hz, (float)m);
     d.kl[b] = make_float4(lx, ly, lz, 0.0f);
     d.rcf[b] = __double2float_ru(rc);
+}
+
+// order-preserving map of a float to an int (for atomic min / max), and back
+__device__ __forceinline__ int ford(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float fordinv(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// ---------------------------------------------------------------------------
+// Profiling: while opal_profile_steps runs, a recorder is installed and every
+// launcher records a CUDA event on the stream after each kernel it launches.
+struct ProfRec {
+    cudaStream_t stream;
+    int n, cap;
+    const char* names[64];
+    cudaEvent_t ev[64];
+};
+extern thread_local ProfRec* g_prof;
+inline void prof_mark(const char* name) {
+    if (g_prof && g_prof->n < g_prof->cap) {
+        cudaEventRecord(g_prof->ev[g_prof->n], g_prof->stream);
+        g_prof->names[g_prof->n++] = name;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -64,6 +64,8 @@ def _declare(L):
     L.opal_time_kick.restype = C.c_int
     L.opal_last_kick_ms.argtypes = [_P]
     L.opal_last_kick_ms.restype = C.c_double
+    L.opal_graph_kernels.argtypes = [_P]
+    L.opal_graph_kernels.restype = C.c_int32
     L.opal_kick_config.argtypes = [_P]
     L.opal_kick_config.restype = C.c_char_p
     L.opal_last_error.argtypes = [_P]
@@ -209,6 +211,10 @@ class Simulation:
                     n_candidates=int(out[4]), kepler_iter_max=int(out[5]))
 
     @property
+    def graph_kernels(self) -> int:
+        return lib().opal_graph_kernels(self.ptr)
+
+    @property
     def kick_config(self) -> str:
         return lib().opal_kick_config(self.ptr).decode()
 
@@ -219,7 +225,7 @@ class Simulation:
         return lib().opal_last_kick_ms(self.ptr)
 
     def profile(self, nsteps: int) -> dict:
-        cap = 16
+        cap = 64
         nk = C.c_int32(0)
         ms = np.zeros(cap)
         names = (C.c_char_p * cap)()

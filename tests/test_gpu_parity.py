@@ -158,7 +158,7 @@ def test_scan_backwards_in_time(opal):
 
 
 # ---------------------------------------------------------------- BS
-def _bs_compare(opal, X0, V0, m, R, rc, dt):
+def _bs_compare(opal, X0, V0, m, R, rc, dt, tol=1e-12, exact_substeps=True):
     n = len(m)
     p = oracle.make_params(dt=dt)
     mo, Ro, rco = m.copy(), R.copy(), rc.copy()
@@ -173,11 +173,14 @@ def _bs_compare(opal, X0, V0, m, R, rc, dt):
     assert out["alive"].tolist() == alive.tolist()
     assert np.array_equal(out["m"], mo)
     live = alive > 0
-    assert relpos(out["x"][live], Xo[live]) <= 1e-12
-    assert np.abs(out["V"][live] - Vo[live]).max() <= 1e-12 * np.abs(Vo[live]).max()
-    assert out["substeps"] == sub
-    if nmg:
-        assert abs(out["E_lost"] - El) <= 1e-12 * abs(El)
+    assert relpos(out["x"][live], Xo[live]) <= tol
+    assert np.abs(out["V"][live] - Vo[live]).max() <= tol * np.abs(Vo[live]).max()
+    if exact_substeps:
+        assert out["substeps"] == sub
+    else:
+        assert abs(out["substeps"] - sub) <= max(2, sub // 50), (out["substeps"], sub)
+    if nmg:   # a difference of nearly equal energies: relative precision ~1e-12 / 1e-3
+        assert abs(out["E_lost"] - El) <= 1e-10 * abs(El)
     return nmg, sub
 
 
@@ -193,6 +196,31 @@ def test_bs_close_encounter_matches_oracle(opal):
     m = np.array([3e-6, 2e-6, 1e-6])
     nmg, sub = _bs_compare(opal, X0, V0, m, np.full(3, 1e-8), np.array([0.02, 0.01, 0.01]), 0.0628)
     assert sub >= 1
+
+
+@pytest.mark.parametrize("dt,offset", [(0.3, 2e-4), (0.6, 5e-5), (0.0628, 1e-4)])
+def test_bs_deep_encounter_with_rejections_matches_oracle(opal, dt, offset):
+    """Close approaches that force 150-340 substeps and many halvings.  The
+    bound is derived from the method's own accuracy on the case: ten times
+    the change of the oracle's result when bs_tol goes from 1e-12 to 1e-13
+    (at least 1e-10).  Substep counts may differ where an accept decision
+    sits at the tolerance."""
+    x1, v1 = ic.elements_to_state(1.0, 1.0, 0.02, 0.0, 0.0, 0.0, 0.0)
+    X0 = np.array([x1, x1 + [0.0, 0.002, offset]])
+    V0 = np.array([v1, v1 + [0.0, -0.06, 0.0]])
+    m = np.array([3e-6, 1e-6])
+    R, rc = np.full(2, 1e-9), np.array([0.02, 0.02])
+    ref = {}
+    for tol in (1e-12, 1e-13):
+        X, V = X0.copy(), V0.copy()
+        st, *_ = oracle.bs_group(oracle.make_params(dt=dt, bs_tol=tol), np.arange(2, dtype=np.int32), m.copy(),
+                                 R.copy(), rc.copy(), np.ones(2, np.int32), X, V)
+        assert st == oracle.OK
+        ref[tol] = X
+    self_change = np.abs(ref[1e-12] - ref[1e-13]).max() / np.abs(ref[1e-13]).max()
+    bound = max(1e-10, 10 * self_change)
+    nmg, sub = _bs_compare(opal, X0, V0, m, R, rc, dt, tol=bound, exact_substeps=False)
+    assert sub >= 100
 
 
 def test_bs_merger_matches_oracle(opal):
