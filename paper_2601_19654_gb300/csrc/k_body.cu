@@ -284,12 +284,20 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
         d.ax[b] = 0.0; d.ay[b] = 0.0; d.az[b] = 0.0;
     }
     segment_sums(d, (int64_t)blockIdx.x * kBodyThreads, px, py, pz, d.pP_open);
-    if (!first && b == 0) {
-        // energy removed by this step's mergers, per system, in group order
-        int ng = d.ctl->ngroups;
-        for (int g = 0; g < ng; g++) {
-            double e = d.glost[g];
-            if (e != 0.0) d.E_lost[d.body_sys[d.members[d.goff[g]]]] += e;
+    if (!first && blockIdx.x == 0 && threadIdx.x < 32) {
+        // energy removed by this step's mergers, per system, in group order;
+        // the warp loads 32 groups at a time and lane 0 adds the nonzero ones
+        const int ng = d.ctl->ngroups;
+        for (int g0 = 0; g0 < ng; g0 += 32) {
+            const int g = g0 + threadIdx.x;
+            const double e = g < ng ? d.glost[g] : 0.0;
+            unsigned mask = __ballot_sync(0xffffffffu, e != 0.0);
+            while (mask) {
+                const int q = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const double eq = __shfl_sync(0xffffffffu, e, q);
+                if (threadIdx.x == 0) d.E_lost[d.body_sys[d.members[d.goff[g0 + q]]]] += eq;
+            }
         }
     }
 }

@@ -9,8 +9,9 @@
 //   1. FP32, on bodies sorted by the cell of their path midpoint c and tile
 //      pairs culled by boxes: |c_j - c_i| < s_i + s_j, where s bounds how far
 //      a body's path strays from its midpoint (plus rc);
-//   2. FP32, on the pairs that pass: distance from the origin to the chord
-//      d0 -> d1 minus a bound on the path's deviation from the chord;
+//   2. FP32, on the list of pairs that pass, one thread per pair: distance
+//      from the origin to the chord d0 -> d1 minus a bound on the path's
+//      deviation from the chord;
 //   3. FP64 exact minimum on the survivors, in the same arithmetic as the
 //      oracle (16 intervals, sign change of d.d', bracketed Newton).
 // Stages 1-2 carry margins far above FP32 rounding, so they never drop a
@@ -79,17 +80,24 @@ __device__ SortGrid sort_grid(const Dev& d, int sys, const SysInfo& si) {
         double a = fmax(W[0], W[1]), b = fmin(W[0], W[1]);
         double wmax = fmax(a, W[2]), wmid = W[2] > a ? a : (W[2] > b ? W[2] : b);
         double cells = fmax(1.0, (double)si.n / 8.0);
-        double h = sqrt(wmax * wmid / cells);
+        double inv_h = sqrt(cells / (wmax * wmid));
         const double nb = (double)(2 * si.cap - 1);
-        for (int it = 0; it < 200; it++) {
-            double n3 = (floor(W[0] / h) + 1) * (floor(W[1] / h) + 1) * (floor(W[2] / h) + 1);
-            if (n3 <= nb) break;
-            h *= 1.25;
+        double n[3];
+        for (int it = 0; it < 400; it++) {
+            for (int k = 0; k < 3; k++) n[k] = fmin(floor(W[k] * inv_h) + 1.0, 1.0e6);
+            if (n[0] * n[1] * n[2] <= nb) break;
+            inv_h *= 0.8;
         }
-        g.inv_h = 1.0 / h;
-        g.nx = (int)(W[0] * g.inv_h) + 1;
-        g.ny = (int)(W[1] * g.inv_h) + 1;
-        g.nz = (int)(W[2] * g.inv_h) + 1;
+        // grid_index clamps to these counts, so every key stays in the system's buckets
+        g.inv_h = inv_h;
+        g.nx = (int)n[0];
+        g.ny = (int)n[1];
+        g.nz = (int)n[2];
+        while ((double)g.nx * g.ny * g.nz > nb) {   // only if 400 shrinks were not enough
+            if (g.nx >= g.ny && g.nx >= g.nz) g.nx = max(1, g.nx / 2);
+            else if (g.ny >= g.nz) g.ny = max(1, g.ny / 2);
+            else g.nz = max(1, g.nz / 2);
+        }
     }
     __syncthreads();
     return g;
@@ -200,12 +208,12 @@ __device__ __forceinline__ bool boxes_overlap(const float* a, const float* b) {
     return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
 }
 
-// tile pairs (A, B >= A) of the sorted order whose boxes overlap
+// tile pairs (A, B >= A) of the sorted order whose boxes overlap: pairs that
+// pass |c_j - c_i| < s_i + s_j go to a list for stage 2
 __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
     __shared__ float4 sj[kSeg];
     __shared__ int gj[kSeg];
     if (d.ctl->status) return;
-    const float T = (float)d.p.dt;
     const int lane = threadIdx.x & 31;
     for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
         const PairTile tl = tiles[it];
@@ -220,28 +228,56 @@ __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __re
         gj[threadIdx.x] = d.csorted[tl.j0 + threadIdx.x];
         __syncthreads();
         const bool diag = tl.i0 == tl.j0;
+#pragma unroll 4
         for (int jj = 0; jj < kSeg; jj++) {
             const float4 cj = sj[jj];
             float dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
             float r2 = dx * dx + dy * dy + dz * dz;
             float Ts = ci.w + cj.w;
             bool pass = (!diag || jj > (int)threadIdx.x) && (r2 < Ts * Ts);
-            int a = 0, b = 0;
-            if (pass) {
-                a = min(gi, gj[jj]);
-                b = max(gi, gj[jj]);
-                pass = d.alive[a] && d.alive[b] && chord_bound_passes(d, a, b, T);
-            }
             unsigned mask = __ballot_sync(0xffffffffu, pass);
             if (mask) {
                 int leader = __ffs(mask) - 1;
                 int base = 0;
-                if (lane == leader) base = atomicAdd(&d.ctl->ncand, __popc(mask));
+                if (lane == leader) base = atomicAdd(&d.ctl->nnear, __popc(mask));
                 base = __shfl_sync(0xffffffffu, base, leader);
                 if (pass) {
                     int idx = base + __popc(mask & ((1u << lane) - 1u));
-                    if (idx < d.cand_cap) d.cand[idx] = make_int2(a, b);
+                    int a = gi, b = gj[jj];
+                    if (idx < d.near_cap) d.near[idx] = make_int2(min(a, b), max(a, b));
                 }
+            }
+        }
+    }
+}
+
+// stage 2 on the stage-1 list, one thread per pair
+__global__ void __launch_bounds__(256) k_chord(Dev d) {
+    if (d.ctl->status) return;
+    const int nn = d.ctl->nnear;
+    if (nn > d.near_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.ctl, kEoverflow, -4);
+        return;
+    }
+    const float T = (float)d.p.dt;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < nn; base += gridDim.x * blockDim.x) {
+        const int k = base + threadIdx.x;
+        bool pass = false;
+        int2 pr = make_int2(0, 0);
+        if (k < nn) {
+            pr = d.near[k];
+            pass = d.alive[pr.x] && d.alive[pr.y] && chord_bound_passes(d, pr.x, pr.y, T);
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, pass);
+        if (mask) {
+            int leader = __ffs(mask) - 1;
+            int b0 = 0;
+            if (lane == leader) b0 = atomicAdd(&d.ctl->ncand, __popc(mask));
+            b0 = __shfl_sync(0xffffffffu, b0, leader);
+            if (pass) {
+                int idx = b0 + __popc(mask & ((1u << lane) - 1u));
+                if (idx < d.cand_cap) d.cand[idx] = pr;
             }
         }
     }
@@ -487,6 +523,8 @@ void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, 
     prof_mark("scan: tile boxes");
     k_scan_tiles<<<grid, kSeg, 0, s>>>(d, tiles, ntiles);
     prof_mark("scan: tile pairs");
+    k_chord<<<152 * 4, 256, 0, s>>>(d);
+    prof_mark("scan: chord bound");
 }
 void launch_confirm(const Dev& d, int grid, cudaStream_t s) {
     k_confirm<<<grid, 256, 0, s>>>(d);

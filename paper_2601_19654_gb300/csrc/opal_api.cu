@@ -313,7 +313,9 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.pP_open, 3 * d.nseg_tot));
     d.flag_cap = P.encounter_capacity;
     d.cand_cap = std::max<int64_t>(1 << 16, 8 * d.flag_cap);
+    d.near_cap = std::max<int64_t>(1 << 20, 64 * N);
     TRYF(dalloc(s, &d.cand, d.cand_cap));
+    TRYF(dalloc(s, &d.near, d.near_cap));
     TRYF(dalloc(s, &d.flag, d.flag_cap));
     TRYF(dalloc(s, &d.members, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.goff, 2 * d.flag_cap + 2));

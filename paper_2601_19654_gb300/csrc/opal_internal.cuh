@@ -35,14 +35,16 @@ struct __align__(32) D4 {
 struct Ctl {
     int status;          // first error of the current opal_step call (0 = ok)
     int detail;          // body or group index that raised it
-    int ncand;           // pairs passing the FP32 bounds (this step)
+    // counters of the current step: zeroed together at its start, from ncand
+    // up to steps_done
+    int ncand;           // pairs passing both FP32 bounds (this step)
+    int nnear;           // pairs passing the FP32 midpoint test (this step)
     int nflag;           // flagged pairs (this step)
     int ngroups;         // encounter groups (this step)
     int ninvolved;       // bodies in groups (this step)
     int nmerge;          // mergers (this step)
     int kepler_max;      // largest drift iteration count (this step)
     int nlarge;          // groups too large for one warp (this step)
-    int pad0;
     unsigned long long nsub;  // BS substeps (this step)
     long long steps_done;
     int cand_overflow;   // candidates lost to a full candidate list (forces a status)
@@ -122,6 +124,7 @@ struct Dev {
     float* tbox;                        // [ntot / 64][6] tile boxes of c +- s
     int ncell;                          // buckets: 2 per body slot
     // encounter pipeline
+    int2* near;  int64_t near_cap;      // pairs passing the midpoint test
     int2* cand;  int64_t cand_cap;      // FP32-bound candidates
     int2* flag;  int64_t flag_cap;      // flagged pairs
     int32_t* label;                     // per body; -1 when not in a group
