@@ -132,9 +132,18 @@ void build_kick_items(opal_sim* s, int slots) {
         const int64_t itiles = si.cap / kPad;
         const double w_tile = (double)kPad * (double)si.n;
         int64_t nchunk = (int64_t)std::llround(w_tile / target);
-        // a single system: make the item count a whole multiple of the grid
-        if (s->sys.size() == 1) nchunk = std::max<int64_t>(1, (slots + itiles - 1) / itiles);
-        nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, std::max<int64_t>(1, si.n / 64)));
+        const int64_t cmax = std::max<int64_t>(1, si.n / 64);
+        if (s->sys.size() == 1) {
+            // a single system: the chunk count whose items finish together.  A block runs
+            // ceil(items / slots) items of 1/c of a row each; take the c with the least such
+            // time, or the smallest c within 2% of it (fewer partial rows to reduce).
+            auto span = [&](int64_t c) { return (double)((itiles * c + slots - 1) / slots) / (double)c; };
+            double best = 1e300;
+            for (int64_t c = 1; c <= std::min<int64_t>(cmax, 256); c++) best = std::min(best, span(c));
+            nchunk = 1;
+            while (span(nchunk) > 1.02 * best) nchunk++;
+        }
+        nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, cmax));
         si.nchunk = (int32_t)nchunk;
         si.slot0 = slot;
         slot += nchunk * si.cap;
