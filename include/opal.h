@@ -116,6 +116,39 @@ opal_status opal_get_state(const opal_sim* sim, int32_t sys, int64_t* n_alive, i
 opal_status opal_energy_momentum(const opal_sim* sim, int32_t sys, double* E, double L[3],
                                  double P[3], double* E_merged_lost);
 
+/* Energy E, angular momentum L and momentum P of one system given in
+ * caller-owned DEVICE arrays, computed the way opal_energy_momentum does it
+ * (democratic heliocentric variables, FP64, fixed-order sums), without
+ * allocating anything.  The paper has no counterpart: this is a diagnostic
+ * for callers that cannot allocate device memory at the point of the check.
+ * Those are callers whose device memory is all held by another allocator
+ * (a caching allocator that has reserved the GPU's HBM), and callers that
+ * must not synchronize the device while steps are in flight (cudaMalloc
+ * and cudaFree may synchronize; this call only enqueues two kernels).
+ *   n          bodies, 0 <= n <= 131072; a larger n returns OPAL_EINVAL and
+ *              launches nothing (the scratch is a fixed 1024 x 13 doubles
+ *              in device memory, one row per 128-body block).
+ *   G, M0      as in opal_params (finite, > 0).
+ *   m[n], x[3n], v[3n]   masses, heliocentric positions and heliocentric
+ *              velocities (row-major n x 3), device memory of the current
+ *              device (or managed), 8-byte aligned; borrowed, not kept.
+ *              Bodies with m = 0 contribute nothing.
+ *   out[7]     device memory: E, L[3], P[3], written by the second kernel.
+ *   stream     cudaStream_t the kernels go on (NULL: the legacy stream).
+ * The call returns once the kernels are enqueued: synchronize the stream
+ * before reading out.  Nothing has to be zeroed first: out and every
+ * scratch row the call reads are written by the same call.
+ * The first call on each device looks up the scratch's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture begins.  All calls on a device share the one
+ * scratch array, so two calls in flight at once (other streams or other
+ * host threads) race and may return wrong values: serialize them.
+ * Errors: OPAL_EINVAL (n out of range, G or M0 invalid, a NULL, misaligned
+ * or host pointer), OPAL_ECUDA (symbol lookup or launch failed); the
+ * reason is in opal_last_error(NULL). */
+opal_status opal_energy_momentum_noalloc(int64_t n, double G, double M0, const double* m, const double* x,
+                                         const double* v, double* out, void* stream);
+
 /* Counters of the last completed step, summed over systems:
  * out[0] flagged pairs, out[1] groups, out[2] mergers, out[3] BS substeps,
  * out[4] pairs that reached the exact minimum-separation test,

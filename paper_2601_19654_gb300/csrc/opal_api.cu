@@ -37,6 +37,17 @@ void set_err(char* buf, const char* fmt, ...) {
     if (buf != g_err) std::memcpy(g_err, buf, 512);
 }
 
+}  // namespace
+
+void opal::set_thread_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+namespace {
+
 const char* status_name(int s) {
     switch (s) {
         case kOk: return "ok";

@@ -338,6 +338,9 @@ int kick_occupancy(int precision, int variant);
 void launch_close(const Dev& d, cudaStream_t s);
 void launch_first_accel_finish(const Dev& d, cudaStream_t s);
 void launch_finish(const Dev& d, cudaStream_t s);
+// Record a one-line reason as the calling thread's last error (opal_last_error(NULL)).
+void set_thread_error(const char* fmt, ...);
+
 void launch_energy(const Dev& d, const PairTile* tiles, int64_t ntiles, const int64_t* tile_off,
                    double* pair_part, double* body_part, double* out, int grid, cudaStream_t s);
 void launch_export(const Dev& d, double* v_helio, cudaStream_t s);

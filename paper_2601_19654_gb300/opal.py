@@ -78,9 +78,10 @@ def _declare(L):
                                   C.POINTER(C.c_int64)]
     L.opal_debug_bs_group.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, _I32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]
+    L.opal_energy_momentum_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, _P, _P, _P, _P, _P]
     for name in ("opal_create", "opal_ensemble_create", "opal_step", "opal_step_async", "opal_wait", "opal_get_state", "opal_energy_momentum",
                  "opal_last_step_stats", "opal_profile_steps", "opal_debug_accel", "opal_debug_drift",
-                 "opal_debug_scan", "opal_debug_bs_group"):
+                 "opal_debug_scan", "opal_debug_bs_group", "opal_energy_momentum_noalloc"):
         getattr(L, name).restype = C.c_int
 
 
@@ -103,6 +104,14 @@ def _check(st, sim_ptr=None):
     if st != OK:
         msg = lib().opal_last_error(sim_ptr)
         raise OpalError(st, msg.decode() if msg else "")
+
+
+def energy_momentum_noalloc(n: int, G: float, M0: float, m_ptr: int, x_ptr: int, v_ptr: int, out_ptr: int,
+                            stream: int = 0) -> None:
+    """opal_energy_momentum_noalloc on device pointers (raw addresses): E, L, P
+    of one system into out_ptr[7], enqueued on stream; nothing is allocated."""
+    _check(lib().opal_energy_momentum_noalloc(int(n), float(G), float(M0), m_ptr, x_ptr, v_ptr, out_ptr,
+                                              stream or None))
 
 
 def default_params(**kw) -> Params:
