@@ -37,31 +37,6 @@ __device__ void system_momentum(const Dev& d, const double* part, const SysInfo&
     __syncthreads();
 }
 
-// Fixed-order reduction of 3 values over a block of kBodyThreads threads into
-// kBodyThreads / kSeg segments: out[c][seg] for each 64-body half.
-__device__ void segment_sums(const Dev& d, int64_t first_body, double vx, double vy, double vz, double* part) {
-    __shared__ double buf[3][kBodyThreads];
-    buf[0][threadIdx.x] = vx;
-    buf[1][threadIdx.x] = vy;
-    buf[2][threadIdx.x] = vz;
-    __syncthreads();
-    for (int w = kSeg / 2; w >= 1; w >>= 1) {
-        int t = threadIdx.x % kSeg;
-        if (t < w) {
-            buf[0][threadIdx.x] += buf[0][threadIdx.x + w];
-            buf[1][threadIdx.x] += buf[1][threadIdx.x + w];
-            buf[2][threadIdx.x] += buf[2][threadIdx.x + w];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x % kSeg == 0) {
-        int64_t sg = (first_body + threadIdx.x) / kSeg;
-        part[sg] = buf[0][threadIdx.x];
-        part[d.nseg_tot + sg] = buf[1][threadIdx.x];
-        part[2 * d.nseg_tot + sg] = buf[2][threadIdx.x];
-    }
-}
-
 // box of the path midpoints of the system's live bodies (block-reduced,
 // then one atomic per block and bound)
 __device__ void note_box(const Dev& d, int s, int64_t b) {
@@ -249,12 +224,48 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     if (!first) system_momentum(d, d.pP_close, si, P);
     const double half = 0.5 * d.p.dt, G = d.p.G;
     const int64_t local = b - si.off;
+    // the kick's partial rows, summed in row order; eight rows' loads are
+    // issued together so their latencies overlap
     double ax = 0, ay = 0, az = 0;
-    for (int c = 0; c < si.nchunk; c++) {
-        int64_t slot = si.slot0 + (int64_t)c * si.cap + local;
+    int c = 0;
+    for (; c + 8 <= si.nchunk; c += 8) {
+        double bx[8], by[8], bz[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int64_t slot = si.slot0 + (int64_t)(c + u) * si.cap + local;
+            bx[u] = d.pacc_x[slot];
+            by[u] = d.pacc_y[slot];
+            bz[u] = d.pacc_z[slot];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            ax += bx[u];
+            ay += by[u];
+            az += bz[u];
+        }
+    }
+    for (; c < si.nchunk; c++) {
+        const int64_t slot = si.slot0 + (int64_t)c * si.cap + local;
         ax += d.pacc_x[slot];
         ay += d.pacc_y[slot];
         az += d.pacc_z[slot];
+    }
+    // after encounters: a member's row was recomputed at its new place, every
+    // other body's row gets the members' old terms swapped for new ones
+    if (!first && d.ctl->ninvolved > 0) {
+        const bool member = d.label[b] >= 0;
+        if (member) d.label[b] = -1;
+        if (d.alive[b]) {
+            if (member) {
+                ax = d.cfx[b];
+                ay = d.cfy[b];
+                az = d.cfz[b];
+            } else {
+                ax += d.cfx[b];
+                ay += d.cfy[b];
+                az += d.cfz[b];
+            }
+        }
     }
     ax *= G;
     ay *= G;
@@ -384,7 +395,19 @@ __global__ void __launch_bounds__(kBodyThreads) k_debug_scan_prep(Dev d) {
     note_box(d, s, b);   // every thread of the block, from this one call site
 }
 
+// create time: sort keys from the current positions, so that the first kicks
+// already run on a spatially sorted body order
+__global__ void __launch_bounds__(kBodyThreads) k_order_prep(Dev d) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
+    if (d.alive[b]) d.cen[b] = make_float4((float)d.x[b], (float)d.y[b], (float)d.z[b], 0.0f);
+    note_box(d, s, b);   // every thread of the block, from this one call site
+}
+
 // ---------------------------------------------------------------------------
+void launch_order_prep(const Dev& d, cudaStream_t s) {
+    k_order_prep<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d);
+}
 void launch_debug_drift(int n, double mu, double dt, int max_iter, double* x, double* v, int* iters, cudaStream_t s) {
     k_debug_drift<<<(n + 127) / 128, 128, 0, s>>>(n, mu, dt, max_iter, x, v, iters);
 }

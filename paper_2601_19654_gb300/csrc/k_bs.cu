@@ -49,8 +49,13 @@ struct BsSh {
     double y[6][M];                     // current state, component-major: X, Y, Z, VX, VY, VZ
     double pos[A][kBsRows][3][M];       // positions of each sequence's evaluation in progress
     double row[A][kBsRows][6][M];       // the last extrapolated row of each member
+    double diag[A][kBsRows][6][M];      // T[k][k] of every finished row (the accepted one is kept)
+    double raw[A][6][M];                // midpoint result of the sequence finishing this round
+    double df2[A][6][M], cur2[A][6][M]; // per component: squared change and squared value
     double err[A][kBsRows][M];          // squared error ratio of each member, per finished row
     double m[M], R[M], rc[M];
+    // per member: rc^2, 1 / (0.9 rc) and 0.1 rc (a pair uses the member with the larger rc)
+    double prc2[M], pinv[M], pc01[M];
     int alive[M], gid[M];
     int kacc[A];                        // accepted row of each attempt, -1 while none
     int decision, collide, nmerge;
@@ -107,10 +112,21 @@ __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, 
         if (o == b || !S.alive[o]) continue;
         double dx = S.pos[a][k][0][o] - xb, dy = S.pos[a][k][1][o] - yb, dz = S.pos[a][k][2][o] - zb;
         double dr2 = dx * dx + dy * dy + dz * dz;
-        double rcbo = S.rc[b] > S.rc[o] ? S.rc[b] : S.rc[o];
-        if (dr2 >= rcbo * rcbo) continue;   // 1 - K = 0 at or beyond rc
+        const int w = S.rc[b] > S.rc[o] ? b : o;   // rc_bo = max(rc_b, rc_o)
+        if (dr2 >= S.prc2[w]) continue;            // 1 - K = 0 at or beyond rc
         double dri = rsqrt(dr2), dr = dr2 * dri;
-        double wgt = 1.0 - changeover(dr, rcbo, p.changeover);
+        // K as the changeover function computes it, with 1 / (0.9 rc) and 0.1 rc
+        // taken once per group instead of a division per evaluation
+        double K;
+        if (dr >= S.rc[w]) {
+            K = 1.0;
+        } else {
+            const double y = (dr - S.pc01[w]) * S.pinv[w];
+            if (y <= 0.0) K = 0.0;
+            else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
+            else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
+        }
+        const double wgt = 1.0 - K;
         if (wgt == 0.0) continue;
         double t = G * S.m[o] * wgt * (dri * dri * dri);
         ax += t * dx;
@@ -120,11 +136,12 @@ __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, 
 }
 
 template <int NT, int A>
-__global__ void __launch_bounds__(NT, 1) k_bs(Dev d, int small) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int small) {
     using Sh = BsSh<NT, A>;
     constexpr int M = Sh::M;
     constexpr int TA = NT / A;            // threads per attempt
-    __shared__ Sh S;
+    extern __shared__ __align__(16) unsigned char bs_smem[];   // one Sh (dynamic: above the static limit)
+    Sh& S = *reinterpret_cast<Sh*>(bs_smem);
     if (d.ctl->status) return;
     const Params p = d.p;
     const int ng = small ? d.ctl->ngroups : d.ctl->nlarge;
@@ -155,13 +172,17 @@ __global__ void __launch_bounds__(NT, 1) k_bs(Dev d, int small) {
             S.R[tid] = d.R[gb];
             S.rc[tid] = d.rc[gb];
             S.alive[tid] = d.alive[gb];
-            d.undo[3 * (mb + tid)] = d.m[gb];
-            d.undo[3 * (mb + tid) + 1] = d.R[gb];
-            d.undo[3 * (mb + tid) + 2] = (double)d.alive[gb];
         }
         if (tid == 0) {
             S.El = 0.0;
             S.nmerge = 0;
+        }
+        __syncthreads();
+        if (tid < nm) {
+            const double rcp = S.rc[tid];
+            S.prc2[tid] = rcp * rcp;
+            S.pc01[tid] = 0.1 * rcp;
+            S.pinv[tid] = 1.0 / (0.9 * rcp);
         }
         __syncthreads();
         const double dt = p.dt;
@@ -179,7 +200,7 @@ __global__ void __launch_bounds__(NT, 1) k_bs(Dev d, int small) {
             }
             const double Ha = ldexp(H, -a);
             const double h = Ha / n;
-            double za[6], zb[6], diag[6];
+            double za[6], zb[6];
             if (act)
                 for (int c = 0; c < 6; c++) za[c] = zb[c] = S.y[c][b];
             if (lt == 0) S.kacc[a] = -1;
@@ -214,38 +235,50 @@ __global__ void __launch_bounds__(NT, 1) k_bs(Dev d, int small) {
                             zb[c] = znew;
                         }
                     } else {
-                        // sequence k done: raw value, then row k of the tableau
-                        double dsq_x = 0.0, dsq_v = 0.0, nx = 0.0, nv = 0.0;
-                        for (int c = 0; c < 6; c++) {
-                            double cur = 0.5 * (zb[c] + za[c] + h * f[c]);
-                            double prev_col = 0.0;
-                            for (int j = 1; j <= k; j++) {
-                                double up = S.row[a][j - 1][c][b];
-                                S.row[a][j - 1][c][b] = cur;
-                                prev_col = cur;
-                                cur = cur + (cur - up) * kNeville[k][j];
-                            }
-                            S.row[a][k][c][b] = cur;
-                            diag[c] = cur;
-                            if (k >= 1) {
-                                double df = cur - prev_col;
-                                if (c < 3) {
-                                    dsq_x += df * df;
-                                    nx += cur * cur;
-                                } else {
-                                    dsq_v += df * df;
-                                    nv += cur * cur;
-                                }
-                            }
+                        // sequence k done: its midpoint result, extrapolated below
+                        for (int c = 0; c < 6; c++) S.raw[a][c][b] = 0.5 * (zb[c] + za[c] + h * f[c]);
+                    }
+                }
+                if (r >= 2 && (r & 1) == 0) {
+                    // row kr of the tableau, one lane per (component, member) of each
+                    // attempt: the six Neville chains of a member run side by side
+                    const int kr = r / 2 - 1;
+                    __syncthreads();
+                    if (lt < 6 * nm) {
+                        const int c = lt / nm, bb = lt % nm;
+                        double cur = S.raw[a][c][bb];
+                        double prev_col = 0.0;
+                        for (int j = 1; j <= kr; j++) {
+                            const double up = S.row[a][j - 1][c][bb];
+                            S.row[a][j - 1][c][bb] = cur;
+                            prev_col = cur;
+                            cur = cur + (cur - up) * kNeville[kr][j];
                         }
-                        // squared error ratio: (|dX|/|X|)^2 vs (|dV|/|V|)^2, larger one
+                        S.row[a][kr][c][bb] = cur;
+                        S.diag[a][kr][c][bb] = cur;
+                        const double df = cur - prev_col;
+                        S.df2[a][c][bb] = df * df;
+                        S.cur2[a][c][bb] = cur * cur;
+                    }
+                    __syncthreads();
+                    if (lt < nm) {
+                        // squared error ratio: (|dX|/|X|)^2 vs (|dV|/|V|)^2, the larger one
                         double e2 = 0.0;
-                        if (k >= 1 && S.alive[b]) {
+                        if (kr >= 1 && S.alive[lt]) {
+                            double dsq_x = 0.0, dsq_v = 0.0, nx = 0.0, nv = 0.0;
+                            for (int c = 0; c < 3; c++) {
+                                dsq_x += S.df2[a][c][lt];
+                                nx += S.cur2[a][c][lt];
+                            }
+                            for (int c = 3; c < 6; c++) {
+                                dsq_v += S.df2[a][c][lt];
+                                nv += S.cur2[a][c][lt];
+                            }
                             double ex = dsq_x / fmax(nx, 2.3e-308), ev = dsq_v / fmax(nv, 2.3e-308);
                             e2 = ex > ev ? ex : ev;
                             if (!(e2 <= 1.7e308)) e2 = HUGE_VAL;   // NaN counts as not converged
                         }
-                        S.err[a][k][b] = e2;
+                        S.err[a][kr][lt] = e2;
                     }
                 }
                 __syncthreads();
@@ -279,8 +312,7 @@ __global__ void __launch_bounds__(NT, 1) k_bs(Dev d, int small) {
                 const double Hq = ldexp(H, -q);
                 if (q == dec) {
                     const int kacc = S.kacc[q];
-                    if (act && a == q && k == kacc)
-                        for (int c = 0; c < 6; c++) S.y[c][b] = diag[c];
+                    if (a == q && lt < 6 * nm) S.y[lt / nm][lt % nm] = S.diag[q][kacc][lt / nm][lt % nm];
                     const int lastq = (q == 0) ? last0 : 0;
                     t = lastq ? dt : t + Hq;
                     if (tid == 0) S.collide = 0;
@@ -328,17 +360,14 @@ __global__ void __launch_bounds__(NT, 1) k_bs(Dev d, int small) {
             if (tid == 0) set_status(d.ctl, kEbs, g);
             return;
         }
+        // results go to the member's slot of the side buffer; the state itself
+        // is updated after the step's kick, which runs beside this kernel
         if (tid < nm) {
-            int gb = S.gid[tid];
-            double x = S.y[0][tid], y = S.y[1][tid], z = S.y[2][tid];
-            d.x[gb] = x; d.y[gb] = y; d.z[gb] = z;
-            d.vx[gb] = S.y[3][tid]; d.vy[gb] = S.y[4][tid]; d.vz[gb] = S.y[5][tid];
-            d.m[gb] = S.m[tid];
-            d.R[gb] = S.R[tid];
-            d.alive[gb] = S.alive[tid];
-            if (S.alive[tid]) kick_floats(d, gb, x, y, z, S.m[tid], d.rc[gb]);
-            else park_floats(d, gb);
-            d.label[gb] = -1;
+            double* o = d.bsout + (int64_t)kBsOut * (mb + tid);
+            for (int c = 0; c < 6; c++) o[c] = S.y[c][tid];
+            o[6] = S.m[tid];
+            o[7] = S.R[tid];
+            o[8] = (double)S.alive[tid];
         }
         if (tid == 0) {
             d.glost[g] = S.El;
@@ -352,10 +381,25 @@ __global__ void __launch_bounds__(NT, 1) k_bs(Dev d, int small) {
 constexpr int kBsSmallThreads = 128;   // groups of up to 4 members: 4 attempts, one warp each
 constexpr int kBsLargeThreads = 512;   // groups of up to 64 members: one attempt
 
+cudaError_t bs_setup() {
+    cudaError_t e = cudaFuncSetAttribute(k_bs<kBsSmallThreads, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(BsSh<kBsSmallThreads, 4>));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_bs<kBsLargeThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(BsSh<kBsLargeThreads, 1>));
+}
+
+// registers one small-group block holds (the kick leaves room for one per SM)
+int bs_block_regs() {
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, k_bs<kBsSmallThreads, 4>) != cudaSuccess) return 65536;
+    return a.numRegs * kBsSmallThreads;
+}
+
 void launch_bs(const Dev& d, int grid, cudaStream_t s) {
-    k_bs<kBsSmallThreads, 4><<<grid, kBsSmallThreads, 0, s>>>(d, 1);
+    k_bs<kBsSmallThreads, 4><<<grid, kBsSmallThreads, sizeof(BsSh<kBsSmallThreads, 4>), s>>>(d, 1);
     prof_mark("bs: groups <= 4");
-    k_bs<kBsLargeThreads, 1><<<(grid + 15) / 16, kBsLargeThreads, 0, s>>>(d, 0);
+    k_bs<kBsLargeThreads, 1><<<(grid + 15) / 16, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s>>>(d, 0);
     prof_mark("bs: groups > 4");
 }
 

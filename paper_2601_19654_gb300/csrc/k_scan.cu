@@ -130,18 +130,35 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_count(Dev d) {
     atomicAdd(&d.cstart[key], 1);
 }
 
-// exclusive prefix sum of the bucket counts (one block)
+// exclusive prefix sum of the bucket counts (one block): each pass, every
+// thread loads 16 consecutive counts at once (vector loads), the block scans
+// the per-thread sums, and a carry runs from pass to pass
 __global__ void __launch_bounds__(1024) k_sort_prefix(Dev d) {
+    constexpr int PER = 16;
     __shared__ int warp_sum[32];
     __shared__ int carry;
     if (d.ctl->status) return;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < d.ncell; base += 1024) {
-        const int k = base + threadIdx.x;
-        int v = k < d.ncell ? d.cstart[k] : 0;
-        int x = v;
+    for (int base = 0; base < d.ncell; base += 1024 * PER) {
+        const int k0 = base + threadIdx.x * PER;
+        int v[PER];
+        if (k0 + PER <= d.ncell) {
+            const int4* src = reinterpret_cast<const int4*>(d.cstart + k0);
+#pragma unroll
+            for (int u = 0; u < PER / 4; u++) {
+                const int4 q = src[u];
+                v[4 * u] = q.x; v[4 * u + 1] = q.y; v[4 * u + 2] = q.z; v[4 * u + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < PER; u++) v[u] = k0 + u < d.ncell ? d.cstart[k0 + u] : 0;
+        }
+        int sum = 0;
+#pragma unroll
+        for (int u = 0; u < PER; u++) sum += v[u];
+        int x = sum;
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
@@ -157,21 +174,48 @@ __global__ void __launch_bounds__(1024) k_sort_prefix(Dev d) {
             warp_sum[lane] = w;
         }
         __syncthreads();
-        const int excl = carry + x - v + (warp > 0 ? warp_sum[warp - 1] : 0);
-        if (k < d.ncell) d.ccursor[k] = excl;
+        int excl = carry + x - sum + (warp > 0 ? warp_sum[warp - 1] : 0);
+        const int last = excl + sum;
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            if (k0 + u < d.ncell) d.ccursor[k0 + u] = excl;
+            excl += v[u];
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
+        if (threadIdx.x == 1023) carry = last;
         __syncthreads();
     }
 }
 
-// scatter into sorted order and copy each body's midpoint record beside it
+// scatter into the buckets (in whatever order the atomics give)
 __global__ void __launch_bounds__(kBodyThreads) k_sort_scatter(Dev d) {
     if (d.ctl->status) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
-    const int pos = atomicAdd(&d.ccursor[d.ckey[b]], 1);
-    d.csorted[pos] = (int)b;
-    d.cen_sorted[pos] = d.cen[b];
+    const int key = d.ckey[b];
+    const int pos = atomicAdd(&d.ccursor[key], 1);
+    d.cscratch[pos] = make_int2((int)b, d.alive[b] ? key : -1);
+}
+
+// ascending ids within each bucket, so the order (and every sum taken in it)
+// is the same on every run; each body's midpoint record goes beside it.
+// A body's new place is its bucket's start plus the number of bucket mates
+// with smaller ids.  The dead bodies' bucket (last of each system) keeps its
+// order: it follows every live body, and dead bodies add nothing to any sum.
+__global__ void __launch_bounds__(kBodyThreads) k_sort_order(Dev d) {
+    if (d.ctl->status) return;
+    const int64_t p = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
+    const int2 bk = d.cscratch[p];   // (body, bucket; -1 for a dead body)
+    const int b = bk.x;
+    int64_t out = p;
+    if (bk.y >= 0) {
+        const int e = d.ccursor[bk.y], s = e - d.cstart[bk.y];
+        int rank = 0;
+#pragma unroll 4
+        for (int q = s; q < e; q++) rank += d.cscratch[q].x < b ? 1 : 0;
+        out = s + rank;
+    }
+    d.csorted[out] = b;
+    d.cen_sorted[out] = d.cen[b];
 }
 
 // box of c +- s over the live bodies of each 64-body tile of the sorted order
@@ -307,50 +351,36 @@ __device__ __forceinline__ double dot3p(const double* a, const double* b) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
-// Minimum of |d(s)|^2: the ends and every local minimum inside (a - to +
-// sign change of g = d.d' on 16 intervals, refined by bracketed Newton on g).
-// The minimum over the intervals does not depend on the order they are
-// visited in; the lanes of a warp refine their intervals together.
-__device__ double min_sep2(double T, const double* d0, const double* u0, const double* d1, const double* u1) {
-    double D = dot3p(d0, d0);
-    double D1 = dot3p(d1, d1);
-    if (D1 < D) D = D1;
+// Stage 3, 16 lanes per candidate pair: lane k looks at interval k of the
+// 16, evaluating d.d' at its two ends exactly as the sequential scan does,
+// and refines its bracket when the sign changes from - to +; the minimum over
+// the ends and the lanes' interior minima is the sequential result (a
+// minimum does not depend on the order its terms are visited in).
+__device__ double interval_min2(double T, int k, const double* d0, const double* u0, const double* d1,
+                                const double* u1) {
     double dd[3], dp[3], d2[3];
-    hermite_rel(0.0, T, d0, u0, d1, u1, dd, dp, d2);
-    double ga = dot3p(dd, dp);
-    unsigned mask = 0;
-    for (int k = 0; k < 16; k++) {
-        double sb = (k + 1) / 16.0;
-        hermite_rel(sb, T, d0, u0, d1, u1, dd, dp, d2);
-        double gb = dot3p(dd, dp);
-        if (ga < 0.0 && gb >= 0.0) mask |= 1u << k;
-        ga = gb;
+    hermite_rel(k / 16.0, T, d0, u0, d1, u1, dd, dp, d2);
+    const double ga = dot3p(dd, dp);
+    hermite_rel((k + 1) / 16.0, T, d0, u0, d1, u1, dd, dp, d2);
+    const double gb = dot3p(dd, dp);
+    if (!(ga < 0.0 && gb >= 0.0)) return HUGE_VAL;
+    double lo = k / 16.0, hi = (k + 1) / 16.0, s = 0.5 * (lo + hi);
+    for (int it = 0; it < 60; it++) {
+        hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
+        double g = dot3p(dd, dp), gp = dot3p(dp, dp) + dot3p(dd, d2);
+        if (g < 0.0) lo = s;
+        else hi = s;
+        double sn = s - g / gp;
+        if (!(gp > 0.0 && sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+        double step = sn - s;
+        s = sn;
+        if (fabs(step) <= 1e-12) break;
     }
-    while (__any_sync(__activemask(), mask != 0)) {
-        if (mask) {
-            int k = __ffs(mask) - 1;
-            mask &= mask - 1;
-            double lo = k / 16.0, hi = (k + 1) / 16.0, s = 0.5 * (lo + hi);
-            for (int it = 0; it < 60; it++) {
-                hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
-                double g = dot3p(dd, dp), gp = dot3p(dp, dp) + dot3p(dd, d2);
-                if (g < 0.0) lo = s;
-                else hi = s;
-                double sn = s - g / gp;
-                if (!(gp > 0.0 && sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
-                double step = sn - s;
-                s = sn;
-                if (fabs(step) <= 1e-12) break;
-            }
-            hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
-            double Dm = dot3p(dd, dd);
-            if (Dm < D) D = Dm;
-        }
-    }
-    return D;
+    hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
+    return dot3p(dd, dd);
 }
 
-__global__ void k_confirm(Dev d) {
+__global__ void __launch_bounds__(256) k_confirm(Dev d) {
     if (d.ctl->status) return;
     const int ncand = d.ctl->ncand;
     if (ncand > d.cand_cap) {
@@ -358,17 +388,33 @@ __global__ void k_confirm(Dev d) {
         return;
     }
     const double T = d.p.dt;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncand; k += gridDim.x * blockDim.x) {
-        const int2 pr = d.cand[k];
-        const int i = pr.x, j = pr.y;
-        if (!d.alive[i] || !d.alive[j]) continue;
-        double d0[3] = {d.x0[j] - d.x0[i], d.y0[j] - d.y0[i], d.z0[j] - d.z0[i]};
-        double u0[3] = {d.vx0[j] - d.vx0[i], d.vy0[j] - d.vy0[i], d.vz0[j] - d.vz0[i]};
-        double d1[3] = {d.x[j] - d.x[i], d.y[j] - d.y[i], d.z[j] - d.z[i]};
-        double u1[3] = {d.vx[j] - d.vx[i], d.vy[j] - d.vy[i], d.vz[j] - d.vz[i]};
-        double rcij = fmax(d.rc[i], d.rc[j]);
-        double D = min_sep2(T, d0, u0, d1, u1);
-        if (D <= rcij * rcij) {
+    const int lane = threadIdx.x & 31, sub = lane & 15;
+    const unsigned half = 0xffffu << (lane & 16);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the two halves of a warp take two pairs; every lane runs every pass
+    for (int64_t kk = 2 * warp; kk < ncand; kk += 2 * nwarp) {
+        const int64_t k = kk + (lane >> 4);
+        bool live = k < ncand;
+        int2 pr = make_int2(0, 0);
+        if (live) {
+            pr = d.cand[k];
+            live = d.alive[pr.x] && d.alive[pr.y];
+        }
+        double D = HUGE_VAL, rcij = 0.0;
+        if (live) {
+            const int i = pr.x, j = pr.y;
+            double d0[3] = {d.x0[j] - d.x0[i], d.y0[j] - d.y0[i], d.z0[j] - d.z0[i]};
+            double u0[3] = {d.vx0[j] - d.vx0[i], d.vy0[j] - d.vy0[i], d.vz0[j] - d.vz0[i]};
+            double d1[3] = {d.x[j] - d.x[i], d.y[j] - d.y[i], d.z[j] - d.z[i]};
+            double u1[3] = {d.vx[j] - d.vx[i], d.vy[j] - d.vy[i], d.vz[j] - d.vz[i]};
+            rcij = fmax(d.rc[i], d.rc[j]);
+            D = fmin(dot3p(d0, d0), dot3p(d1, d1));
+            D = fmin(D, interval_min2(T, sub, d0, u0, d1, u1));
+        }
+#pragma unroll
+        for (int o = 8; o >= 1; o >>= 1) D = fmin(D, __shfl_xor_sync(half, D, o));
+        if (live && sub == 0 && D <= rcij * rcij) {
             int idx = atomicAdd(&d.ctl->nflag, 1);
             if (idx < d.flag_cap) d.flag[idx] = pr;
             else set_status(d.ctl, kEoverflow, -2);
@@ -511,7 +557,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(Dev d) {
     for (int k = threadIdx.x; k < total_u; k += blockDim.x) d.undo[3 * k + 2] = -1.0;
 }
 
-void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s) {
+void launch_sort_bodies(const Dev& d, cudaStream_t s) {
     const unsigned nb = (unsigned)(d.ntot / kBodyThreads);
     k_sort_count<<<nb, kBodyThreads, 0, s>>>(d);
     prof_mark("scan: sort count");
@@ -519,6 +565,12 @@ void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, 
     prof_mark("scan: sort prefix");
     k_sort_scatter<<<nb, kBodyThreads, 0, s>>>(d);
     prof_mark("scan: sort scatter");
+    k_sort_order<<<nb, kBodyThreads, 0, s>>>(d);
+    prof_mark("scan: sort order");
+}
+
+void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s) {
+    launch_sort_bodies(d, s);
     k_tile_box<<<(unsigned)(d.ntot / kSeg), kSeg, 0, s>>>(d);
     prof_mark("scan: tile boxes");
     k_scan_tiles<<<grid, kSeg, 0, s>>>(d, tiles, ntiles);

@@ -69,6 +69,8 @@ struct opal_sim {
     int dev = 0;
     int nsm = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;             // the kick's branch of the step graph
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<SysInfo> sys;
@@ -130,41 +132,34 @@ bool finite_all(const double* a, int64_t n) {
     return true;
 }
 
-// The kick's work list: 128-body i-tiles against j-chunks of the real bodies,
-// chunk counts chosen so the items fill the persistent grid evenly.
-void build_kick_items(opal_sim* s, int slots) {
+// The kick's work list: i-tiles of itile bodies against j-chunks of the system's
+// first n places, chunk edges on whole j-tiles.  The kick takes items from a
+// queue, largest first; about eight items per resident block keep the tail
+// short.  Chunks of one system are of equal length to within a tile.
+void build_kick_items(opal_sim* s, int slots, int itile) {
     double work = 0;
     for (auto& si : s->sys) work += (double)si.cap * (double)si.n;
-    const double target = std::max(1.0, work / std::max(1, slots));
+    const double target = std::max(1.0, work / (8.0 * std::max(1, slots)));
     s->items.clear();
     int64_t slot = 0;
     for (size_t k = 0; k < s->sys.size(); k++) {
         SysInfo& si = s->sys[k];
-        const int64_t itiles = si.cap / kPad;
-        const double w_tile = (double)kPad * (double)si.n;
+        const int64_t itiles = si.cap / itile;
+        const int64_t jtiles = (si.n + kKickJTile - 1) / kKickJTile;
+        const double w_tile = (double)itile * (double)si.n;
         int64_t nchunk = (int64_t)std::llround(w_tile / target);
-        const int64_t cmax = std::max<int64_t>(1, si.n / 64);
-        if (s->sys.size() == 1) {
-            // a single system: the chunk count whose items finish together.  A block runs
-            // ceil(items / slots) items of 1/c of a row each; take the c with the least such
-            // time, or the smallest c within 2% of it (fewer partial rows to reduce).
-            auto span = [&](int64_t c) { return (double)((itiles * c + slots - 1) / slots) / (double)c; };
-            double best = 1e300;
-            for (int64_t c = 1; c <= std::min<int64_t>(cmax, 256); c++) best = std::min(best, span(c));
-            nchunk = 1;
-            while (span(nchunk) > 1.02 * best) nchunk++;
-        }
-        nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, cmax));
+        nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, jtiles));
         si.nchunk = (int32_t)nchunk;
         si.slot0 = slot;
         slot += nchunk * si.cap;
         for (int64_t c = 0; c < nchunk; c++) {
-            int64_t j0 = si.off + (si.n * c) / nchunk, j1 = si.off + (si.n * (c + 1)) / nchunk;
+            const int64_t t0 = jtiles * c / nchunk, t1 = jtiles * (c + 1) / nchunk;
+            const int64_t j0 = si.off + t0 * kKickJTile, j1 = si.off + std::min(si.n, t1 * kKickJTile);
             for (int64_t t = 0; t < itiles; t++) {
                 KickItem it{};
                 it.sys = (int32_t)k;
                 it.chunk = (int32_t)c;
-                it.i0 = si.off + t * kPad;
+                it.i0 = si.off + t * itile;
                 it.j0 = j0;
                 it.j1 = j1;
                 s->items.push_back(it);
@@ -209,6 +204,8 @@ opal_status validate(const opal_params* p, char* err) {
 }
 
 opal_status capture_graph(opal_sim* s);
+
+void reset_scan_order(opal_sim* s);
 
 opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, const double* m, const double* x,
                         const double* v, const double* R, opal_sim** out) {
@@ -255,7 +252,11 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     CKF(cudaGetDevice(&s->dev));
     CKF(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
     CKF(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    CKF(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+    CKF(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
+    CKF(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
     CKF(group_setup());
+    CKF(bs_setup());
 
     // parameters
     Params& P = s->d.p;
@@ -292,7 +293,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     int64_t max_slots = 0;
     for (int v = 0; v < nvar; v++) {
         int occ = std::max(1, kick_occupancy(p->precision, v));
-        build_kick_items(s, s->nsm * occ);
+        build_kick_items(s, s->nsm * occ, kick_itile(p->precision, v));
         var_items[v] = s->items;
         var_sys[v] = s->sys;
         var_grid[v] = (int)std::min<int64_t>((int64_t)s->items.size(), (int64_t)s->nsm * occ);
@@ -323,6 +324,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.cstart, d.ncell));
     TRYF(dalloc(s, &d.ccursor, d.ncell));
     TRYF(dalloc(s, &d.csorted, N));
+    TRYF(dalloc(s, &d.cscratch, N));
     TRYF(dalloc(s, &d.cen_sorted, N));
     TRYF(dalloc(s, &d.tbox, 6 * (N / kSeg)));
     TRYF(dalloc(s, &d.rcmax, nsys));
@@ -342,6 +344,18 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.glarge, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.glost, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.undo, 3 * (2 * d.flag_cap + 2)));
+    {
+        const int64_t mcap = std::min<int64_t>(2 * d.flag_cap + 2, N + 2);   // members are distinct bodies
+        TRYF(dalloc(s, &d.bsout, kBsOut * mcap));
+        TRYF(dalloc(s, &d.okh, mcap));
+        TRYF(dalloc(s, &d.okl, mcap));
+        TRYF(dalloc(s, &d.okx, mcap));
+    }
+    TRYF(dalloc(s, &d.mlo, nsys));
+    TRYF(dalloc(s, &d.mhi, nsys));
+    TRYF(dalloc(s, &d.cfx, N));
+    TRYF(dalloc(s, &d.cfy, N));
+    TRYF(dalloc(s, &d.cfz, N));
     TRYF(dalloc(s, &d.E_lost, nsys));
     TRYF(dalloc(s, &d.ctl, 1));
     TRYF(dalloc(s, &d.sys, nsys));
@@ -397,9 +411,13 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     CKF(up(d.sys, var_sys[0].data(), nsys * sizeof(SysInfo)));
     launch_to_dh(d, s->stream);
     launch_prime(d, s->stream);
+    // a spatially sorted body order for the kick (each step's scan sorts again)
+    reset_scan_order(s);
+    launch_order_prep(d, s->stream);
+    launch_sort_bodies(d, s->stream);
     // pick the kick variant: timed on this simulation's own positions
     {
-        int best = p->precision == 1 ? 1 : 0;
+        int best = 0;
         const char* force = getenv("OPAL_KICK_VARIANT");
         double work = 0;
         for (auto& si : s->sys) work += (double)si.cap * (double)si.n;
@@ -433,7 +451,14 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         s->kick_variant = best;
         s->items = var_items[best];
         s->sys = var_sys[best];
-        s->kick_grid = var_grid[best];
+        // the kick runs beside the encounter integrator: leave each SM room for one of its blocks
+        {
+            const int occ = std::max(1, kick_occupancy(p->precision, best));
+            const int kr = std::max(1, kick_block_regs(p->precision, best));
+            const int room = (bs_block_regs() + kr - 1) / kr;
+            s->kick_grid = (int)std::min<int64_t>((int64_t)var_items[best].size(),
+                                                  (int64_t)s->nsm * std::max(1, occ - room));
+        }
         snprintf(s->kick_desc, sizeof(s->kick_desc), "%s, grid %d, %zu items, %d j-chunks (system 0)%s",
                  kick_variant_name(p->precision, best), s->kick_grid, s->items.size(), s->sys[0].nchunk,
                  force ? ", forced" : (best_ms >= 0 ? ", autotuned" : ""));
@@ -468,32 +493,38 @@ void reset_scan_order(opal_sim* s) {
 
 // the kernels of one step, in order; names for profiling
 const char* kKernelNames[] = {"counters", "open(kick+jump+drift)", "scan", "confirm", "group", "bs", "kick",
-                              "close(jump+kick)", "finish"};
-constexpr int kNumKernels = 9;
+                              "kick fix", "close(jump+kick)", "finish"};
+constexpr int kNumKernels = 10;
+constexpr int kStageBs = 5, kStageKick = 6;
 
-void launch_stage(opal_sim* s, int k) {
+// stage k of a step on stream st (the kick does not read what the BS writes,
+// so the two may run at once)
+void launch_stage(opal_sim* s, int k, cudaStream_t st) {
     const Dev& d = s->d;
     switch (k) {
         case 0:
             cudaMemsetAsync(reinterpret_cast<char*>(d.ctl) + offsetof(Ctl, ncand), 0,
-                            offsetof(Ctl, steps_done) - offsetof(Ctl, ncand), s->stream);
-            cudaMemsetAsync(d.rcmax, 0, d.nsys * sizeof(float), s->stream);
+                            offsetof(Ctl, steps_done) - offsetof(Ctl, ncand), st);
+            cudaMemsetAsync(d.rcmax, 0, d.nsys * sizeof(float), st);
+            cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), st);
+            cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), st);
             reset_scan_order(s);
             prof_mark("memsets");
             break;
-        case 1: launch_open(d, s->stream); break;
-        case 2: launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, s->stream); break;
-        case 3: launch_confirm(d, s->confirm_grid, s->stream); break;
-        case 4: launch_group(d, s->stream); break;
-        case 5: launch_bs(d, s->bs_grid, s->stream); break;
-        case 6:
-            launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant,
-                        s->stream);
+        case 1: launch_open(d, st); break;
+        case 2: launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, st); break;
+        case 3: launch_confirm(d, s->confirm_grid, st); break;
+        case 4: launch_group(d, st); break;
+        case kStageBs: launch_bs(d, s->bs_grid, st); break;
+        case kStageKick:
+            launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
             break;
-        case 7: launch_close(d, s->stream); break;
-        case 8: launch_finish(d, s->stream); break;
+        case 7: launch_kick_fix(d, s->nsm, st); break;
+        case 8: launch_close(d, st); break;
+        case 9: launch_finish(d, st); break;
     }
 }
+void launch_stage(opal_sim* s, int k) { launch_stage(s, k, s->stream); }
 
 opal_status capture_graph(opal_sim* s) {
     if (s->exec) {
@@ -506,9 +537,20 @@ opal_status capture_graph(opal_sim* s) {
     }
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < kNumKernels; k++) {
-        if (s->time_kick && k == 6) cudaEventRecordWithFlags(s->kick_ev[0], s->stream, cudaEventRecordExternal);
+        if (k == kStageKick) continue;
+        if (k == kStageBs) {
+            // fork: the kick on the side stream, the encounter integrator here; join before the fix
+            CK(cudaEventRecord(s->fork_ev, s->stream));
+            CK(cudaStreamWaitEvent(s->side, s->fork_ev, 0));
+            if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[0], s->side, cudaEventRecordExternal);
+            launch_stage(s, kStageKick, s->side);
+            if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[1], s->side, cudaEventRecordExternal);
+            CK(cudaEventRecord(s->join_ev, s->side));
+            launch_stage(s, kStageBs, s->stream);
+            CK(cudaStreamWaitEvent(s->stream, s->join_ev, 0));
+            continue;
+        }
         launch_stage(s, k);
-        if (s->time_kick && k == 6) cudaEventRecordWithFlags(s->kick_ev[1], s->stream, cudaEventRecordExternal);
     }
     cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
     if (e != cudaSuccess) {
@@ -742,12 +784,16 @@ double opal_last_kick_ms(const opal_sim* cs) {
 void opal_destroy(opal_sim* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->side) cudaStreamSynchronize(s->side);
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     for (auto e : s->kick_ev)
         if (e) cudaEventDestroy(e);
     for (void* p : s->allocs) cudaFree(p);
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+    if (s->join_ev) cudaEventDestroy(s->join_ev);
     delete s;
 }
 
@@ -770,6 +816,7 @@ opal_status opal_debug_accel(opal_sim* s, const double* rc, double* a) {
     CK(cudaMemsetAsync(d.rcmax, 0, d.nsys * 4, s->stream));
     reset_scan_order(s);
     launch_debug_scan_prep(d, s->stream);
+    launch_sort_bodies(d, s->stream);
     launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, s->stream);
     launch_first_accel_finish(d, s->stream);
     CK(cudaGetLastError());
@@ -917,7 +964,10 @@ opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0,
         CK(cudaMemcpy(d.glarge, &zero, sizeof(int), cudaMemcpyHostToDevice));
     }
     CK(cudaMemcpy(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), s->stream));
+    CK(cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), s->stream));
     launch_bs(d, 1, s->stream);
+    launch_kick_fix(d, s->nsm, s->stream);   // puts the result into the state
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));

@@ -13,10 +13,12 @@
 
 namespace opal {
 
-constexpr int kPad = 128;        // body padding of every system (block of the body kernels)
+constexpr int kPad = 256;        // body padding of every system (largest kick i-tile)
 constexpr int kSeg = 64;         // bodies per partial-sum segment
 constexpr int kBodyThreads = 128;
 constexpr int kBsMaxMembers = 64;   // bodies per encounter group
+constexpr int kKickJTile = 256;     // j-bodies the kick stages in shared memory at a time
+constexpr int kBsOut = 9;           // doubles per member slot of the BS side buffer: x, V, m, R, alive
 constexpr int kBsRows = 8;          // extrapolation rows: n_k = 2, 4, ..., 16
 constexpr int kGroupMaxBodies = 4096;   // flagged pairs the grouping kernel takes per step
 constexpr float kFar = 1.0e18f;     // parking coordinate of ghost and dead bodies (float copies)
@@ -49,6 +51,10 @@ struct Ctl {
     long long steps_done;
     int cand_overflow;   // candidates lost to a full candidate list (forces a status)
     int pad;
+    // work queue of the kick: next item, blocks done; the last block out puts
+    // both back to zero, so every launch starts from an empty queue
+    int kick_next;
+    int kick_done;
 };
 
 // Per-system constants.
@@ -119,7 +125,8 @@ struct Dev {
     int* ckey;                          // per body: its bucket
     int* cstart;                        // [ncell] bucket counts
     int* ccursor;                       // [ncell] scatter cursors
-    int* csorted;                       // bodies in sorted order
+    int2* cscratch;                     // (body, bucket or -1 if dead) after the scatter, any order in a bucket
+    int* csorted;                       // bodies in sorted order, ascending ids within a cell
     float4* cen_sorted;                 // their midpoint records, in sorted order
     float* tbox;                        // [ntot / 64][6] tile boxes of c +- s
     int ncell;                          // buckets: 2 per body slot
@@ -133,6 +140,13 @@ struct Dev {
     int32_t* glarge;                    // groups of more than 4 members
     double* glost;                      // per group energy lost to mergers
     double* undo;                       // per member slot: m, R, alive (3 doubles)
+    double* bsout;                      // per member slot: the BS result (kBsOut doubles)
+    float4* okh;                        // per member slot: kh before the BS result was applied
+    float4* okl;                        // per member slot: kl before it
+    D4* okx;                            // per member slot: x, y, z, m before it
+    int* mlo;                           // [nsys] first member slot of the system (or a large value)
+    int* mhi;                           // [nsys] one past its last member slot (or 0)
+    double *cfx, *cfy, *cfz;            // per body: kick correction (others) or full row (members)
     double* E_lost;                     // per system running sum
     Ctl* ctl;
 };
@@ -147,6 +161,32 @@ __device__ __forceinline__ void set_status(Ctl* c, int code, int detail) {
 __device__ __forceinline__ double dot3(double ax, double ay, double az, double bx, double by, double bz) {
     return ax * bx + ay * by + az * bz;
 }
+
+// Fixed-order reduction of 3 values over a block of kBodyThreads threads into
+// kBodyThreads / kSeg segments: out[c][seg] for each 64-body half.
+__device__ __forceinline__ void segment_sums(const Dev& d, int64_t first_body, double vx, double vy, double vz, double* part) {
+    __shared__ double buf[3][kBodyThreads];
+    buf[0][threadIdx.x] = vx;
+    buf[1][threadIdx.x] = vy;
+    buf[2][threadIdx.x] = vz;
+    __syncthreads();
+    for (int w = kSeg / 2; w >= 1; w >>= 1) {
+        int t = threadIdx.x % kSeg;
+        if (t < w) {
+            buf[0][threadIdx.x] += buf[0][threadIdx.x + w];
+            buf[1][threadIdx.x] += buf[1][threadIdx.x + w];
+            buf[2][threadIdx.x] += buf[2][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x % kSeg == 0) {
+        int64_t sg = (first_body + threadIdx.x) / kSeg;
+        part[sg] = buf[0][threadIdx.x];
+        part[d.nseg_tot + sg] = buf[1][threadIdx.x];
+        part[2 * d.nseg_tot + sg] = buf[2][threadIdx.x];
+    }
+}
+
 
 // Changeover weight K(r; rc): the rational form y^2/(2y^2-2y+1) or the
 // quintic 10y^3-15y^4+6y^5, y = (r - 0.1 rc)/(0.9 rc); 1 beyond rc, 0 below 0.1 rc.
@@ -325,16 +365,26 @@ inline void prof_mark(const char* name) {
 void launch_to_dh(const Dev& d, cudaStream_t s);
 void launch_prime(const Dev& d, cudaStream_t s);
 void launch_open(const Dev& d, cudaStream_t s);
+// counting sort of each system's bodies by the cell of cen (csorted); the
+// caller resets the buckets and notes the boxes first
+void launch_sort_bodies(const Dev& d, cudaStream_t s);
+void launch_order_prep(const Dev& d, cudaStream_t s);
 void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s);
 void launch_confirm(const Dev& d, int grid, cudaStream_t s);
 void launch_group(const Dev& d, cudaStream_t s);
 cudaError_t group_setup();
+cudaError_t bs_setup();   // dynamic shared memory of the BS kernels
 void launch_bs(const Dev& d, int grid, cudaStream_t s);
 void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int variant,
                  cudaStream_t s);
+// after the BS (which ran beside the kick): apply its results, fix the kick's rows
+void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s);
 int kick_num_variants(int precision);
 const char* kick_variant_name(int precision, int variant);
 int kick_occupancy(int precision, int variant);
+int kick_block_regs(int precision, int variant);   // registers one block of variant v holds
+int bs_block_regs();
+int kick_itile(int precision, int variant);   // i-bodies per work item (a divisor of kPad)
 void launch_close(const Dev& d, cudaStream_t s);
 void launch_first_accel_finish(const Dev& d, cudaStream_t s);
 void launch_finish(const Dev& d, cudaStream_t s);
