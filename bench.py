@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble vs per-system comparison")
+    ap.add_argument("--ensemble-steps", type=int, default=10)
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args(argv)
 
@@ -187,6 +189,49 @@ def e2e_rate(system, steps: int, precision: int):
                                               "amortised over the steps; state read back every step"}
 
 
+def ensemble_rates(seed: int, steps: int, warmup: int):
+    """The 256-system ensemble (N log-uniform in 64-4096, each drawn like the
+    10-body workload) advanced as one simulation, against the same systems as
+    256 simulations of their own: launched one after another (each step
+    waits), and launched all at once on their own streams (then one wait).
+    All rates are ensemble steps/s (every system advanced one step)."""
+    from paper_2601_19654_gb300 import opal
+    systems = ic.ensemble(seed, 256)
+    ens = opal.Simulation.ensemble(systems, precision=1)
+    E0 = ens.energy()[0]
+    ens.step(warmup)
+    t0 = time.perf_counter()
+    ens.step(steps)
+    t_ens = time.perf_counter() - t0
+    dE = abs(ens.energy()[0] - E0) / abs(E0)
+    st = ens.stats()
+    ens.close()
+    per = [opal.Simulation.from_system(s, precision=1) for s in systems]
+    for sim in per:
+        sim.step(warmup)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for sim in per:
+            sim.step(1)
+    t_serial = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for sim in per:
+            sim.step_async(1)
+    for sim in per:
+        sim.wait()
+    t_async = time.perf_counter() - t0
+    for sim in per:
+        sim.close()
+    r_ens, r_ser, r_asy = steps / t_ens, steps / t_serial, steps / t_async
+    return {"workload": "256 systems, N log-uniform 64-4096 (each like the 10-body workload), mixed form",
+            "bodies": int(sum(s.n for s in systems)), "steps": steps, "warmup": warmup,
+            "ensemble_steps_per_s": r_ens, "per_system_serial_steps_per_s": r_ser,
+            "per_system_streams_steps_per_s": r_asy, "over_serial": r_ens / r_ser,
+            "over_streams": r_ens / r_asy, "dE_over_E": dE, "encounters_last_step": st,
+            "timing": "host clock around opal_step calls (each call ends in a device sync)"}
+
+
 def oracle_rate(system, seconds: float, max_steps: int | None = None):
     import oracle
     oracle.build()
@@ -302,6 +347,8 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0:
         line["e2e"] = e2e_rate(system, max(5, min(args.steps, 50)), precision=1)
+        if not args.no_ensemble:
+            line["ensemble"] = ensemble_rates(args.seed, args.ensemble_steps, 3)
         if not args.no_cpu_baseline:
             v, done, el, threads, dE = oracle_rate(system, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",

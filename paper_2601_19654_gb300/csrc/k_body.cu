@@ -250,12 +250,13 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
         ay += d.pacc_y[slot];
         az += d.pacc_z[slot];
     }
-    // after encounters: a member's row was recomputed at its new place, every
-    // other body's row gets the members' old terms swapped for new ones
+    // after encounters, when the kick ran beside the BS: a member's row was
+    // recomputed at its new place, every other body's row gets the members'
+    // old terms swapped for new ones
     if (!first && d.ctl->ninvolved > 0) {
         const bool member = d.label[b] >= 0;
-        if (member) d.label[b] = -1;
-        if (d.alive[b]) {
+        if (member) d.label[b] = -1;   // in both orders: next step's groups start from no labels
+        if (d.overlap && d.alive[b]) {
             if (member) {
                 ax = d.cfx[b];
                 ay = d.cfy[b];
@@ -295,21 +296,35 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
         d.ax[b] = 0.0; d.ay[b] = 0.0; d.az[b] = 0.0;
     }
     segment_sums(d, (int64_t)blockIdx.x * kBodyThreads, px, py, pz, d.pP_open);
-    if (!first && blockIdx.x == 0 && threadIdx.x < 32) {
-        // energy removed by this step's mergers, per system, in group order;
-        // the warp loads 32 groups at a time and lane 0 adds the nonzero ones
+    if (!first && (int64_t)blockIdx.x * kBodyThreads == si.off && threadIdx.x < 32) {
+        // energy removed by this step's mergers in this system: groups come in
+        // ascending order of their lowest member, so the system's groups are the
+        // run whose lowest member lies in [off, off + cap); one warp sums them in
+        // a fixed order
         const int ng = d.ctl->ngroups;
-        for (int g0 = 0; g0 < ng; g0 += 32) {
-            const int g = g0 + threadIdx.x;
-            const double e = g < ng ? d.glost[g] : 0.0;
-            unsigned mask = __ballot_sync(0xffffffffu, e != 0.0);
-            while (mask) {
-                const int q = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const double eq = __shfl_sync(0xffffffffu, e, q);
-                if (threadIdx.x == 0) d.E_lost[d.body_sys[d.members[d.goff[g0 + q]]]] += eq;
+        int lo = 0, hi = 0;
+        if (threadIdx.x == 0 && ng > 0) {
+            int a = 0, b = ng;
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (d.members[d.goff[mid]] < si.off) a = mid + 1;
+                else b = mid;
             }
+            lo = a;
+            b = ng;
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (d.members[d.goff[mid]] < si.off + si.cap) a = mid + 1;
+                else b = mid;
+            }
+            hi = a;
         }
+        lo = __shfl_sync(0xffffffffu, lo, 0);
+        hi = __shfl_sync(0xffffffffu, hi, 0);
+        double e = 0.0;
+        for (int g = lo + (int)threadIdx.x; g < hi; g += 32) e += d.glost[g];
+        for (int o = 16; o >= 1; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (threadIdx.x == 0 && e != 0.0) d.E_lost[s] += e;
     }
 }
 
@@ -325,17 +340,17 @@ __global__ void k_finish(Dev d) {
         d.x[b] = d.xs[b]; d.y[b] = d.ys[b]; d.z[b] = d.zs[b];
         d.vx[b] = d.vxs[b]; d.vy[b] = d.vys[b]; d.vz[b] = d.vzs[b];
         d.rc[b] = d.rcs[b];
+        d.label[b] = -1;   // the step may have stopped with pairs marked but not grouped
     }
     // masses, radii and flags of group members as they were before the BS
     int nmem = c->ninvolved;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nmem; k += (int64_t)gridDim.x * blockDim.x) {
         int b = d.members[k];
-        if (d.undo[3 * k + 2] >= 0.0) {   // slot written by the BS kernel
+        if (d.undo[3 * k + 2] >= 0.0) {   // slot written when the BS results were applied
             d.m[b] = d.undo[3 * k];
             d.R[b] = d.undo[3 * k + 1];
             d.alive[b] = (int)d.undo[3 * k + 2];
         }
-        d.label[b] = -1;
     }
 }
 

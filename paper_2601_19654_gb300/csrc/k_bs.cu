@@ -28,6 +28,13 @@
 
 namespace opal {
 
+// Few groups (kBsManyGroups or fewer in a step): the lockstep kernels (one
+// block per group, all sequences and four step sizes at once) give each group
+// the shortest chain of dependent operations.  Many groups: the packed kernel
+// (one lane per member, many groups per warp) makes each group's first
+// attempt, the whole step, which settles most of them; the groups it rejects
+// go on to the lockstep kernels, which start them again from the beginning.
+
 // Neville coefficients 1 / ((n_k / n_{k-j})^2 - 1) with n_k = 2(k+1): exact
 // rationals (k-j+1)^2 / ((k+1)^2 - (k-j+1)^2), rounded once.
 __constant__ double kNeville[kBsRows][kBsRows] = {
@@ -62,8 +69,11 @@ struct BsSh {
     double El;
 };
 
-template <int NT, int A>
-__device__ void bs_merge(BsSh<NT, A>& S, const Params& p, int b, int q) {
+// Perfect merger of members b and q of a group held in S (y[6][.], m, R, gid,
+// alive): mass, momentum and centre of mass kept, R = cbrt(R_b^3 + R_q^3),
+// the heavier body (lower id on a tie) survives; El gets the energy removed.
+template <class SH>
+__device__ void bs_merge(SH& S, const Params& p, int b, int q, double& El, int& nmerge) {
     const double G = p.G, M0 = p.M0;
     double mb = S.m[b], mq = S.m[q], M = mb + mq;
     double d[3] = {S.y[0][q] - S.y[0][b], S.y[1][q] - S.y[1][b], S.y[2][q] - S.y[2][b]};
@@ -81,7 +91,7 @@ __device__ void bs_merge(BsSh<NT, A>& S, const Params& p, int b, int q) {
     double vn2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
     double rn = sqrt(xn[0] * xn[0] + xn[1] * xn[1] + xn[2] * xn[2]);
     double e_after = 0.5 * M * vn2 - G * M0 * M / rn;
-    S.El += e_before - e_after;
+    El += e_before - e_after;
     int keep, gone;
     if (mb > mq) keep = b, gone = q;
     else if (mq > mb) keep = q, gone = b;
@@ -95,7 +105,35 @@ __device__ void bs_merge(BsSh<NT, A>& S, const Params& p, int b, int q) {
     S.R[keep] = Rn;
     S.m[gone] = 0.0;
     S.alive[gone] = 0;
-    S.nmerge++;
+    nmerge++;
+}
+
+// (1 - K) weighted attraction of a member at (xb, yb, zb) towards one at
+// (xo, yo, zo) of mass mo, added to (ax, ay, az).  rc, rc2, c01, inv belong to
+// the member with the larger rc (rc_bo = max(rc_b, rc_o)): rc, rc^2, 0.1 rc and
+// 1 / (0.9 rc), so K needs no division by rc.
+__device__ __forceinline__ void bs_pair(const Params& p, double xb, double yb, double zb, double xo, double yo,
+                                        double zo, double mo, double rc, double rc2, double c01, double inv,
+                                        double& ax, double& ay, double& az) {
+    const double dx = xo - xb, dy = yo - yb, dz = zo - zb;
+    const double dr2 = dx * dx + dy * dy + dz * dz;
+    if (dr2 >= rc2) return;   // 1 - K = 0 at or beyond rc
+    const double dri = rsqrt(dr2), dr = dr2 * dri;
+    double K;
+    if (dr >= rc) {
+        K = 1.0;
+    } else {
+        const double y = (dr - c01) * inv;
+        if (y <= 0.0) K = 0.0;
+        else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
+        else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
+    }
+    const double wgt = 1.0 - K;
+    if (wgt == 0.0) return;
+    const double t = p.G * mo * wgt * (dri * dri * dri);
+    ax += t * dx;
+    ay += t * dy;
+    az += t * dz;
 }
 
 // acceleration of member b of sequence k at its position (x, y, z)
@@ -110,28 +148,9 @@ __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, 
     az = s * zb;
     for (int o = 0; o < nm; o++) {
         if (o == b || !S.alive[o]) continue;
-        double dx = S.pos[a][k][0][o] - xb, dy = S.pos[a][k][1][o] - yb, dz = S.pos[a][k][2][o] - zb;
-        double dr2 = dx * dx + dy * dy + dz * dz;
         const int w = S.rc[b] > S.rc[o] ? b : o;   // rc_bo = max(rc_b, rc_o)
-        if (dr2 >= S.prc2[w]) continue;            // 1 - K = 0 at or beyond rc
-        double dri = rsqrt(dr2), dr = dr2 * dri;
-        // K as the changeover function computes it, with 1 / (0.9 rc) and 0.1 rc
-        // taken once per group instead of a division per evaluation
-        double K;
-        if (dr >= S.rc[w]) {
-            K = 1.0;
-        } else {
-            const double y = (dr - S.pc01[w]) * S.pinv[w];
-            if (y <= 0.0) K = 0.0;
-            else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
-            else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
-        }
-        const double wgt = 1.0 - K;
-        if (wgt == 0.0) continue;
-        double t = G * S.m[o] * wgt * (dri * dri * dri);
-        ax += t * dx;
-        ay += t * dy;
-        az += t * dz;
+        bs_pair(p, xb, yb, zb, S.pos[a][k][0][o], S.pos[a][k][1][o], S.pos[a][k][2][o], S.m[o], S.rc[w],
+                S.prc2[w], S.pc01[w], S.pinv[w], ax, ay, az);
     }
 }
 
@@ -144,15 +163,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int small) {
     Sh& S = *reinterpret_cast<Sh*>(bs_smem);
     if (d.ctl->status) return;
     const Params p = d.p;
-    const int ng = small ? d.ctl->ngroups : d.ctl->nlarge;
+    // the groups this kernel takes: few groups: all (small) or the list of those
+    // above 4 members (large); many groups: the list the packed kernel left
+    const bool many = d.ctl->ngroups > kBsManyGroups;
+    const int* list = many ? d.ghard : (small ? nullptr : d.glarge);
+    const int ng = many ? d.ctl->nhard : (small ? d.ctl->ngroups : d.ctl->nlarge);
     const int tid = threadIdx.x;
     const int a = tid / TA, lt = tid % TA;
     const int cap = p.bs_max_substeps;
     const double tol2 = p.bs_tol * p.bs_tol;
     for (int gi = blockIdx.x; gi < ng; gi += gridDim.x) {
-        const int g = small ? gi : d.glarge[gi];
+        const int g = list ? list[gi] : gi;
         const int mb = d.goff[g], nm = d.goff[g + 1] - mb;
         if (small && nm > M) continue;      // handled by the large-group kernel
+        if (!small && nm <= 4) continue;    // handled by the small-group kernel
         if (nm > M) {
             if (tid == 0) set_status(d.ctl, kEoverflow, 1000000 + g);
             return;
@@ -334,7 +358,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int small) {
                                 double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
                                        dz = S.y[2][w] - S.y[2][u];
                                 if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w])
-                                    bs_merge<NT, A>(S, p, u, w);
+                                    bs_merge(S, p, u, w, S.El, S.nmerge);
                             }
                     }
                     __syncthreads();
@@ -378,12 +402,266 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int small) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Many groups: the first attempt of each group (the whole step as one
+// substep), with one lane per member and many groups to a warp; a group whose
+// attempt is rejected goes on the list the lockstep kernels take next.  A warp
+// works through the size classes (groups of at most 16, 8, 4, 2 members) in
+// turn; its lanes form 32 / Wc segments of Wc lanes, and each segment takes
+// groups of the class from a queue, the next one as soon as its group is done.  Every lane runs the same instructions on each pass of the
+// loop: one derivative at the member's evaluation point, then the midpoint
+// step or, at the end of a sequence, its row of the extrapolation tableau and
+// the group's decision.  The sequences n_k run one after another as in the
+// sequential method, so a pass does the work of up to 32 members.  What a
+// group shares (positions for the forces, the error maximum, contacts) goes
+// through shared memory within its segment.
+constexpr int kPkWarps = 2;    // warps per block
+
+struct PkWarp {
+    double row[kBsRows][6][32];          // each lane's extrapolation tableau (in place)
+    double y[6][32];                     // states at a substep's end (contacts, mergers)
+    double px[32], py[32], pz[32];       // positions of the current evaluation
+    double err[32];
+    double m[32], R[32], rc[32], prc2[32], pinv[32], pc01[32];
+    int alive[32], gid[32];
+    int seg_g[16];                       // group each segment took from the queue
+};
+
+__global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
+    extern __shared__ __align__(16) unsigned char pk_smem[];
+    const int lane = threadIdx.x & 31;
+    PkWarp& W = reinterpret_cast<PkWarp*>(pk_smem)[threadIdx.x >> 5];
+    if (d.ctl->status) return;
+    if (d.ctl->ngroups <= kBsManyGroups) return;   // few groups: the lockstep kernels take them
+    const Params p = d.p;
+    const double tol2 = p.bs_tol * p.bs_tol, dt = p.dt, GM0 = p.G * p.M0;
+    const int cap = p.bs_max_substeps;
+    for (int c = 3; c >= 0; c--) {
+        const int Wc = 2 << c;                      // 16, 8, 4, 2 lanes a segment
+        const int nq = d.ctl->ncls[c];
+        const int seg = lane / Wc, sl = lane % Wc, base = seg * Wc;
+        const unsigned segmask = (Wc == 32 ? 0xffffffffu : ((1u << Wc) - 1u)) << base;
+        int g = -1, sz = 0, mslot = 0;
+        double yv[6] = {0, 0, 0, 0, 0, 0}, z0[6] = {0, 0, 0, 0, 0, 0}, z1[6] = {0, 0, 0, 0, 0, 0};
+        double t = 0.0, H = 0.0, El = 0.0;
+        int k = 0, ms = 0, nsub = 0, last = 0, nmerge = 0;
+        bool need = true;
+        for (;;) {
+            // segments that need a group take the next one of the class
+            if (need && sl == 0) {
+                const int q = atomicAdd(&d.ctl->qcls[c], 1);
+                W.seg_g[seg] = q < nq ? d.gcls[c * d.gcap + q] : -1;
+            }
+            __syncwarp();
+            if (need) {
+                need = false;
+                g = W.seg_g[seg];
+                sz = g >= 0 ? d.goff[g + 1] - d.goff[g] : 0;
+                W.alive[lane] = 0;
+                if (sl < sz) {
+                    mslot = d.goff[g] + sl;
+                    const int gb = d.members[mslot];
+                    W.gid[lane] = gb;
+                    yv[0] = d.x0[gb]; yv[1] = d.y0[gb]; yv[2] = d.z0[gb];
+                    yv[3] = d.vx0[gb]; yv[4] = d.vy0[gb]; yv[5] = d.vz0[gb];
+                    W.m[lane] = d.m[gb];
+                    W.R[lane] = d.R[gb];
+                    const double rc = d.rc[gb];
+                    W.rc[lane] = rc;
+                    W.prc2[lane] = rc * rc;
+                    W.pc01[lane] = 0.1 * rc;
+                    W.pinv[lane] = 1.0 / (0.9 * rc);
+                    W.alive[lane] = d.alive[gb];
+                }
+                t = 0.0;
+                H = dt;
+                last = 0;
+                if (fabs(H) >= fabs(dt - t)) {
+                    H = dt - t;
+                    last = 1;
+                }
+                k = 0;
+                ms = 0;
+                nsub = 0;
+                El = 0.0;
+                nmerge = 0;
+            }
+            __syncwarp();
+            const bool active = g >= 0;
+            if (!__any_sync(0xffffffffu, active)) break;   // the class is done for the whole warp
+            const bool live = active && sl < sz;
+            // evaluation point: the substep's start (ms == 0) or the midpoint chain
+            {
+                const bool st = ms == 0;
+                W.px[lane] = st ? yv[0] : z1[0];
+                W.py[lane] = st ? yv[1] : z1[1];
+                W.pz[lane] = st ? yv[2] : z1[2];
+            }
+            __syncwarp();
+            double f[6] = {0, 0, 0, 0, 0, 0};
+            if (live && W.alive[lane]) {
+                const double P0 = W.px[lane], P1 = W.py[lane], P2 = W.pz[lane];
+                const bool st = ms == 0;
+                f[0] = st ? yv[3] : z1[3];
+                f[1] = st ? yv[4] : z1[4];
+                f[2] = st ? yv[5] : z1[5];
+                const double r2 = P0 * P0 + P1 * P1 + P2 * P2, ri = rsqrt(r2);
+                const double sk = -GM0 * (ri * ri * ri);
+                double ax = sk * P0, ay = sk * P1, az = sk * P2;
+                for (int o = base; o < base + Wc; o++) {
+                    if (o == lane || !W.alive[o]) continue;
+                    const int w = W.rc[lane] > W.rc[o] ? lane : o;
+                    bs_pair(p, P0, P1, P2, W.px[o], W.py[o], W.pz[o], W.m[o], W.rc[w], W.prc2[w], W.pc01[w],
+                            W.pinv[w], ax, ay, az);
+                }
+                f[3] = ax;
+                f[4] = ay;
+                f[5] = az;
+            }
+            const int n = 2 * (k + 1);
+            const double h = H / n;
+            const int stage = ms == 0 ? 0 : (ms < n ? 1 : 2);
+            double cur[6] = {0, 0, 0, 0, 0, 0};
+            double e2 = 0.0;
+            if (stage < 2) {
+                // first step z1 = y + h f; then z0 <- z1, z1 <- z0 + 2 h f
+                for (int q = 0; q < 6; q++) {
+                    const double b0 = stage == 0 ? yv[q] : z0[q];
+                    const double zn = b0 + (stage == 0 ? h : 2.0 * h) * f[q];
+                    z0[q] = stage == 0 ? yv[q] : z1[q];
+                    z1[q] = zn;
+                }
+            } else if (live) {
+                double dsq_x = 0.0, dsq_v = 0.0, nx = 0.0, nv = 0.0;
+                for (int q = 0; q < 6; q++) {
+                    double cv = 0.5 * (z1[q] + z0[q] + h * f[q]), pv = 0.0;
+                    for (int j = 1; j <= k; j++) {
+                        const double up = W.row[j - 1][q][lane];
+                        W.row[j - 1][q][lane] = cv;
+                        pv = cv;
+                        cv = cv + (cv - up) * kNeville[k][j];
+                    }
+                    W.row[k][q][lane] = cv;
+                    cur[q] = cv;
+                    const double df = cv - pv;
+                    if (q < 3) {
+                        dsq_x += df * df;
+                        nx += cv * cv;
+                    } else {
+                        dsq_v += df * df;
+                        nv += cv * cv;
+                    }
+                }
+                if (k >= 1 && W.alive[lane]) {
+                    const double ex = dsq_x / fmax(nx, 2.3e-308), ev = dsq_v / fmax(nv, 2.3e-308);
+                    e2 = ex > ev ? ex : ev;
+                    if (!(e2 <= 1.7e308)) e2 = HUGE_VAL;   // NaN counts as not converged
+                }
+            }
+            W.err[lane] = e2;
+            __syncwarp();
+            // 0: on with the sequence, 1: next sequence, 2: accept row k, 3: reject the substep
+            int decision = 0;
+            if (active && stage == 2) {
+                double gerr = 0.0;
+                for (int o = base; o < base + Wc; o++) gerr = fmax(gerr, W.err[o]);
+                const bool acc = k >= 1 && gerr <= tol2;
+                decision = acc ? 2 : (k == kBsRows - 1 ? 3 : 1);
+            }
+            if (decision == 2 && live)
+                for (int q = 0; q < 6; q++) W.y[q][lane] = cur[q];
+            __syncwarp();
+            // contacts after an accepted substep: each lane tests its pairs with
+            // later members; the segment's first lane merges in the sequential order
+            bool touch = false;
+            if (decision == 2 && live && W.alive[lane])
+                for (int o = lane + 1; o < base + sz; o++) {
+                    if (!W.alive[o]) continue;
+                    const double ddx = cur[0] - W.y[0][o], ddy = cur[1] - W.y[1][o], ddz = cur[2] - W.y[2][o];
+                    const double rs = W.R[lane] + W.R[o];
+                    if (ddx * ddx + ddy * ddy + ddz * ddz <= rs * rs * (1.0 + 1e-9)) touch = true;
+                }
+            const unsigned tb = __ballot_sync(0xffffffffu, touch);
+            if (decision == 2 && sl == 0 && (tb & segmask)) {
+                for (int u = base; u < base + sz; u++)
+                    for (int w = u + 1; w < base + sz && W.alive[u]; w++) {
+                        if (!W.alive[w]) continue;
+                        const double ddx = W.y[0][w] - W.y[0][u], ddy = W.y[1][w] - W.y[1][u],
+                                     ddz = W.y[2][w] - W.y[2][u];
+                        if (sqrt(ddx * ddx + ddy * ddy + ddz * ddz) <= W.R[u] + W.R[w])
+                            bs_merge(W, p, u, w, El, nmerge);
+                    }
+            }
+            __syncwarp();
+            if (decision == 2 && live)
+                for (int q = 0; q < 6; q++) yv[q] = W.y[q][lane];
+            // step control (the same on every lane of a segment)
+            if (active) {
+                if (stage < 2) {
+                    ms++;
+                } else {
+                    ms = 0;
+                    if (decision == 1) {
+                        k++;
+                    } else {
+                        nsub++;
+                        bool fin = false, failed = false, hard = false;
+                        if (decision == 2) {
+                            t = last ? dt : t + H;
+                            if (last) fin = true;
+                            else if (k <= 2) H *= 2.0;
+                            else if (k >= 6) H *= 0.5;
+                        } else {
+                            hard = fin = true;   // first attempt rejected: the lockstep kernels redo the group
+                        }
+                        if (!fin && nsub >= cap) fin = failed = true;
+                        k = 0;
+                        if (fin && hard) {
+                            if (sl == 0) {
+                                const int q = atomicAdd(&d.ctl->nhard, 1);
+                                if (q < d.gcap) d.ghard[q] = g;
+                                else set_status(d.ctl, kEoverflow, -7);
+                            }
+                            need = true;
+                        } else if (fin) {
+                            if (live) {
+                                double* o = d.bsout + (int64_t)kBsOut * mslot;
+                                for (int q = 0; q < 6; q++) o[q] = yv[q];
+                                o[6] = W.m[lane];
+                                o[7] = W.R[lane];
+                                o[8] = (double)W.alive[lane];
+                            }
+                            if (sl == 0) {
+                                d.glost[g] = El;
+                                if (nmerge) atomicAdd(&d.ctl->nmerge, nmerge);
+                                atomicAdd(&d.ctl->nsub, (unsigned long long)nsub);
+                                if (failed) set_status(d.ctl, kEbs, g);
+                            }
+                            need = true;
+                        } else {
+                            last = 0;
+                            if (fabs(H) >= fabs(dt - t)) {
+                                H = dt - t;
+                                last = 1;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 constexpr int kBsSmallThreads = 128;   // groups of up to 4 members: 4 attempts, one warp each
 constexpr int kBsLargeThreads = 512;   // groups of up to 64 members: one attempt
 
 cudaError_t bs_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_bs<kBsSmallThreads, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(BsSh<kBsSmallThreads, 4>));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_bs_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kPkWarps * sizeof(PkWarp)));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_bs<kBsLargeThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(BsSh<kBsLargeThreads, 1>));
@@ -397,9 +675,14 @@ int bs_block_regs() {
 }
 
 void launch_bs(const Dev& d, int grid, cudaStream_t s) {
+    // two warps an SM: FP64 issues about one warp instruction per 17 cycles an
+    // SM, so fewer warps sharing it finish their groups' chains sooner
+    k_bs_packed<<<(grid + 3) / 4, 32 * kPkWarps, kPkWarps * sizeof(PkWarp), s>>>(d);
+    prof_mark("bs: many groups, packed");
     k_bs<kBsSmallThreads, 4><<<grid, kBsSmallThreads, sizeof(BsSh<kBsSmallThreads, 4>), s>>>(d, 1);
     prof_mark("bs: groups <= 4");
-    k_bs<kBsLargeThreads, 1><<<(grid + 15) / 16, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s>>>(d, 0);
+    // one block fills an SM's registers: at most one block per SM
+    k_bs<kBsLargeThreads, 1><<<(grid + 3) / 4, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s>>>(d, 0);
     prof_mark("bs: groups > 4");
 }
 

@@ -365,13 +365,14 @@ __global__ void __launch_bounds__(T) k_kick_fp64(Dev d, const KickItem* __restri
 }
 
 // ---------------------------------------------------------------------------
-// After the encounter integrator.  The kick runs beside it, on the state after
-// the drift, so its partial rows hold every group member at its old place.
-// k_kick_apply puts each member's BS result into the state, keeping the old
-// float copies and position; k_kick_fix then
+// After the encounter integrator.  k_kick_apply puts each member's BS result
+// into the state, keeping the old float copies and position.  When the kick
+// ran beside the BS (overlap), on the state after the drift, its partial rows
+// hold every group member at its old place, and k_kick_fix then
 //   - recomputes the full row of each member at its new place,
 //   - for every other body swaps the members' old terms for their new ones,
-//   - sums m V per 64-body segment for the closing jump (after the mergers).
+//   - sums m V per 64-body segment for the closing jump (after the mergers;
+//     this part runs in both orders).
 // A pair's term is computed exactly as the kick computes it: the slow path
 // when r^2 < (2 (rc_i + rc_max))^2, where the kick's tile test sends it too.
 
@@ -426,6 +427,10 @@ __global__ void __launch_bounds__(256) k_kick_apply(Dev d) {
         d.okl[k] = d.kl[g];
         d.okx[k] = D4{d.x[g], d.y[g], d.z[g], d.m[g]};
         const double* o = d.bsout + (int64_t)kBsOut * k;
+        if (o[8] < 0.0) {   // no encounter kernel wrote this member's result
+            set_status(d.ctl, kEoverflow, -6);
+            continue;
+        }
         d.x[g] = o[0]; d.y[g] = o[1]; d.z[g] = o[2];
         d.vx[g] = o[3]; d.vy[g] = o[4]; d.vz[g] = o[5];
         d.m[g] = o[6];
@@ -457,7 +462,7 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
             const double m = al ? d.m[b] : 0.0;
             segment_sums(d, (int64_t)blockIdx.x * kFixThreads, m * d.vx[b], m * d.vy[b], m * d.vz[b], d.pP_close);
         }
-        if (nm == 0) return;
+        if (nm == 0 || !d.overlap) return;
         const int k0 = d.mlo[s], k1 = d.mhi[s];
         const bool want = al && d.label[b] < 0;   // members get their full rows below
         const float rcm = d.rcmax[s];
@@ -530,6 +535,7 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
         return;
     }
     // member rows, one block per member at a time
+    if (!d.overlap) return;
     for (int k = (int)blockIdx.x - nbody_blocks; k < nm; k += (int)gridDim.x - nbody_blocks) {
         const int g = d.members[k];
         const int s = d.body_sys[g];
@@ -617,9 +623,12 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
     }
 }
 
-void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s) {
+void launch_bs_apply(const Dev& d, int nsm, cudaStream_t s) {
     k_kick_apply<<<nsm, 256, 0, s>>>(d);
-    prof_mark("kick fix: apply BS results");
+    prof_mark("apply BS results");
+}
+
+void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s) {
     const int nb = (int)(d.ntot / kFixThreads);
     k_kick_fix<<<nb + 2 * nsm, kFixThreads, 0, s>>>(d, nb);
     prof_mark("kick fix: member rows and corrections");

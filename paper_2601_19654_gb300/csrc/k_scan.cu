@@ -64,7 +64,7 @@ struct SortGrid {
 };
 
 // grid of the system: cells of side h with the system's bodies over at most
-// 2 cap - 1 cells, about 8 live bodies per cell in the two widest directions
+// cap / 4 - 1 cells, about 8 live bodies per cell in the two widest directions
 __device__ SortGrid sort_grid(const Dev& d, int sys, const SysInfo& si) {
     __shared__ SortGrid g;
     if (threadIdx.x == 0) {
@@ -81,7 +81,7 @@ __device__ SortGrid sort_grid(const Dev& d, int sys, const SysInfo& si) {
         double wmax = fmax(a, W[2]), wmid = W[2] > a ? a : (W[2] > b ? W[2] : b);
         double cells = fmax(1.0, (double)si.n / 8.0);
         double inv_h = sqrt(cells / (wmax * wmid));
-        const double nb = (double)(2 * si.cap - 1);
+        const double nb = (double)(si.cap / kBucketDiv - 1);
         double n[3];
         for (int it = 0; it < 400; it++) {
             for (int k = 0; k < 3; k++) n[k] = fmin(floor(W[k] * inv_h) + 1.0, 1.0e6);
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_count(Dev d) {
     const int sys = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
     const SysInfo si = d.sys[sys];
     const SortGrid g = sort_grid(d, sys, si);
-    const int64_t base = 2 * si.off;               // the system's buckets: [2 off, 2 off + 2 cap)
+    const int64_t base = si.off / kBucketDiv;      // the system's buckets: cap / 4 from off / 4
     int key;
     if (d.alive[b]) {
         const float4 c = d.cen[b];
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_count(Dev d) {
         if (iy & 1) ix = g.nx - 1 - ix;            // serpentine rows keep row ends together
         key = (int)(base + ((int64_t)iz * g.ny + iy) * g.nx + ix);
     } else {
-        key = (int)(base + 2 * si.cap - 1);        // dead and padding bodies last
+        key = (int)(base + si.cap / kBucketDiv - 1);   // dead and padding bodies last
     }
     d.ckey[b] = key;
     atomicAdd(&d.cstart[key], 1);
@@ -416,145 +416,228 @@ __global__ void __launch_bounds__(256) k_confirm(Dev d) {
         for (int o = 8; o >= 1; o >>= 1) D = fmin(D, __shfl_xor_sync(half, D, o));
         if (live && sub == 0 && D <= rcij * rcij) {
             int idx = atomicAdd(&d.ctl->nflag, 1);
-            if (idx < d.flag_cap) d.flag[idx] = pr;
-            else set_status(d.ctl, kEoverflow, -2);
+            if (idx < d.flag_cap) {
+                d.flag[idx] = pr;
+                d.label[pr.x] = pr.x;   // both ends become members (their own union-find roots)
+                d.label[pr.y] = pr.y;
+            } else {
+                set_status(d.ctl, kEoverflow, -2);
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------- groups
-// One block: min-label propagation over the flagged pairs (label = lowest
-// body index of the component), then a bitonic sort of (label, body) keys
-// and two block scans give the members, grouped and ascending, and the
-// group offsets.
-constexpr int kGroupThreads = 1024;
-constexpr int kGroupMaxKeys = 2 * kGroupMaxBodies;   // two keys per flagged pair
+// Connected components of the flagged pairs, for any number of pairs:
+//   k_confirm marks both ends of a flagged pair (label = its own index);
+//   k_group_link joins the ends of every pair in a lock-free union-find that
+//     always hooks the larger root under the smaller, so the root of a
+//     component is its lowest body;
+//   k_group_count points every member at its root and counts each group;
+//   k_group_offsets (one block) scans the counts in body order, so groups
+//     come in ascending root order, each with its range in the member list;
+//   k_group_place puts every member into its group's range;
+//   k_group_order sorts each range ascending (one block per group) and lists
+//     the groups the small-group encounter kernel leaves to the large one.
+constexpr int kUfSteps = 1 << 20;         // bound on any one union-find walk
+constexpr int kGroupSortMax = 8192;       // members one block sorts in shared memory
 
-__device__ void block_exclusive_scan(int* v, int n, int* total, int* warp_buf) {
-    // each thread owns a contiguous run of ceil(n / blockDim) entries
-    const int per = (n + blockDim.x - 1) / blockDim.x;
-    const int a = min(n, (int)threadIdx.x * per), b = min(n, a + per);
-    int s = 0;
-    for (int k = a; k < b; k++) s += v[k];
-    // inclusive scan of the per-thread sums across the block
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+// root of x, halving the path on the way; -1 if the walk runs past its bound
+__device__ __forceinline__ int uf_root(int* parent, int x) {
+    for (int it = 0; it < kUfSteps; it++) {
+        const int p = __ldcg(&parent[x]);
+        if (p == x) return x;
+        const int gp = __ldcg(&parent[p]);
+        if (gp != p) atomicCAS(&parent[x], p, gp);
+        x = gp;
     }
-    if (lane == 31) warp_buf[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int wsum = (lane < (int)(blockDim.x >> 5)) ? warp_buf[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, wsum, o);
-            if (lane >= o) wsum += y;
-        }
-        if (lane < (int)(blockDim.x >> 5)) warp_buf[lane] = wsum;
-    }
-    __syncthreads();
-    int base = x - s + (warp > 0 ? warp_buf[warp - 1] : 0);
-    for (int k = a; k < b; k++) {
-        int t = v[k];
-        v[k] = base;
-        base += t;
-    }
-    if (threadIdx.x == blockDim.x - 1) *total = base;
-    __syncthreads();
+    return -1;
 }
 
-__global__ void __launch_bounds__(kGroupThreads) k_group(Dev d) {
-    extern __shared__ unsigned char smem[];
-    long long* keys = reinterpret_cast<long long*>(smem);
-    int* uslot = reinterpret_cast<int*>(keys + kGroupMaxKeys);
-    int* gidx = uslot + kGroupMaxKeys;
-    __shared__ int changed, total_u, total_g, warp_buf[32];
+__global__ void __launch_bounds__(256) k_group_link(Dev d) {
     if (d.ctl->status) return;
     const int nf = d.ctl->nflag;
-    if (nf == 0) return;
-    if (nf > d.flag_cap || 2 * nf > kGroupMaxKeys) {
-        if (threadIdx.x == 0) set_status(d.ctl, kEoverflow, -3);
+    if (nf > d.flag_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(d.ctl, kEoverflow, -3);
         return;
     }
-    for (int p = threadIdx.x; p < nf; p += blockDim.x) {
-        int2 pr = d.flag[p];
-        d.label[pr.x] = pr.x;
-        d.label[pr.y] = pr.y;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nf; p += gridDim.x * blockDim.x) {
+        const int2 pr = d.flag[p];
+        bool done = false;
+        for (int it = 0; it < kUfSteps && !done; it++) {
+            int ra = uf_root(d.label, pr.x), rb = uf_root(d.label, pr.y);
+            if (ra < 0 || rb < 0) break;
+            if (ra == rb) {
+                done = true;
+                break;
+            }
+            if (ra > rb) {
+                const int t = ra;
+                ra = rb;
+                rb = t;
+            }
+            done = atomicCAS(&d.label[rb], rb, ra) == rb;   // the larger root goes under the smaller
+        }
+        if (!done) set_status(d.ctl, kEoverflow, -5);
     }
+}
+
+__global__ void __launch_bounds__(kBodyThreads) k_group_count(Dev d) {
+    if (d.ctl->status || d.ctl->nflag == 0) return;
+    const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
+    if (__ldcg(&d.label[b]) < 0) return;
+    const int r = uf_root(d.label, (int)b);
+    if (r < 0) {
+        set_status(d.ctl, kEoverflow, -5);
+        return;
+    }
+    d.label[b] = r;
+    atomicAdd(&d.gcount[r], 1);
+}
+
+// one block: exclusive scans, in body order, of the group sizes (member
+// offsets) and of the root flags (group indices), 16 counts per thread a pass
+__global__ void __launch_bounds__(1024) k_group_offsets(Dev d) {
+    constexpr int PER = 16;
+    __shared__ long long warp_sum[32];
+    __shared__ long long carry;
+    if (d.ctl->status || d.ctl->nflag == 0) return;
+    if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    // min-label propagation; a component of k bodies settles within k rounds
-    for (int round = 0; round <= nf + 1; round++) {
-        if (threadIdx.x == 0) changed = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t N = d.ntot;
+    for (int64_t base = 0; base < N; base += 1024 * PER) {
+        const int64_t k0 = base + (int64_t)threadIdx.x * PER;
+        int v[PER];
+        if (k0 + PER <= N) {
+            const int4* src = reinterpret_cast<const int4*>(d.gcount + k0);
+#pragma unroll
+            for (int u = 0; u < PER / 4; u++) {
+                const int4 q = src[u];
+                v[4 * u] = q.x; v[4 * u + 1] = q.y; v[4 * u + 2] = q.z; v[4 * u + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < PER; u++) v[u] = k0 + u < N ? d.gcount[k0 + u] : 0;
+        }
+        // low 32 bits: members; high 32 bits: groups (roots have a nonzero count)
+        long long sum = 0;
+#pragma unroll
+        for (int u = 0; u < PER; u++) sum += (long long)v[u] + (v[u] > 0 ? (1LL << 32) : 0LL);
+        long long x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
         __syncthreads();
-        for (int p = threadIdx.x; p < nf; p += blockDim.x) {
-            int2 pr = d.flag[p];
-            int li = atomicAdd(&d.label[pr.x], 0), lj = atomicAdd(&d.label[pr.y], 0);
-            if (li != lj) {
-                int l = min(li, lj);
-                atomicMin(&d.label[pr.x], l);
-                atomicMin(&d.label[pr.y], l);
-                changed = 1;
+        if (warp == 0) {
+            long long w = warp_sum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sum[lane] = w;
+        }
+        __syncthreads();
+        long long excl = carry + x - sum + (warp > 0 ? warp_sum[warp - 1] : 0);
+        const long long last = excl + sum;
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            if (v[u] > 0) {
+                const int gi = (int)(excl >> 32), off = (int)(excl & 0xffffffffLL);
+                d.gofs[k0 + u] = off;
+                d.goff[gi] = off;
+                d.gidx[k0 + u] = gi;
+            }
+            excl += (long long)v[u] + (v[u] > 0 ? (1LL << 32) : 0LL);
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = last;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int ng = (int)(carry >> 32), nm = (int)(carry & 0xffffffffLL);
+        d.goff[ng] = nm;
+        d.ctl->ngroups = ng;
+        d.ctl->ninvolved = nm;
+    }
+}
+
+__global__ void __launch_bounds__(kBodyThreads) k_group_place(Dev d) {
+    if (d.ctl->status || d.ctl->nflag == 0) return;
+    const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
+    const int r = d.label[b];
+    if (r < 0) return;
+    // the count goes back to zero as the range fills, ready for the next step
+    const int pos = d.gofs[r] + atomicSub(&d.gcount[r], 1) - 1;
+    d.members[pos] = (int)b;
+}
+
+__global__ void __launch_bounds__(256) k_group_order(Dev d) {
+    __shared__ int v[kGroupSortMax];
+    if (d.ctl->status || d.ctl->nflag == 0) return;
+    const int ng = d.ctl->ngroups;
+    for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+        const int m0 = d.goff[g], n = d.goff[g + 1] - m0;
+        if (threadIdx.x == 0) {
+            if (ng > kBsManyGroups) {
+                // many groups: up to 16 members to the packed kernel's class lists, larger
+                // ones straight to the lockstep kernels
+                if (n <= 16) {
+                    const int c = n <= 2 ? 0 : (n <= 4 ? 1 : (n <= 8 ? 2 : 3));
+                    d.gcls[c * d.gcap + atomicAdd(&d.ctl->ncls[c], 1)] = g;
+                } else {
+                    const int q = atomicAdd(&d.ctl->nhard, 1);
+                    if (q < d.gcap) d.ghard[q] = g;
+                    else set_status(d.ctl, kEoverflow, -7);
+                }
+            } else if (n > 4) {
+                d.glarge[atomicAdd(&d.ctl->nlarge, 1)] = g;
             }
         }
-        __syncthreads();
-        int c = changed;
-        __syncthreads();
-        if (!c) break;
-    }
-    // keys (label, body), padded to a power of two with the largest key
-    const int nk = 2 * nf;
-    int np2 = 1;
-    while (np2 < nk) np2 <<= 1;
-    for (int k = threadIdx.x; k < np2; k += blockDim.x) {
-        long long key = 0x7fffffffffffffffLL;
-        if (k < nk) {
-            int2 pr = d.flag[k >> 1];
-            int b = (k & 1) ? pr.y : pr.x;
-            key = ((long long)__ldcg(&d.label[b]) << 32) | (long long)(unsigned)b;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            d.undo[3 * (m0 + k) + 2] = -1.0;
+            d.bsout[(int64_t)kBsOut * (m0 + k) + 8] = -1.0;   // no result yet (the BS kernels write one)
         }
-        keys[k] = key;
-    }
-    __syncthreads();
-    for (int size = 2; size <= np2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int k = threadIdx.x; k < np2; k += blockDim.x) {
-                int q = k ^ stride;
-                if (q > k) {
-                    bool up = (k & size) == 0;
-                    long long a = keys[k], b = keys[q];
-                    if ((a > b) == up) {
-                        keys[k] = b;
-                        keys[q] = a;
-                    }
+        if (n <= 1) continue;
+        if (n == 2) {
+            if (threadIdx.x == 0) {
+                const int a = d.members[m0], b = d.members[m0 + 1];
+                if (a > b) {
+                    d.members[m0] = b;
+                    d.members[m0 + 1] = a;
                 }
             }
-            __syncthreads();
+            continue;
         }
+        if (n > kGroupSortMax) {
+            if (threadIdx.x == 0) set_status(d.ctl, kEoverflow, 2000000 + g);
+            return;
+        }
+        int np2 = 1;
+        while (np2 < n) np2 <<= 1;
+        __syncthreads();
+        for (int k = threadIdx.x; k < np2; k += blockDim.x) v[k] = k < n ? d.members[m0 + k] : 0x7fffffff;
+        __syncthreads();
+        for (int size = 2; size <= np2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int k = threadIdx.x; k < np2; k += blockDim.x) {
+                    const int q = k ^ stride;
+                    if (q > k) {
+                        const bool up = (k & size) == 0;
+                        const int x = v[k], y = v[q];
+                        if ((x > y) == up) {
+                            v[k] = y;
+                            v[q] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int k = threadIdx.x; k < n; k += blockDim.x) d.members[m0 + k] = v[k];
     }
-    // member slot of each distinct key, and group index of each label run
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-        uslot[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1 : 0;
-        gidx[k] = (k == 0 || (keys[k] >> 32) != (keys[k - 1] >> 32)) ? 1 : 0;
-    }
-    __syncthreads();
-    block_exclusive_scan(uslot, nk, &total_u, warp_buf);
-    block_exclusive_scan(gidx, nk, &total_g, warp_buf);
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-        if (k == 0 || keys[k] != keys[k - 1]) d.members[uslot[k]] = (int)(keys[k] & 0xffffffffLL);
-        if (k == 0 || (keys[k] >> 32) != (keys[k - 1] >> 32)) d.goff[gidx[k]] = uslot[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        d.goff[total_g] = total_u;
-        d.ctl->ngroups = total_g;
-        d.ctl->ninvolved = total_u;
-    }
-    __syncthreads();
-    // groups too large for the one-warp encounter kernel
-    for (int g = threadIdx.x; g < total_g; g += blockDim.x)
-        if (d.goff[g + 1] - d.goff[g] > 4) d.glarge[atomicAdd(&d.ctl->nlarge, 1)] = g;
-    for (int k = threadIdx.x; k < total_u; k += blockDim.x) d.undo[3 * k + 2] = -1.0;
 }
 
 void launch_sort_bodies(const Dev& d, cudaStream_t s) {
@@ -583,13 +666,18 @@ void launch_confirm(const Dev& d, int grid, cudaStream_t s) {
     prof_mark("confirm (FP64)");
 }
 
-size_t group_smem() { return (size_t)kGroupMaxKeys * (sizeof(long long) + 2 * sizeof(int)); }
-void launch_group(const Dev& d, cudaStream_t s) {
-    k_group<<<1, kGroupThreads, group_smem(), s>>>(d);
-    prof_mark("group");
-}
-cudaError_t group_setup() {
-    return cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem());
+void launch_group(const Dev& d, int nsm, cudaStream_t s) {
+    const unsigned nb = (unsigned)(d.ntot / kBodyThreads);
+    k_group_link<<<nsm * 2, 256, 0, s>>>(d);
+    prof_mark("group: link");
+    k_group_count<<<nb, kBodyThreads, 0, s>>>(d);
+    prof_mark("group: count");
+    k_group_offsets<<<1, 1024, 0, s>>>(d);
+    prof_mark("group: offsets");
+    k_group_place<<<nb, kBodyThreads, 0, s>>>(d);
+    prof_mark("group: place");
+    k_group_order<<<nsm * 2, 256, 0, s>>>(d);
+    prof_mark("group: order");
 }
 
 }  // namespace opal

@@ -85,6 +85,7 @@ struct opal_sim {
     int kick_variant = 0;
     char kick_desc[256] = {0};
     int time_kick = 0;                       // graph records events around the kick
+    int64_t last_involved = 0;               // bodies in encounters in the last step
     cudaEvent_t kick_ev[2] = {nullptr, nullptr};
     double* d_vh = nullptr;        // heliocentric velocities for get_state
     double* d_en_body = nullptr;
@@ -255,7 +256,6 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     CKF(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
     CKF(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
     CKF(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
-    CKF(group_setup());
     CKF(bs_setup());
 
     // parameters
@@ -318,7 +318,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     float4** f4[] = {&d.kh, &d.kl, &d.cen, &d.sc0, &d.sc1, &d.sv0, &d.sv1};
     for (auto pp : f4) TRYF(dalloc(s, pp, N));
     TRYF(dalloc(s, &d.rcf, N));
-    d.ncell = (int)(2 * N);
+    d.ncell = (int)(N / kBucketDiv);
     TRYF(dalloc(s, &d.sbox, 6 * nsys));
     TRYF(dalloc(s, &d.ckey, N));
     TRYF(dalloc(s, &d.cstart, d.ncell));
@@ -342,6 +342,9 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.members, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.goff, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.glarge, 2 * d.flag_cap + 2));
+    d.gcap = std::min<int64_t>(d.flag_cap + 1, N / 2 + 1);   // a group has two members at least
+    TRYF(dalloc(s, &d.gcls, 4 * d.gcap));
+    TRYF(dalloc(s, &d.ghard, d.gcap));
     TRYF(dalloc(s, &d.glost, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.undo, 3 * (2 * d.flag_cap + 2)));
     {
@@ -351,6 +354,10 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         TRYF(dalloc(s, &d.okl, mcap));
         TRYF(dalloc(s, &d.okx, mcap));
     }
+    TRYF(dalloc(s, &d.gcount, N));
+    TRYF(dalloc(s, &d.gofs, N));
+    TRYF(dalloc(s, &d.gidx, N));
+    CKF(cudaMemsetAsync(d.gcount, 0, N * sizeof(int), s->stream));
     TRYF(dalloc(s, &d.mlo, nsys));
     TRYF(dalloc(s, &d.mhi, nsys));
     TRYF(dalloc(s, &d.cfx, N));
@@ -491,14 +498,13 @@ void reset_scan_order(opal_sim* s) {
     cudaMemsetAsync(d.sbox + 3 * d.nsys, 0x80, 3 * d.nsys * sizeof(int), s->stream);
 }
 
-// the kernels of one step, in order; names for profiling
+// the kernels of one step; names for profiling
 const char* kKernelNames[] = {"counters", "open(kick+jump+drift)", "scan", "confirm", "group", "bs", "kick",
-                              "kick fix", "close(jump+kick)", "finish"};
-constexpr int kNumKernels = 10;
-constexpr int kStageBs = 5, kStageKick = 6;
+                              "apply bs", "kick fix", "close(jump+kick)", "finish"};
+constexpr int kNumKernels = 11;
+constexpr int kStageBs = 5, kStageKick = 6, kStageApply = 7;
 
-// stage k of a step on stream st (the kick does not read what the BS writes,
-// so the two may run at once)
+// stage k of a step on stream st
 void launch_stage(opal_sim* s, int k, cudaStream_t st) {
     const Dev& d = s->d;
     switch (k) {
@@ -508,23 +514,37 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
             cudaMemsetAsync(d.rcmax, 0, d.nsys * sizeof(float), st);
             cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), st);
             cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), st);
+            cudaMemsetAsync(d.gcount, 0, d.ntot * sizeof(int), st);
             reset_scan_order(s);
             prof_mark("memsets");
             break;
         case 1: launch_open(d, st); break;
         case 2: launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, st); break;
         case 3: launch_confirm(d, s->confirm_grid, st); break;
-        case 4: launch_group(d, st); break;
+        case 4: launch_group(d, s->nsm, st); break;
         case kStageBs: launch_bs(d, s->bs_grid, st); break;
         case kStageKick:
             launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
             break;
-        case 7: launch_kick_fix(d, s->nsm, st); break;
-        case 8: launch_close(d, st); break;
-        case 9: launch_finish(d, st); break;
+        case kStageApply: launch_bs_apply(d, s->nsm, st); break;
+        case 8: launch_kick_fix(d, s->nsm, st); break;
+        case 9: launch_close(d, st); break;
+        case 10: launch_finish(d, st); break;
     }
 }
 void launch_stage(opal_sim* s, int k) { launch_stage(s, k, s->stream); }
+
+// Order of the stages.  Overlap: the kick runs beside the BS on the state
+// after the drift and the fix puts the members right afterwards.  In order:
+// the BS results are applied first and the kick sees them (the fix only sums
+// the momentum), which is cheaper when many bodies are in encounters.
+int stage_order(const opal_sim* s, int* out) {
+    static const int ov[] = {0, 1, 2, 3, 4, kStageBs, kStageKick, kStageApply, 8, 9, 10};
+    static const int sq[] = {0, 1, 2, 3, 4, kStageBs, kStageApply, kStageKick, 8, 9, 10};
+    const int* o = s->d.overlap ? ov : sq;
+    for (int k = 0; k < kNumKernels; k++) out[k] = o[k];
+    return kNumKernels;
+}
 
 opal_status capture_graph(opal_sim* s) {
     if (s->exec) {
@@ -535,10 +555,13 @@ opal_status capture_graph(opal_sim* s) {
         CK(cudaGraphDestroy(s->graph));
         s->graph = nullptr;
     }
+    int order[kNumKernels];
+    const int ns = stage_order(s, order);
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < kNumKernels; k++) {
-        if (k == kStageKick) continue;
-        if (k == kStageBs) {
+    for (int q = 0; q < ns; q++) {
+        const int k = order[q];
+        if (s->d.overlap && k == kStageKick) continue;
+        if (s->d.overlap && k == kStageBs) {
             // fork: the kick on the side stream, the encounter integrator here; join before the fix
             CK(cudaEventRecord(s->fork_ev, s->stream));
             CK(cudaStreamWaitEvent(s->side, s->fork_ev, 0));
@@ -550,7 +573,9 @@ opal_status capture_graph(opal_sim* s) {
             CK(cudaStreamWaitEvent(s->stream, s->join_ev, 0));
             continue;
         }
+        if (s->time_kick && k == kStageKick) cudaEventRecordWithFlags(s->kick_ev[0], s->stream, cudaEventRecordExternal);
         launch_stage(s, k);
+        if (s->time_kick && k == kStageKick) cudaEventRecordWithFlags(s->kick_ev[1], s->stream, cudaEventRecordExternal);
     }
     cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
     if (e != cudaSuccess) {
@@ -561,11 +586,25 @@ opal_status capture_graph(opal_sim* s) {
     return OPAL_OK;
 }
 
+// Overlap pays while the fix (about three member-sized kicks) stays small
+// against the kick it hides: choose by the share of bodies in encounters in
+// the last step, with some hysteresis.
+opal_status choose_mode(opal_sim* s) {
+    const double share = s->n_total > 0 ? (double)s->last_involved / (double)s->n_total : 0.0;
+    int want = s->d.overlap;
+    if (share < 0.03) want = 1;
+    else if (share > 0.08) want = 0;
+    if (want == s->d.overlap && s->exec) return OPAL_OK;
+    s->d.overlap = want;
+    return capture_graph(s);
+}
+
 opal_status finish_steps(opal_sim* s, int64_t before) {
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     Ctl c{};
     CK(cudaMemcpy(&c, s->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    s->last_involved = c.ninvolved;
     if (c.status) {
         set_err(s->err, "step %lld: %s (detail %d)", (long long)(c.steps_done + 1), status_name(c.status),
                 c.detail);
@@ -607,6 +646,7 @@ opal_status opal_ensemble_create(const opal_params* p, int32_t nsys, const int64
 opal_status opal_step(opal_sim* s, int64_t nsteps) {
     if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
     if (nsteps < 0) return set_err(s->err, "nsteps < 0"), OPAL_EINVAL;
+    TRY(choose_mode(s));
     for (int64_t k = 0; k < nsteps; k++) CK(cudaGraphLaunch(s->exec, s->stream));
     return finish_steps(s, 0);
 }
@@ -614,6 +654,7 @@ opal_status opal_step(opal_sim* s, int64_t nsteps) {
 opal_status opal_step_async(opal_sim* s, int64_t nsteps) {
     if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
     if (nsteps < 0) return set_err(s->err, "nsteps < 0"), OPAL_EINVAL;
+    TRY(choose_mode(s));
     for (int64_t k = 0; k < nsteps; k++) CK(cudaGraphLaunch(s->exec, s->stream));
     return OPAL_OK;
 }
@@ -706,6 +747,7 @@ void* opal_stream(const opal_sim* s) { return s ? (void*)s->stream : nullptr; }
 opal_status opal_profile_steps(opal_sim* s, int64_t nsteps, int32_t cap, int32_t* nk, double* ms,
                                const char** names) {
     if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
+    TRY(choose_mode(s));
     ProfRec rec{};
     rec.stream = s->stream;
     rec.cap = 64;
@@ -718,7 +760,9 @@ opal_status opal_profile_steps(opal_sim* s, int64_t nsteps, int32_t cap, int32_t
         rec.n = 0;
         g_prof = &rec;
         CK(cudaEventRecord(start, s->stream));
-        for (int k = 0; k < kNumKernels; k++) launch_stage(s, k);
+        int stages[kNumKernels];
+        const int ns = stage_order(s, stages);
+        for (int q = 0; q < ns; q++) launch_stage(s, stages[q]);
         g_prof = nullptr;
         CK(cudaEventSynchronize(rec.ev[rec.n - 1]));
         for (int k = 0; k < rec.n; k++) {
@@ -899,6 +943,7 @@ opal_status opal_debug_scan(opal_sim* s, const double* x0, const double* V0, con
     launch_debug_scan_prep(d, s->stream);
     launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, s->stream);
     launch_confirm(d, s->confirm_grid, s->stream);
+    CK(cudaMemsetAsync(d.label, 0xff, d.ntot * sizeof(int32_t), s->stream));   // no groups formed here
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     Ctl c{};
@@ -967,7 +1012,7 @@ opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0,
     CK(cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), s->stream));
     CK(cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), s->stream));
     launch_bs(d, 1, s->stream);
-    launch_kick_fix(d, s->nsm, s->stream);   // puts the result into the state
+    launch_bs_apply(d, s->nsm, s->stream);   // puts the result into the state
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));

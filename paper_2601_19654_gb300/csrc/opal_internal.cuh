@@ -18,9 +18,10 @@ constexpr int kSeg = 64;         // bodies per partial-sum segment
 constexpr int kBodyThreads = 128;
 constexpr int kBsMaxMembers = 64;   // bodies per encounter group
 constexpr int kKickJTile = 256;     // j-bodies the kick stages in shared memory at a time
+constexpr int kBsManyGroups = 608;  // above this many groups a step integrates them packed, lane per member
+constexpr int kBucketDiv = 4;       // body slots per bucket of the spatial sort (cap / 4 buckets a system)
 constexpr int kBsOut = 9;           // doubles per member slot of the BS side buffer: x, V, m, R, alive
 constexpr int kBsRows = 8;          // extrapolation rows: n_k = 2, 4, ..., 16
-constexpr int kGroupMaxBodies = 4096;   // flagged pairs the grouping kernel takes per step
 constexpr float kFar = 1.0e18f;     // parking coordinate of ghost and dead bodies (float copies)
 
 
@@ -47,6 +48,9 @@ struct Ctl {
     int nmerge;          // mergers (this step)
     int kepler_max;      // largest drift iteration count (this step)
     int nlarge;          // groups too large for one warp (this step)
+    int ncls[4];         // groups of 2, 3-4, 5-8, 9-16 members (this step)
+    int qcls[4];         // how far the packed encounter kernel has taken each list (this step)
+    int nhard;           // groups left to the lockstep kernels when groups are many (this step)
     unsigned long long nsub;  // BS substeps (this step)
     long long steps_done;
     int cand_overflow;   // candidates lost to a full candidate list (forces a status)
@@ -94,6 +98,7 @@ struct Params {
 struct Dev {
     int64_t ntot;
     int nsys;
+    int overlap;       // 1: the kick runs beside the BS and is fixed afterwards; 0: after it
     Params p;
     SysInfo* sys;
     int32_t* body_sys;
@@ -129,7 +134,7 @@ struct Dev {
     int* csorted;                       // bodies in sorted order, ascending ids within a cell
     float4* cen_sorted;                 // their midpoint records, in sorted order
     float* tbox;                        // [ntot / 64][6] tile boxes of c +- s
-    int ncell;                          // buckets: 2 per body slot
+    int ncell;                          // buckets: one per kBucketDiv body slots
     // encounter pipeline
     int2* near;  int64_t near_cap;      // pairs passing the midpoint test
     int2* cand;  int64_t cand_cap;      // FP32-bound candidates
@@ -138,6 +143,12 @@ struct Dev {
     int32_t* members;                   // group members, grouped, ascending
     int32_t* goff;                      // [ngroups + 1] member offsets
     int32_t* glarge;                    // groups of more than 4 members
+    int32_t* gcls;                      // [4][gcap]: groups by size class (2, 4, 8, 16 members at most)
+    int32_t* ghard;                     // [gcap]: groups for the lockstep kernels when groups are many
+    int64_t gcap;                       // capacity of each class list
+    int* gcount;                        // per body: members of the group it roots (zero between steps)
+    int* gofs;                          // per root: its group's first member slot
+    int* gidx;                          // per root: its group's index
     double* glost;                      // per group energy lost to mergers
     double* undo;                       // per member slot: m, R, alive (3 doubles)
     double* bsout;                      // per member slot: the BS result (kBsOut doubles)
@@ -371,13 +382,13 @@ void launch_sort_bodies(const Dev& d, cudaStream_t s);
 void launch_order_prep(const Dev& d, cudaStream_t s);
 void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s);
 void launch_confirm(const Dev& d, int grid, cudaStream_t s);
-void launch_group(const Dev& d, cudaStream_t s);
-cudaError_t group_setup();
+void launch_group(const Dev& d, int nsm, cudaStream_t s);
 cudaError_t bs_setup();   // dynamic shared memory of the BS kernels
 void launch_bs(const Dev& d, int grid, cudaStream_t s);
 void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int variant,
                  cudaStream_t s);
-// after the BS (which ran beside the kick): apply its results, fix the kick's rows
+// after the BS: apply its results; fix the kick's rows when it ran beside the BS
+void launch_bs_apply(const Dev& d, int nsm, cudaStream_t s);
 void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s);
 int kick_num_variants(int precision);
 const char* kick_variant_name(int precision, int variant);

@@ -325,6 +325,33 @@ def test_ensemble_matches_each_system(opal):
             assert relpos(st["x"], osim.x[osim.alive > 0]) <= 1e-12
 
 
+@pytest.mark.parametrize("inflate", [1.0, 30.0])
+def test_many_groups_take_the_packed_path_and_match_the_oracle(opal, inflate):
+    """More encounter groups in a step than the lockstep kernels take (608):
+    the packed kernel (one lane per member) integrates them, and the step runs
+    the kick after the encounters (many bodies involved).  Every system must
+    still match the oracle; with inflated radii some groups merge."""
+    systems = [ic.random_cluster(seed=300 + k, n=100, spread=0.15, vspread=0.01, mass=3e-7) for k in range(64)]
+    for s in systems:
+        s.R = s.R * inflate
+    with opal.Simulation.ensemble(systems, precision=0) as sim:
+        sim.step(1)
+        assert sim.stats()["n_groups"] > 608
+        sim.step(4)
+        merged = 0
+        for k, s in enumerate(systems):
+            osim = oracle.Sim.from_system(s)
+            assert osim.step(5) == oracle.OK
+            st = sim.state(k)
+            alive = np.nonzero(osim.alive)[0]
+            assert st["ids"].tolist() == alive.tolist()
+            merged += s.n - alive.size
+            assert relpos(st["x"], osim.x[alive]) <= 1e-9
+            assert np.allclose(st["m"], osim.m[alive], rtol=1e-15, atol=0)
+        if inflate > 1.0:
+            assert merged > 0
+
+
 def test_get_state_roundtrip_continues_the_run(opal):
     s = ic.tiny(1)
     with opal.Simulation.from_system(s, precision=0) as a:
