@@ -155,7 +155,7 @@ __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, 
 }
 
 template <int NT, int A>
-__global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int small) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
     using Sh = BsSh<NT, A>;
     constexpr int M = Sh::M;
     constexpr int TA = NT / A;            // threads per attempt
@@ -163,8 +163,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int small) {
     Sh& S = *reinterpret_cast<Sh*>(bs_smem);
     if (d.ctl->status) return;
     const Params p = d.p;
-    // the groups this kernel takes: few groups: all (small) or the list of those
-    // above 4 members (large); many groups: the list the packed kernel left
+    // kind 0: groups of up to 4 members, 1: 5-32, 2: 33-64.  The groups it looks
+    // at: few groups: all (kind 0) or the list of those above 4 members; many
+    // groups: the list the packed kernel left.  (Four attempts pay for groups of
+    // up to 4 members; for larger ones they only add FP64 work to the SM.)
+    const bool small = kind == 0;
+    const int lo = kind == 0 ? 1 : (kind == 1 ? 5 : 33);
     const bool many = d.ctl->ngroups > kBsManyGroups;
     const int* list = many ? d.ghard : (small ? nullptr : d.glarge);
     const int ng = many ? d.ctl->nhard : (small ? d.ctl->ngroups : d.ctl->nlarge);
@@ -172,11 +176,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int small) {
     const int a = tid / TA, lt = tid % TA;
     const int cap = p.bs_max_substeps;
     const double tol2 = p.bs_tol * p.bs_tol;
-    for (int gi = blockIdx.x; gi < ng; gi += gridDim.x) {
+    __shared__ int s_gi;
+    for (;;) {
+        // blocks take groups from a queue, so a long group holds up only its own block
+        __syncthreads();
+        if (tid == 0) s_gi = atomicAdd(&d.ctl->qlock[kind], 1);
+        __syncthreads();
+        const int gi = s_gi;
+        if (gi >= ng) break;
         const int g = list ? list[gi] : gi;
         const int mb = d.goff[g], nm = d.goff[g + 1] - mb;
-        if (small && nm > M) continue;      // handled by the large-group kernel
-        if (!small && nm <= 4) continue;    // handled by the small-group kernel
+        if (nm < lo || (nm > M && kind < 2)) continue;   // another lockstep kernel's group
         if (nm > M) {
             if (tid == 0) set_status(d.ctl, kEoverflow, 1000000 + g);
             return;
@@ -654,7 +664,8 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
 }
 
 constexpr int kBsSmallThreads = 128;   // groups of up to 4 members: 4 attempts, one warp each
-constexpr int kBsLargeThreads = 512;   // groups of up to 64 members: one attempt
+constexpr int kBsLargeThreads = 256;   // groups of up to 32 members: one attempt
+constexpr int kBsLargerThreads = 512;  // groups of up to 64 members: one attempt
 
 cudaError_t bs_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_bs<kBsSmallThreads, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -663,8 +674,11 @@ cudaError_t bs_setup() {
     e = cudaFuncSetAttribute(k_bs_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kPkWarps * sizeof(PkWarp)));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_bs<kBsLargeThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(BsSh<kBsLargeThreads, 1>));
+    e = cudaFuncSetAttribute(k_bs<kBsLargeThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BsSh<kBsLargeThreads, 1>));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_bs<kBsLargerThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(BsSh<kBsLargerThreads, 1>));
 }
 
 // registers one small-group block holds (the kick leaves room for one per SM)
@@ -674,16 +688,27 @@ int bs_block_regs() {
     return a.numRegs * kBsSmallThreads;
 }
 
-void launch_bs(const Dev& d, int grid, cudaStream_t s) {
+void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
     // two warps an SM: FP64 issues about one warp instruction per 17 cycles an
     // SM, so fewer warps sharing it finish their groups' chains sooner
-    k_bs_packed<<<(grid + 3) / 4, 32 * kPkWarps, kPkWarps * sizeof(PkWarp), s>>>(d);
+    k_bs_packed<<<nsm, 32 * kPkWarps, kPkWarps * sizeof(PkWarp), s>>>(d);
     prof_mark("bs: many groups, packed");
-    k_bs<kBsSmallThreads, 4><<<grid, kBsSmallThreads, sizeof(BsSh<kBsSmallThreads, 4>), s>>>(d, 1);
+    // the small- and large-group kernels side by side (two small blocks and one
+    // large one fill an SM's registers); s2 == s runs them one after the other
+    if (s2 != s) {
+        cudaEventRecord(fork, s);
+        cudaStreamWaitEvent(s2, fork, 0);
+    }
+    k_bs<kBsLargeThreads, 1><<<nsm, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s2>>>(d, 1);
+    if (s2 == s) prof_mark("bs: groups of 5-32");
+    k_bs<kBsLargerThreads, 1><<<nsm, kBsLargerThreads, sizeof(BsSh<kBsLargerThreads, 1>), s2>>>(d, 2);
+    if (s2 == s) prof_mark("bs: groups of 33-64");
+    k_bs<kBsSmallThreads, 4><<<2 * nsm, kBsSmallThreads, sizeof(BsSh<kBsSmallThreads, 4>), s>>>(d, 0);
     prof_mark("bs: groups <= 4");
-    // one block fills an SM's registers: at most one block per SM
-    k_bs<kBsLargeThreads, 1><<<(grid + 3) / 4, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s>>>(d, 0);
-    prof_mark("bs: groups > 4");
+    if (s2 != s) {
+        cudaEventRecord(join, s2);
+        cudaStreamWaitEvent(s, join, 0);
+    }
 }
 
 }  // namespace opal

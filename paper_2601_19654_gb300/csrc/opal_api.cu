@@ -71,6 +71,8 @@ struct opal_sim {
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;             // the kick's branch of the step graph
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaStream_t side2 = nullptr;            // the large-group BS kernel's branch
+    cudaEvent_t fork2_ev = nullptr, join2_ev = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<SysInfo> sys;
@@ -256,6 +258,9 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     CKF(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
     CKF(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
     CKF(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
+    CKF(cudaStreamCreateWithFlags(&s->side2, cudaStreamNonBlocking));
+    CKF(cudaEventCreateWithFlags(&s->fork2_ev, cudaEventDisableTiming));
+    CKF(cudaEventCreateWithFlags(&s->join2_ev, cudaEventDisableTiming));
     CKF(bs_setup());
 
     // parameters
@@ -522,7 +527,10 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
         case 2: launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, st); break;
         case 3: launch_confirm(d, s->confirm_grid, st); break;
         case 4: launch_group(d, s->nsm, st); break;
-        case kStageBs: launch_bs(d, s->bs_grid, st); break;
+        case kStageBs:
+            // the two lockstep kernels on parallel branches (one stream when profiling)
+            launch_bs(d, s->nsm, st, g_prof ? st : s->side2, s->fork2_ev, s->join2_ev);
+            break;
         case kStageKick:
             launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
             break;
@@ -829,6 +837,7 @@ void opal_destroy(opal_sim* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->side) cudaStreamSynchronize(s->side);
+    if (s->side2) cudaStreamSynchronize(s->side2);
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     for (auto e : s->kick_ev)
@@ -838,6 +847,9 @@ void opal_destroy(opal_sim* s) {
     if (s->side) cudaStreamDestroy(s->side);
     if (s->fork_ev) cudaEventDestroy(s->fork_ev);
     if (s->join_ev) cudaEventDestroy(s->join_ev);
+    if (s->side2) cudaStreamDestroy(s->side2);
+    if (s->fork2_ev) cudaEventDestroy(s->fork2_ev);
+    if (s->join2_ev) cudaEventDestroy(s->join2_ev);
     delete s;
 }
 
@@ -1011,7 +1023,7 @@ opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0,
     CK(cudaMemcpy(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
     CK(cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), s->stream));
     CK(cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), s->stream));
-    launch_bs(d, 1, s->stream);
+    launch_bs(d, s->nsm, s->stream, s->stream, nullptr, nullptr);
     launch_bs_apply(d, s->nsm, s->stream);   // puts the result into the state
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));

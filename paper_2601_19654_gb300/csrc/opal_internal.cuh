@@ -16,7 +16,7 @@ namespace opal {
 constexpr int kPad = 256;        // body padding of every system (largest kick i-tile)
 constexpr int kSeg = 64;         // bodies per partial-sum segment
 constexpr int kBodyThreads = 128;
-constexpr int kBsMaxMembers = 64;   // bodies per encounter group
+constexpr int kBsMaxMembers = 64;   // bodies per encounter group of the lockstep kernels
 constexpr int kKickJTile = 256;     // j-bodies the kick stages in shared memory at a time
 constexpr int kBsManyGroups = 608;  // above this many groups a step integrates them packed, lane per member
 constexpr int kBucketDiv = 4;       // body slots per bucket of the spatial sort (cap / 4 buckets a system)
@@ -51,6 +51,7 @@ struct Ctl {
     int ncls[4];         // groups of 2, 3-4, 5-8, 9-16 members (this step)
     int qcls[4];         // how far the packed encounter kernel has taken each list (this step)
     int nhard;           // groups left to the lockstep kernels when groups are many (this step)
+    int qlock[3];        // queues of the lockstep kernels: up to 4, 32, 64 members (this step)
     unsigned long long nsub;  // BS substeps (this step)
     long long steps_done;
     int cand_overflow;   // candidates lost to a full candidate list (forces a status)
@@ -384,7 +385,7 @@ void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, 
 void launch_confirm(const Dev& d, int grid, cudaStream_t s);
 void launch_group(const Dev& d, int nsm, cudaStream_t s);
 cudaError_t bs_setup();   // dynamic shared memory of the BS kernels
-void launch_bs(const Dev& d, int grid, cudaStream_t s);
+void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
 void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int variant,
                  cudaStream_t s);
 // after the BS: apply its results; fix the kick's rows when it ran beside the BS
