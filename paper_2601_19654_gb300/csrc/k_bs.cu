@@ -35,19 +35,6 @@ namespace opal {
 // attempt, the whole step, which settles most of them; the groups it rejects
 // go on to the lockstep kernels, which start them again from the beginning.
 
-// Neville coefficients 1 / ((n_k / n_{k-j})^2 - 1) with n_k = 2(k+1): exact
-// rationals (k-j+1)^2 / ((k+1)^2 - (k-j+1)^2), rounded once.
-__constant__ double kNeville[kBsRows][kBsRows] = {
-    {0, 0, 0, 0, 0, 0, 0, 0},
-    {0, 1.0 / 3.0, 0, 0, 0, 0, 0, 0},
-    {0, 4.0 / 5.0, 1.0 / 8.0, 0, 0, 0, 0, 0},
-    {0, 9.0 / 7.0, 4.0 / 12.0, 1.0 / 15.0, 0, 0, 0, 0},
-    {0, 16.0 / 9.0, 9.0 / 16.0, 4.0 / 21.0, 1.0 / 24.0, 0, 0, 0},
-    {0, 25.0 / 11.0, 16.0 / 20.0, 9.0 / 27.0, 4.0 / 32.0, 1.0 / 35.0, 0, 0},
-    {0, 36.0 / 13.0, 25.0 / 24.0, 16.0 / 33.0, 9.0 / 40.0, 4.0 / 45.0, 1.0 / 48.0, 0},
-    {0, 49.0 / 15.0, 36.0 / 28.0, 25.0 / 39.0, 16.0 / 48.0, 9.0 / 55.0, 4.0 / 60.0, 1.0 / 63.0},
-};
-
 // NT threads hold A attempts (step sizes H, H/2, ..., H/2^(A-1)) of one group
 // of up to M members, one thread per (attempt, sequence, member).
 template <int NT, int A>
@@ -702,6 +689,8 @@ void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent
     k_bs<kBsLargeThreads, 1><<<nsm, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s2>>>(d, 1);
     if (s2 == s) prof_mark("bs: groups of 5-32");
     k_bs<kBsLargerThreads, 1><<<nsm, kBsLargerThreads, sizeof(BsSh<kBsLargerThreads, 1>), s2>>>(d, 2);
+    if (s2 == s) prof_mark("bs: groups of 33-64");
+    launch_bs_huge(d, nsm, s2);
     if (s2 == s) prof_mark("bs: groups of 33-64");
     k_bs<kBsSmallThreads, 4><<<2 * nsm, kBsSmallThreads, sizeof(BsSh<kBsSmallThreads, 4>), s>>>(d, 0);
     prof_mark("bs: groups <= 4");

@@ -580,7 +580,11 @@ __global__ void __launch_bounds__(256) k_group_order(Dev d) {
     const int ng = d.ctl->ngroups;
     for (int g = blockIdx.x; g < ng; g += gridDim.x) {
         const int m0 = d.goff[g], n = d.goff[g + 1] - m0;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && n > 64) {
+            // the whole-GPU kernel's, one after another
+            if (n <= d.hb.cap) d.ghuge[atomicAdd(&d.ctl->nhuge, 1)] = g;
+            else set_status(d.ctl, kEoverflow, 2000000 + g);
+        } else if (threadIdx.x == 0) {
             if (ng > kBsManyGroups) {
                 // many groups: up to 16 members to the packed kernel's class lists, larger
                 // ones straight to the lockstep kernels

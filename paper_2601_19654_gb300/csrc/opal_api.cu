@@ -350,6 +350,28 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     d.gcap = std::min<int64_t>(d.flag_cap + 1, N / 2 + 1);   // a group has two members at least
     TRYF(dalloc(s, &d.gcls, 4 * d.gcap));
     TRYF(dalloc(s, &d.ghard, d.gcap));
+    TRYF(dalloc(s, &d.ghuge, d.gcap));
+    {
+        // buffers of the whole-GPU encounter kernel, for groups of up to min(N, kHugeMax)
+        HugeBuf& H = d.hb;
+        H.cap = std::min<int64_t>(N, kHugeMax);
+        const int64_t nch = (H.cap + 63) / 64;
+        TRYF(dalloc(s, &H.y, 6 * H.cap));
+        TRYF(dalloc(s, &H.z0, 6 * H.cap));
+        TRYF(dalloc(s, &H.z1, 6 * H.cap));
+        TRYF(dalloc(s, &H.row, (int64_t)kBsRows * 6 * H.cap));
+        TRYF(dalloc(s, &H.pos, 3 * H.cap));
+        TRYF(dalloc(s, &H.posf, H.cap));
+        TRYF(dalloc(s, &H.part, 3 * H.cap * nch));
+        TRYF(dalloc(s, &H.m, H.cap));
+        TRYF(dalloc(s, &H.R, H.cap));
+        TRYF(dalloc(s, &H.rc, H.cap));
+        TRYF(dalloc(s, &H.pinv, H.cap));
+        TRYF(dalloc(s, &H.alive, H.cap));
+        TRYF(dalloc(s, &H.gid, H.cap));
+        TRYF(dalloc(s, &d.hctl, 1));
+        CKF(cudaMemsetAsync(d.hctl, 0, sizeof(HugeCtl), s->stream));
+    }
     TRYF(dalloc(s, &d.glost, 2 * d.flag_cap + 2));
     TRYF(dalloc(s, &d.undo, 3 * (2 * d.flag_cap + 2)));
     {
@@ -520,6 +542,7 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
             cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), st);
             cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), st);
             cudaMemsetAsync(d.gcount, 0, d.ntot * sizeof(int), st);
+            cudaMemsetAsync(d.hctl, 0, sizeof(HugeCtl), st);
             reset_scan_order(s);
             prof_mark("memsets");
             break;

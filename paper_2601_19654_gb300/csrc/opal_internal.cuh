@@ -52,6 +52,7 @@ struct Ctl {
     int qcls[4];         // how far the packed encounter kernel has taken each list (this step)
     int nhard;           // groups left to the lockstep kernels when groups are many (this step)
     int qlock[3];        // queues of the lockstep kernels: up to 4, 32, 64 members (this step)
+    int nhuge;           // groups of more than 64 members (this step)
     unsigned long long nsub;  // BS substeps (this step)
     long long steps_done;
     int cand_overflow;   // candidates lost to a full candidate list (forces a status)
@@ -60,6 +61,43 @@ struct Ctl {
     // both back to zero, so every launch starts from an empty queue
     int kick_next;
     int kick_done;
+};
+
+// Encounter groups of more than 64 members: working arrays of one group
+// (component-major [q][cap] arrays, cap = the largest such group).
+constexpr int kHugeMax = 16384;   // members of the largest group these buffers take
+constexpr int kHugeCand = 1024;   // member pairs in contact after one substep
+struct HugeBuf {
+    int64_t cap;
+    double *y, *z0, *z1;      // [6][cap]: substep state, midpoint chain
+    double* row;              // [kBsRows][6][cap]: extrapolation tableau (in place)
+    double* pos;              // [3][cap]: positions of the current evaluation
+    float4* posf;             // [cap]: the same in float, with rc (rounded up)
+    double* part;             // [cap * chunks][3]: (1 - K) sums of each (member, 64-member chunk)
+    double *m, *R, *rc, *pinv;
+    int *alive, *gid;
+};
+// barrier and bookkeeping of the whole-GPU encounter kernel (zeroed every step)
+struct HugeCtl {
+    unsigned int bar_count, bar_gen;
+    int abort, skip;
+    int ncand, nmerge;
+    double El;
+    unsigned long long err[kBsRows];   // grid-wide maximum error of each row (bits of a double >= 0)
+    int2 cand[kHugeCand];
+};
+
+// Neville coefficients 1 / ((n_k / n_{k-j})^2 - 1) with n_k = 2(k+1): exact
+// rationals (k-j+1)^2 / ((k+1)^2 - (k-j+1)^2), rounded once.
+static __constant__ double kNeville[kBsRows][kBsRows] = {
+    {0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 1.0 / 3.0, 0, 0, 0, 0, 0, 0},
+    {0, 4.0 / 5.0, 1.0 / 8.0, 0, 0, 0, 0, 0},
+    {0, 9.0 / 7.0, 4.0 / 12.0, 1.0 / 15.0, 0, 0, 0, 0},
+    {0, 16.0 / 9.0, 9.0 / 16.0, 4.0 / 21.0, 1.0 / 24.0, 0, 0, 0},
+    {0, 25.0 / 11.0, 16.0 / 20.0, 9.0 / 27.0, 4.0 / 32.0, 1.0 / 35.0, 0, 0},
+    {0, 36.0 / 13.0, 25.0 / 24.0, 16.0 / 33.0, 9.0 / 40.0, 4.0 / 45.0, 1.0 / 48.0, 0},
+    {0, 49.0 / 15.0, 36.0 / 28.0, 25.0 / 39.0, 16.0 / 48.0, 9.0 / 55.0, 4.0 / 60.0, 1.0 / 63.0},
 };
 
 // Per-system constants.
@@ -146,6 +184,9 @@ struct Dev {
     int32_t* glarge;                    // groups of more than 4 members
     int32_t* gcls;                      // [4][gcap]: groups by size class (2, 4, 8, 16 members at most)
     int32_t* ghard;                     // [gcap]: groups for the lockstep kernels when groups are many
+    int32_t* ghuge;                     // [gcap]: groups of more than 64 members
+    HugeBuf hb;                         // working arrays of the whole-GPU encounter kernel
+    HugeCtl* hctl;
     int64_t gcap;                       // capacity of each class list
     int* gcount;                        // per body: members of the group it roots (zero between steps)
     int* gofs;                          // per root: its group's first member slot
@@ -389,6 +430,7 @@ void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent
 void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int variant,
                  cudaStream_t s);
 // after the BS: apply its results; fix the kick's rows when it ran beside the BS
+void launch_bs_huge(const Dev& d, int nsm, cudaStream_t s);
 void launch_bs_apply(const Dev& d, int nsm, cudaStream_t s);
 void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s);
 int kick_num_variants(int precision);

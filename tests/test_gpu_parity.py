@@ -352,6 +352,35 @@ def test_many_groups_take_the_packed_path_and_match_the_oracle(opal, inflate):
             assert merged > 0
 
 
+def _jupiter_zone(n, seed=21, inflate=1.0):
+    """n small bodies on orbits about Jupiter's (4.6-5.8 au) and a Jupiter
+    analogue: every step one encounter group of about n / 15 members."""
+    disk = ic._disk(seed, 11, n, lambda u: np.full_like(u, 1e-4 * ic.M_EARTH), 4.6, 5.8, 0.02, 0.01, 2.0)
+    jup = ic._giant(seed, 12, ic.M_JUP, 5.2, 0.048, 1.33)
+    m, x, v, R = ic._cat(disk, jup)
+    return ic.System(f"jupiter_zone_n{n}", m, x, v, R * inflate, dt=0.05 * ic.YEAR, nsteps=3)
+
+
+@pytest.mark.parametrize("n,inflate", [(1500, 1.0), (2500, 1.0), (2500, 300.0)])
+def test_groups_of_more_than_64_members_match_the_oracle(opal, n, inflate):
+    """A group of about 100-160 members (Jupiter's critical sphere) goes to the
+    whole-GPU encounter kernel; with inflated radii its members merge."""
+    s = _jupiter_zone(n, inflate=inflate)
+    out = _run_pair(opal, s, 3, 0, block=1)
+    assert out["sim"].stats()["n_groups"] >= 1
+    err = _alive_parity(out)
+    assert err <= 1e-9, err
+    st, osim = out["st"], out["osim"]
+    assert np.allclose(st["m"], osim.m[osim.alive > 0], rtol=1e-14, atol=0)
+    if inflate > 1.0:
+        assert osim.alive.sum() < s.n
+        # E_lost is a difference of nearly equal energies, led by the pair's mutual
+        # term at contact: separation ~3e-5 au against positions ~5 au, so states
+        # that agree to 1e-9 relative fix it to about 1e-4 at worst
+        El, Elo = out["sim"].energy()[3], out["osim"].energy()[3]
+        assert abs(El - Elo) <= 1e-4 * abs(Elo)
+
+
 def test_get_state_roundtrip_continues_the_run(opal):
     s = ic.tiny(1)
     with opal.Simulation.from_system(s, precision=0) as a:
