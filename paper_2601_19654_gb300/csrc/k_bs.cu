@@ -24,9 +24,13 @@
 // the four schedulers of an SM) try the step sizes H, H/2, H/4, H/8 at once:
 // the first one accepted in that order is the one the sequential method
 // would reach after its rejections, so only the cost of rejections changes.
+#include <cooperative_groups.h>
+
 #include "opal_internal.cuh"
 
 namespace opal {
+
+namespace cg = cooperative_groups;
 
 // Few groups (kBsManyGroups or fewer in a step): the lockstep kernels (one
 // block per group, all sequences and four step sizes at once) give each group
@@ -52,6 +56,7 @@ struct BsSh {
     double prc2[M], pinv[M], pc01[M];
     int alive[M], gid[M];
     int kacc[A];                        // accepted row of each attempt, -1 while none
+    int gi, kq[4];                      // cluster form: the group taken, every attempt's accepted row
     int decision, collide, nmerge;
     double El;
 };
@@ -141,14 +146,21 @@ __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, 
     }
 }
 
-template <int NT, int A>
-__global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
+// CA > 1 (the cluster form): the CA attempts of a group are the CA blocks of
+// a thread-block cluster, one attempt each on its own SM, so one group's
+// rounds do not share an SM's FP64 pipe; the blocks exchange the decisions
+// and the accepted state through distributed shared memory.  Every block of
+// a cluster takes the same path (the same values decide it), so the cluster
+// barriers are always met.
+template <int NT, int A, int CA>
+__global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int kind) {
     using Sh = BsSh<NT, A>;
     constexpr int M = Sh::M;
     constexpr int TA = NT / A;            // threads per attempt
     extern __shared__ __align__(16) unsigned char bs_smem[];   // one Sh (dynamic: above the static limit)
     Sh& S = *reinterpret_cast<Sh*>(bs_smem);
-    if (d.ctl->status) return;
+    const int arank = CA > 1 ? (int)cg::this_cluster().block_rank() : 0;   // this block's attempt
+    if (CA == 1 && d.ctl->status) return;   // (the cluster form reads nothing another kernel may change)
     const Params p = d.p;
     // kind 0: groups of up to 4 members, 1: 5-32, 2: 33-64.  The groups it looks
     // at: few groups: all (kind 0) or the list of those above 4 members; many
@@ -167,7 +179,15 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
     for (;;) {
         // blocks take groups from a queue, so a long group holds up only its own block
         __syncthreads();
-        if (tid == 0) s_gi = atomicAdd(&d.ctl->qlock[kind], 1);
+        if (CA > 1) {
+            // the cluster's first block takes the group; the others read it there
+            if (arank == 0 && tid == 0) S.gi = atomicAdd(&d.ctl->qlock[kind], 1);
+            cg::this_cluster().sync();
+            if (tid == 0) s_gi = cg::this_cluster().map_shared_rank(&S, 0)->gi;
+            cg::this_cluster().sync();
+        } else if (tid == 0) {
+            s_gi = atomicAdd(&d.ctl->qlock[kind], 1);
+        }
         __syncthreads();
         const int gi = s_gi;
         if (gi >= ng) break;
@@ -175,7 +195,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
         const int mb = d.goff[g], nm = d.goff[g + 1] - mb;
         if (nm < lo || (nm > M && kind < 2)) continue;   // another lockstep kernel's group
         if (nm > M) {
-            if (tid == 0) set_status(d.ctl, kEoverflow, 1000000 + g);
+            if (tid == 0 && arank == 0) set_status(d.ctl, kEoverflow, 1000000 + g);
             return;
         }
         const int k = lt / nm, b = lt % nm;       // sequence and member of this thread
@@ -219,7 +239,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
                 H = rem;
                 last0 = 1;
             }
-            const double Ha = ldexp(H, -a);
+            const double Ha = ldexp(H, -(a + arank));
             const double h = Ha / n;
             double za[6], zb[6];
             if (act)
@@ -283,7 +303,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
                     }
                     __syncthreads();
                     if (lt < nm) {
-                        // squared error ratio: (|dX|/|X|)^2 vs (|dV|/|V|)^2, the larger one
+                        // this member passes (0) or fails (HUGE_VAL) the acceptance test
                         double e2 = 0.0;
                         if (kr >= 1 && S.alive[lt]) {
                             double dsq_x = 0.0, dsq_v = 0.0, nx = 0.0, nv = 0.0;
@@ -295,9 +315,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
                                 dsq_v += S.df2[a][c][lt];
                                 nv += S.cur2[a][c][lt];
                             }
-                            double ex = dsq_x / fmax(nx, 2.3e-308), ev = dsq_v / fmax(nv, 2.3e-308);
-                            e2 = ex > ev ? ex : ev;
-                            if (!(e2 <= 1.7e308)) e2 = HUGE_VAL;   // NaN counts as not converged
+                            // |dX|^2 <= tol^2 |X|^2 and the same for V (the test without its
+                            // divisions); a NaN fails it.  0 passes, HUGE_VAL does not.
+                            e2 = (dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308)) ? 0.0
+                                                                                                         : HUGE_VAL;
                         }
                         S.err[a][kr][lt] = e2;
                     }
@@ -310,15 +331,27 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
                         for (int q = 0; q < nm; q++) e2 = fmax(e2, S.err[a][kr][q]);
                         if (e2 <= tol2) S.kacc[a] = kr;
                     }
-                    __syncthreads();
+                    if (CA > 1) {
+                        // every attempt's row of this round is in place; each block reads all
+                        // of them, then waits until all have read before any moves on
+                        cg::this_cluster().sync();
+                        if (tid == 0)
+                            for (int q = 0; q < CA; q++) S.kq[q] = cg::this_cluster().map_shared_rank(&S, q)->kacc[0];
+                        cg::this_cluster().sync();
+                    } else {
+                        __syncthreads();
+                        if (tid == 0)
+                            for (int q = 0; q < A; q++) S.kq[q] = S.kacc[q];
+                    }
                     if (tid == 0) {
                         // attempt 0 accepted: done; at the last round every attempt has
                         // decided and the first accepted one (in halving order) is taken
-                        if (S.kacc[0] >= 0) S.decision = 0;
+                        constexpr int NA = CA > 1 ? CA : A;
+                        if (S.kq[0] >= 0) S.decision = 0;
                         else if (r == 2 * kBsRows) {
-                            int dcs = A;
-                            for (int q = A - 1; q >= 0; q--)
-                                if (S.kacc[q] >= 0) dcs = q;
+                            int dcs = NA;
+                            for (int q = NA - 1; q >= 0; q--)
+                                if (S.kq[q] >= 0) dcs = q;
                             S.decision = dcs;
                         }
                     }
@@ -328,12 +361,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
             }
             const int dec = S.decision;
             // replay the sequential control flow over the attempts just made
-            for (int q = 0; q < A; q++) {
+            constexpr int NA = CA > 1 ? CA : A;
+            for (int q = 0; q < NA; q++) {
                 nsub++;
                 const double Hq = ldexp(H, -q);
                 if (q == dec) {
-                    const int kacc = S.kacc[q];
-                    if (a == q && lt < 6 * nm) S.y[lt / nm][lt % nm] = S.diag[q][kacc][lt / nm][lt % nm];
+                    const int kacc = S.kq[q];
+                    if (CA > 1) {
+                        // the accepted state from attempt q's block; all copy before it moves on
+                        if (lt < 6 * nm)
+                            S.y[lt / nm][lt % nm] =
+                                cg::this_cluster().map_shared_rank(&S, q)->diag[0][kacc][lt / nm][lt % nm];
+                        cg::this_cluster().sync();
+                    } else if (a == q && lt < 6 * nm) {
+                        S.y[lt / nm][lt % nm] = S.diag[q][kacc][lt / nm][lt % nm];
+                    }
                     const int lastq = (q == 0) ? last0 : 0;
                     t = lastq ? dt : t + Hq;
                     if (tid == 0) S.collide = 0;
@@ -374,23 +416,23 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Dev d, int kind) {
                     break;
                 }
             }
-            if (dec == A && !failed) H = ldexp(H, -A);   // every attempt rejected
+            if (dec == NA && !failed) H = ldexp(H, -NA);   // every attempt rejected
             __syncthreads();
         }
         if (failed) {
-            if (tid == 0) set_status(d.ctl, kEbs, g);
+            if (tid == 0 && arank == 0) set_status(d.ctl, kEbs, g);
             return;
         }
         // results go to the member's slot of the side buffer; the state itself
         // is updated after the step's kick, which runs beside this kernel
-        if (tid < nm) {
+        if (tid < nm && arank == 0) {
             double* o = d.bsout + (int64_t)kBsOut * (mb + tid);
             for (int c = 0; c < 6; c++) o[c] = S.y[c][tid];
             o[6] = S.m[tid];
             o[7] = S.R[tid];
             o[8] = (double)S.alive[tid];
         }
-        if (tid == 0) {
+        if (tid == 0 && arank == 0) {
             d.glost[g] = S.El;
             if (S.nmerge) atomicAdd(&d.ctl->nmerge, S.nmerge);
             atomicAdd(&d.ctl->nsub, (unsigned long long)nsub);
@@ -550,9 +592,8 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
                     }
                 }
                 if (k >= 1 && W.alive[lane]) {
-                    const double ex = dsq_x / fmax(nx, 2.3e-308), ev = dsq_v / fmax(nv, 2.3e-308);
-                    e2 = ex > ev ? ex : ev;
-                    if (!(e2 <= 1.7e308)) e2 = HUGE_VAL;   // NaN counts as not converged
+                    // |dX|^2 <= tol^2 |X|^2 and the same for V; a NaN fails it
+                    e2 = (dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308)) ? 0.0 : HUGE_VAL;
                 }
             }
             W.err[lane] = e2;
@@ -650,29 +691,28 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
     }
 }
 
-constexpr int kBsSmallThreads = 128;   // groups of up to 4 members: 4 attempts, one warp each
 constexpr int kBsLargeThreads = 256;   // groups of up to 32 members: one attempt
 constexpr int kBsLargerThreads = 512;  // groups of up to 64 members: one attempt
 
 cudaError_t bs_setup() {
-    cudaError_t e = cudaFuncSetAttribute(k_bs<kBsSmallThreads, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(BsSh<kBsSmallThreads, 4>));
+    cudaError_t e = cudaFuncSetAttribute(k_bs<32, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(BsSh<32, 1>));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_bs_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kPkWarps * sizeof(PkWarp)));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_bs<kBsLargeThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_bs<kBsLargeThreads, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(BsSh<kBsLargeThreads, 1>));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_bs<kBsLargerThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_bs<kBsLargerThreads, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(BsSh<kBsLargerThreads, 1>));
 }
 
 // registers one small-group block holds (the kick leaves room for one per SM)
 int bs_block_regs() {
     cudaFuncAttributes a{};
-    if (cudaFuncGetAttributes(&a, k_bs<kBsSmallThreads, 4>) != cudaSuccess) return 65536;
-    return a.numRegs * kBsSmallThreads;
+    if (cudaFuncGetAttributes(&a, k_bs<32, 1, 4>) != cudaSuccess) return 65536;
+    return a.numRegs * 32;
 }
 
 void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
@@ -686,13 +726,28 @@ void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent
         cudaEventRecord(fork, s);
         cudaStreamWaitEvent(s2, fork, 0);
     }
-    k_bs<kBsLargeThreads, 1><<<nsm, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s2>>>(d, 1);
+    k_bs<kBsLargeThreads, 1, 1><<<nsm, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s2>>>(d, 1);
     if (s2 == s) prof_mark("bs: groups of 5-32");
-    k_bs<kBsLargerThreads, 1><<<nsm, kBsLargerThreads, sizeof(BsSh<kBsLargerThreads, 1>), s2>>>(d, 2);
+    k_bs<kBsLargerThreads, 1, 1><<<nsm, kBsLargerThreads, sizeof(BsSh<kBsLargerThreads, 1>), s2>>>(d, 2);
     if (s2 == s) prof_mark("bs: groups of 33-64");
     launch_bs_huge(d, nsm, s2);
     if (s2 == s) prof_mark("bs: groups of 33-64");
-    k_bs<kBsSmallThreads, 4><<<2 * nsm, kBsSmallThreads, sizeof(BsSh<kBsSmallThreads, 4>), s>>>(d, 0);
+    {
+        // groups of up to 4 members: clusters of four one-warp blocks, one attempt each
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(4 * 2 * nsm));
+        cfg.blockDim = dim3(32);
+        cfg.dynamicSmemBytes = sizeof(BsSh<32, 1>);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 4;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_bs<32, 1, 4>, d, 0);
+    }
     prof_mark("bs: groups <= 4");
     if (s2 != s) {
         cudaEventRecord(join, s2);

@@ -302,9 +302,10 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
                                 }
                             }
                             if (k >= 1 && H.alive[b]) {
-                                const double ex = dsq_x / fmax(nx, 2.3e-308), ev = dsq_v / fmax(nv, 2.3e-308);
-                                double e2 = ex > ev ? ex : ev;
-                                if (!(e2 <= 1.7e308)) e2 = HUGE_VAL;
+                                // |dX|^2 <= tol^2 |X|^2 and the same for V; a NaN fails it
+                                const double e2 =
+                                    (dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308)) ? 0.0
+                                                                                                             : HUGE_VAL;
                                 emax = fmax(emax, e2);
                             }
                         }
