@@ -191,6 +191,22 @@ def encounter_heavy(seed: int = 0, n: int = 131072) -> System:
     return System(f"encounter_heavy_n{n}_seed{seed}", m, x, v, R, dt=0.05 * YEAR, nsteps=500)
 
 
+def embryos_planetesimals(seed: int = 0, n_big: int = 1024, n_small: int = 262144) -> System:
+    """Big bodies first, then small ones (Mercury's big and small lists):
+    n_big - 1 embryos of 0.01-0.1 Earth masses at 0.7-3 au (rho 3) and Jupiter
+    at 5.2 au, then n_small massless planetesimals at 0.7-3 au with the radius
+    of a 1e-4 Earth-mass body of density 2; e/i Rayleigh 0.02/0.01."""
+    big = _disk(seed, 10, n_big - 1, lambda u: log_uniform(u, 0.01 * M_EARTH, 0.1 * M_EARTH),
+                0.7, 3.0, 0.02, 0.01, 3.0)
+    jup = _giant(seed, 11, M_JUP, 5.2, 0.048, 1.33)
+    small = _disk(seed, 12, n_small, lambda u: np.zeros_like(u), 0.7, 3.0, 0.02, 0.01, 2.0)
+    r_small = radius_from_density(np.array([1e-4 * M_EARTH]), 2.0)[0]
+    small = (small[0], small[1], small[2], np.full(n_small, r_small))
+    m, x, v, R = _cat(big, jup, small)
+    return System(f"embryos{n_big}_planetesimals{n_small}_seed{seed}", m, x, v, R, dt=0.01 * YEAR,
+                  nsteps=1000, meta={"n_big": n_big, "n_small": n_small})
+
+
 def ensemble_sizes(seed: int = 0, nsys: int = 256, lo: int = 64, hi: int = 4096) -> np.ndarray:
     """Body counts of an ensemble, log-uniform in [lo, hi]."""
     u = Stream(seed, 8).take(nsys)
@@ -235,4 +251,5 @@ CONFIGS = {
     "planetesimals_jupiter": planetesimals_jupiter,
     "equal_mass_disk": equal_mass_disk,
     "encounter_heavy": encounter_heavy,
+    "embryos_planetesimals": embryos_planetesimals,
 }

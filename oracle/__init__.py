@@ -73,7 +73,7 @@ def lib():
             L.orc_kepler_drift.restype = C.c_int32
             L.orc_min_sep2.argtypes = [C.c_double, _D, _D, _D, _D]
             L.orc_min_sep2.restype = C.c_double
-            L.orc_scan.argtypes = [_i64, C.c_double, _D, _D, _D, _D, _D, _I, _i64, _I, _I,
+            L.orc_scan.argtypes = [_i64, C.c_double, _D, _D, _D, _D, _D, _I, C.c_void_p, _i64, _I, _I,
                                    C.POINTER(C.c_int64)]
             L.orc_scan.restype = C.c_int64
             L.orc_groups.argtypes = [_i64, _i64, _I, _I, _I]
@@ -157,15 +157,19 @@ def min_sep2(dt, d0, u0, d1, u1):
     return lib().orc_min_sep2(dt, _d(d0), _d(u0), _d(d1), _d(u1))
 
 
-def scan(dt, x0, V0, x1, V1, rc, alive=None):
+def scan(dt, x0, V0, x1, V1, rc, alive=None, m=None):
+    """Flagged pairs; m (optional) marks the small bodies (m == 0), no two of
+    which are ever a pair.  Without m every body counts as big."""
     n = np.asarray(rc).size
     cap = max(16, 4 * n)
+    mm = None if m is None else _d(m)
     while True:
         pi = np.empty(cap, np.int32)
         pj = np.empty(cap, np.int32)
         nc = C.c_int64(0)
         cnt = lib().orc_scan(n, dt, _d(x0, (n, 3)), _d(V0, (n, 3)), _d(x1, (n, 3)), _d(V1, (n, 3)),
-                             _d(rc), _alive(n, alive), cap, pi, pj, C.byref(nc))
+                             _d(rc), _alive(n, alive),
+                             None if mm is None else mm.ctypes.data_as(C.c_void_p), cap, pi, pj, C.byref(nc))
         if cnt <= cap:
             return pi[:cnt].copy(), pj[:cnt].copy(), nc.value
         cap = int(cnt)

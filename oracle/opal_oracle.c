@@ -22,7 +22,11 @@
  *   - Bulirsch-Stoer integration of the bodies in close encounter from the
  *     saved start-of-drift state, with collisions: Sec. 2.1.1 footnote 2,
  *     Sec. 3.2 data-management listing, Sec. 2.1.2 (mce_coll);
- *   - energy and momentum: Sec. 2.1.1 item (7).
+ *   - energy and momentum: Sec. 2.1.1 item (7);
+ *   - small bodies (Sec. 2.1): bodies of zero mass are massless particles
+ *     that feel the star and the big bodies (mass > 0) but are the source of
+ *     no force; two small bodies never interact, so a pair of them is never
+ *     flagged, never integrated together and never merged.
  *
  * Pins: every function here is checked by tests/test_oracle_*.py against
  * closed forms, brute force at high precision, conservation laws and the
@@ -103,7 +107,9 @@ void orc_hill_rcrit(int64_t n, double M0, double f_hill, const double* m, const 
 
 /* Mutual accelerations of the kick (Sec. 3.1, force block, LOOP 2):
  * a_i = sum_{j != i} G m_j K(r_ij; rc_ij) (x_j - x_i) / r_ij^3, with
- * rc_ij = max(rc_i, rc_j).  Each a_i is summed over j in increasing order. */
+ * rc_ij = max(rc_i, rc_j).  Each a_i is summed over j in increasing order;
+ * small bodies (m_j = 0) are no source and are left out of the sum (Sec. 2.1:
+ * only the big bodies are gravity sources). */
 void orc_accel(int64_t n, double G, int32_t form, const double* m, const double* x,
                const double* rc, const int32_t* alive, double* a) {
 #ifdef _OPENMP
@@ -113,7 +119,7 @@ void orc_accel(int64_t n, double G, int32_t form, const double* m, const double*
         double ai[3] = {0, 0, 0};
         if (alive[i]) {
             for (int64_t j = 0; j < n; j++) {
-                if (j == i || !alive[j]) continue;
+                if (j == i || !alive[j] || m[j] == 0.0) continue;
                 double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
                 double r2 = dot3(d, d);
                 double r = sqrt(r2);
@@ -314,6 +320,8 @@ double orc_min_sep2(double T, const double d0[3], const double u0[3], const doub
  * the critical distance rc_ij = max(rc_i, rc_j) (the comparison is ".le.").
  * x0, V0 are the saved start-of-drift state (Sec. 3.1, third block), x1, V1
  * the state after the drift.  Pairs are listed with i ascending, then j.
+ * Two small bodies (m = 0 both; m may be NULL: no small bodies) are never a
+ * pair: they do not interact (Sec. 2.1).
  *
  * Two exact bounds skip pairs that cannot be flagged (they only save time;
  * the flagged set is the one of the exact test):
@@ -329,7 +337,7 @@ double orc_min_sep2(double T, const double d0[3], const double u0[3], const doub
  *      (4/27)|T|(|u0| + |u1|) =: E; so |d(s)| >= dist(0, chord) - E.
  * Returns the number of flagged pairs (the first min(count, cap) are written). */
 int64_t orc_scan(int64_t n, double T, const double* x0, const double* V0, const double* x1,
-                 const double* V1, const double* rc, const int32_t* alive, int64_t cap,
+                 const double* V1, const double* rc, const int32_t* alive, const double* m, int64_t cap,
                  int32_t* pi, int32_t* pj, int64_t* n_candidates) {
     double* rho = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double* cen = (double*)malloc(sizeof(double) * (size_t)(3 * n > 0 ? 3 * n : 1));
@@ -349,6 +357,7 @@ int64_t orc_scan(int64_t n, double T, const double* x0, const double* V0, const 
         if (!alive[i]) continue;
         for (int64_t j = i + 1; j < n; j++) {
             if (!alive[j]) continue;
+            if (m && m[i] == 0.0 && m[j] == 0.0) continue; /* two small bodies */
             double rcij = rc[i] > rc[j] ? rc[i] : rc[j];
             double d1[3], d0[3], u0[3], u1[3], dc[3];
             for (int k = 0; k < 3; k++) {
@@ -468,7 +477,7 @@ static void bs_deriv(const bs_ctx* c, const double* y, double* f) {
         double s = -G * M0 / (r2 * r);
         double acc[3] = {s * xb[0], s * xb[1], s * xb[2]};
         for (int64_t q = 0; q < nm; q++) {
-            if (q == b || !c->am[q]) continue;
+            if (q == b || !c->am[q] || c->mm[q] == 0.0) continue; /* a small body pulls nothing */
             double d[3] = {X[3 * q] - xb[0], X[3 * q + 1] - xb[1], X[3 * q + 2] - xb[2]};
             double dr2 = dot3(d, d), dr = sqrt(dr2);
             double rcbq = c->rcm[b] > c->rcm[q] ? c->rcm[b] : c->rcm[q];
@@ -618,7 +627,7 @@ int32_t orc_bs_group(const orc_params* p, int64_t nm, const int32_t* members, do
             t = last ? dt : t + H;
             for (int64_t b = 0; b < nm; b++) {
                 for (int64_t e = b + 1; e < nm && am[b]; e++) {
-                    if (!am[e]) continue;
+                    if (!am[e] || (mm[b] == 0.0 && mm[e] == 0.0)) continue; /* two small bodies never touch */
                     double d[3] = {y[3 * e] - y[3 * b], y[3 * e + 1] - y[3 * b + 1], y[3 * e + 2] - y[3 * b + 2]};
                     if (norm3(d) <= Rm[b] + Rm[e]) {
                         bs_merge(&c, y, b, e, E_lost);
@@ -677,7 +686,8 @@ void orc_energy(int64_t n, double G, double M0, const double* m, const double* x
         if (!alive[i]) continue;
         nsum row = {0, 0};
         for (int64_t j = i + 1; j < n; j++) {
-            if (!alive[j]) continue;
+            /* a small body has no mutual potential energy with anything */
+            if (!alive[j] || m[i] == 0.0 || m[j] == 0.0) continue;
             double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
             nadd(&row, -G * m[i] * m[j] / norm3(d));
         }
@@ -756,12 +766,12 @@ int32_t orc_step(const orc_params* p, int64_t n, double* m, double* R, double* x
         }
         if (status == ORC_OK) {
             orc_hill_rcrit(n, M0, p->rcrit_hill, m, x, alive, rc);
-            int64_t np = orc_scan(n, dt, x0, V0, x, V, rc, alive, cap, pi, pj, &s.n_candidates);
+            int64_t np = orc_scan(n, dt, x0, V0, x, V, rc, alive, m, cap, pi, pj, &s.n_candidates);
             if (np > cap) {
                 cap = np;
                 pi = realloc(pi, sizeof(int32_t) * (size_t)cap);
                 pj = realloc(pj, sizeof(int32_t) * (size_t)cap);
-                np = orc_scan(n, dt, x0, V0, x, V, rc, alive, cap, pi, pj, &s.n_candidates);
+                np = orc_scan(n, dt, x0, V0, x, V, rc, alive, m, cap, pi, pj, &s.n_candidates);
             }
             s.n_pairs = np;
             if (np > 0) {

@@ -60,8 +60,8 @@ int32_t orc_kepler_drift(double mu, double dt, double x[3], double v[3], int32_t
 double orc_min_sep2(double dt, const double d0[3], const double u0[3], const double d1[3],
                     const double u1[3]);
 int64_t orc_scan(int64_t n, double dt, const double* x0, const double* V0, const double* x1,
-                 const double* V1, const double* rc, const int32_t* alive, int64_t cap,
-                 int32_t* pi, int32_t* pj, int64_t* n_candidates);
+                 const double* V1, const double* rc, const int32_t* alive, const double* m,
+                 int64_t cap, int32_t* pi, int32_t* pj, int64_t* n_candidates);
 int64_t orc_groups(int64_t n, int64_t npairs, const int32_t* pi, const int32_t* pj,
                    int32_t* label);
 
