@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble vs per-system comparison")
     ap.add_argument("--ensemble-steps", type=int, default=10)
+    ap.add_argument("--no-small", action="store_true", help="skip the small-body (planetesimal) workload")
+    ap.add_argument("--small-steps", type=int, default=50)
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args(argv)
 
@@ -241,6 +243,30 @@ def ensemble_rates(seed: int, steps: int, warmup: int):
             "timing": "host clock around opal_step calls (each call ends in a device sync)"}
 
 
+def small_body_rates(seed: int, steps: int, warmup: int, flush):
+    """The production regime of the paper's Sec. 2.1: 1023 embryos and Jupiter
+    (big bodies) with 262144 massless planetesimals (small bodies), mixed
+    form, device-timed like the headline.  Each step costs (N_big + N_small)
+    x N_big kick interactions (small bodies are sources of nothing)."""
+    from paper_2601_19654_gb300 import opal
+    system = ic.embryos_planetesimals(seed)
+    nb, n = system.meta["n_big"], system.n
+    sim = opal.Simulation.from_system(system, precision=1)
+    E0 = sim.energy()[0]
+    step_ms, kick_ms = time_steps(sim, steps, warmup, flush)
+    dE = abs(sim.energy()[0] - E0) / abs(E0)
+    st = sim.stats()
+    kcfg = sim.kick_config
+    sim.close()
+    ms = float(np.mean(step_ms))
+    inter = n * nb - nb
+    return {"workload": system.name, "n_big": nb, "n_small": n - nb, "steps": steps, "warmup": warmup,
+            "steps_per_s": 1e3 / ms, "ms_per_step": ms, "interactions_per_step": inter,
+            "interactions_per_s": inter * 1e3 / ms, "kick_ms": float(np.mean(kick_ms)), "kick": kcfg,
+            "dE_over_E": dE, "encounters_last_step": st,
+            "timing": "CUDA events on the simulation's stream, L2 flushed before every step"}
+
+
 def oracle_rate(system, seconds: float, max_steps: int | None = None):
     import oracle
     oracle.build()
@@ -360,6 +386,8 @@ def run_ours(args, rank, world, local):
         line["e2e"] = e2e_rate(system, max(5, min(args.steps, 50)), precision=1)
         if not args.no_ensemble:
             line["ensemble"] = ensemble_rates(args.seed, args.ensemble_steps, 3)
+        if not args.no_small:
+            line["small_bodies"] = small_body_rates(args.seed, args.small_steps, 5, flush)
         if not args.no_cpu_baseline:
             v, done, el, threads, dE = oracle_rate(system, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",

@@ -103,13 +103,14 @@ __device__ void bs_merge(SH& S, const Params& p, int b, int q, double& El, int& 
 // (1 - K) weighted attraction of a member at (xb, yb, zb) towards one at
 // (xo, yo, zo) of mass mo, added to (ax, ay, az).  rc, rc2, c01, inv belong to
 // the member with the larger rc (rc_bo = max(rc_b, rc_o)): rc, rc^2, 0.1 rc and
-// 1 / (0.9 rc), so K needs no division by rc.
+// 1 / (0.9 rc), so K needs no division by rc.  A small body (mo = 0) pulls
+// nothing (Sec. 2.1: only big bodies are gravity sources).
 __device__ __forceinline__ void bs_pair(const Params& p, double xb, double yb, double zb, double xo, double yo,
                                         double zo, double mo, double rc, double rc2, double c01, double inv,
                                         double& ax, double& ay, double& az) {
     const double dx = xo - xb, dy = yo - yb, dz = zo - zb;
     const double dr2 = dx * dx + dy * dy + dz * dz;
-    if (dr2 >= rc2) return;   // 1 - K = 0 at or beyond rc
+    if (dr2 >= rc2 || mo == 0.0) return;   // 1 - K = 0 at or beyond rc
     const double dri = rsqrt(dr2), dr = dr2 * dri;
     double K;
     if (dr >= rc) {
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                     // any pair in contact?  (exact sequential resolution only if so)
                     for (int e = tid; e < nm * nm; e += NT) {
                         int u = e / nm, w = e % nm;
-                        if (w > u && S.alive[u] && S.alive[w]) {
+                        if (w > u && S.alive[u] && S.alive[w] && bs_can_touch(S.m[u], S.m[w])) {
                             double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
                                    dz = S.y[2][w] - S.y[2][u];
                             if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w]) S.collide = 1;
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                     if (S.collide && tid == 0) {
                         for (int u = 0; u < nm; u++)
                             for (int w = u + 1; w < nm && S.alive[u]; w++) {
-                                if (!S.alive[w]) continue;
+                                if (!S.alive[w] || !bs_can_touch(S.m[u], S.m[w])) continue;
                                 double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
                                        dz = S.y[2][w] - S.y[2][u];
                                 if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w])
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
             bool touch = false;
             if (decision == 2 && live && W.alive[lane])
                 for (int o = lane + 1; o < base + sz; o++) {
-                    if (!W.alive[o]) continue;
+                    if (!W.alive[o] || !bs_can_touch(W.m[lane], W.m[o])) continue;
                     const double ddx = cur[0] - W.y[0][o], ddy = cur[1] - W.y[1][o], ddz = cur[2] - W.y[2][o];
                     const double rs = W.R[lane] + W.R[o];
                     if (ddx * ddx + ddy * ddy + ddz * ddz <= rs * rs * (1.0 + 1e-9)) touch = true;
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
             if (decision == 2 && sl == 0 && (tb & segmask)) {
                 for (int u = base; u < base + sz; u++)
                     for (int w = u + 1; w < base + sz && W.alive[u]; w++) {
-                        if (!W.alive[w]) continue;
+                        if (!W.alive[w] || !bs_can_touch(W.m[u], W.m[w])) continue;
                         const double ddx = W.y[0][w] - W.y[0][u], ddy = W.y[1][w] - W.y[1][u],
                                      ddz = W.y[2][w] - W.y[2][u];
                         if (sqrt(ddx * ddx + ddy * ddy + ddz * ddz) <= W.R[u] + W.R[w])

@@ -68,7 +68,7 @@ __device__ __forceinline__ void huge_pair(const Dev& d, const Params& p, int b, 
     const int64_t c = H.cap;
     const double dx = H.pos[o] - xb, dy = H.pos[c + o] - yb, dz = H.pos[2 * c + o] - zb;
     const double dr2 = dx * dx + dy * dy + dz * dz;
-    if (dr2 >= rc * rc) return;
+    if (dr2 >= rc * rc || H.m[o] == 0.0) return;   // beyond rc, or a small body (no source)
     const double dri = rsqrt(dr2), dr = dr2 * dri;
     double K;
     if (dr >= rc) {
@@ -134,8 +134,10 @@ __device__ __forceinline__ void huge_set_pos(const Dev& d, int b, double x, doub
     H.posf[b] = make_float4((float)x, (float)y, (float)z, __double2float_ru(H.rc[b]));
 }
 
-// exact contact test of two members (the small-group kernels' comparison)
+// exact contact test of two members (the small-group kernels' comparison);
+// two small bodies never touch
 __device__ __forceinline__ bool huge_touch(const HugeBuf& H, int u, int w) {
+    if (!bs_can_touch(H.m[u], H.m[w])) return false;
     const int64_t c = H.cap;
     const double dx = H.y[w] - H.y[u], dy = H.y[c + w] - H.y[c + u], dz = H.y[2 * c + w] - H.y[2 * c + u];
     return sqrt(dx * dx + dy * dy + dz * dz) <= H.R[u] + H.R[w];
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
                     const int u = (int)(w / nch), ch = (int)(w % nch);
                     if (!H.alive[u]) continue;
                     for (int o = ch * kHugeChunk; o < min(M, (ch + 1) * kHugeChunk); o++) {
-                        if (o <= u || !H.alive[o]) continue;
+                        if (o <= u || !H.alive[o] || !bs_can_touch(H.m[u], H.m[o])) continue;
                         const double dx = H.y[o] - H.y[u], dy = H.y[c + o] - H.y[c + u], dz = H.y[2 * c + o] - H.y[2 * c + u];
                         const double rs = H.R[u] + H.R[o];
                         if (dx * dx + dy * dy + dz * dz <= rs * rs * (1.0 + 1e-9)) {

@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
     __shared__ D4 snx[kFixThreads], sox[kFixThreads];
     __shared__ double snrd[kFixThreads];
     __shared__ double red[3][kFixThreads];
+    __shared__ int wcnt[kFixThreads / 32];
     if (d.ctl->status) return;
     const int nm = d.ctl->ninvolved;
     const int form = d.p.changeover;
@@ -464,6 +465,7 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
         }
         if (nm == 0 || !d.overlap) return;
         const int k0 = d.mlo[s], k1 = d.mhi[s];
+        const int64_t big_end = d.sys[s].off + d.sys[s].nb;
         const bool want = al && d.label[b] < 0;   // members get their full rows below
         const float rcm = d.rcmax[s];
         // i-side values of both forms
@@ -479,24 +481,37 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
         double cx = 0.0, cy = 0.0, cz = 0.0;
         float hx = 0.0f, hy = 0.0f, hz = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
         for (int kb = k0; kb < k1; kb += kFixThreads) {
-            const int n = min(kFixThreads, k1 - kb);
+            const int nk = min(kFixThreads, k1 - kb);
             __syncthreads();
-            if ((int)threadIdx.x < n) {
-                const int k = kb + threadIdx.x, g = d.members[k];
+            // only members that were big at the start of the step are sources
+            // (a small one adds nothing, old or new), so only they are staged
+            const int k = kb + threadIdx.x;
+            const int g = (int)threadIdx.x < nk ? d.members[k] : -1;
+            const bool src = g >= 0 && g < big_end;
+            const unsigned bm = __ballot_sync(0xffffffffu, src);
+            if ((threadIdx.x & 31) == 0) wcnt[threadIdx.x >> 5] = __popc(bm);
+            __syncthreads();
+            int slot = __popc(bm & ((1u << (threadIdx.x & 31)) - 1u)), n = 0;
+#pragma unroll
+            for (int w = 0; w < kFixThreads / 32; w++) {
+                if (w < (int)(threadIdx.x >> 5)) slot += wcnt[w];
+                n += wcnt[w];
+            }
+            if (src) {
                 if (mixed) {
-                    snh[threadIdx.x] = d.kh[g];
-                    snl[threadIdx.x] = d.kl[g];
-                    snr[threadIdx.x] = d.rcf[g];
-                    soh[threadIdx.x] = d.okh[k];
-                    sol[threadIdx.x] = d.okl[k];
+                    snh[slot] = d.kh[g];
+                    snl[slot] = d.kl[g];
+                    snr[slot] = d.rcf[g];
+                    soh[slot] = d.okh[k];
+                    sol[slot] = d.okl[k];
                 } else {
-                    snx[threadIdx.x] = D4{d.x[g], d.y[g], d.z[g], d.m[g]};
-                    sox[threadIdx.x] = d.okx[k];
-                    snrd[threadIdx.x] = d.rc[g];
+                    snx[slot] = D4{d.x[g], d.y[g], d.z[g], d.m[g]};
+                    sox[slot] = d.okx[k];
+                    snrd[slot] = d.rc[g];
                 }
             }
             __syncthreads();
-            if (!want) continue;
+            if (!want || n == 0) continue;
             if (mixed) {
                 float tx = 0.0f, ty = 0.0f, tz = 0.0f;
                 for (int q = 0; q < n; q++) {
@@ -553,7 +568,7 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
             if (mixed) {
                 // float sums of 16 terms at a time, folded into hi/lo pairs
                 float hx = 0.0f, hy = 0.0f, hz = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
-                const int64_t jend = si.off + si.n;
+                const int64_t jend = si.off + si.nb;   // sources: the big bodies
                 for (int64_t j0 = si.off + threadIdx.x; j0 < jend; j0 += 8 * kFixThreads) {
                     // eight records loaded together (their latencies overlap); lo parts
                     // and rc only for the rare pair that takes the slow path
@@ -591,7 +606,7 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
                 ax = (double)hx + (double)lx;
                 ay = (double)hy + (double)ly;
                 az = (double)hz + (double)lz;
-            } else for (int64_t j = si.off + threadIdx.x; j < si.off + si.n; j += kFixThreads) {
+            } else for (int64_t j = si.off + threadIdx.x; j < si.off + si.nb; j += kFixThreads) {
                 if (j == g) continue;
                 {
                     double tx, ty, tz;

@@ -63,44 +63,51 @@ struct SortGrid {
     int nx, ny, nz;
 };
 
-// grid of the system: cells of side h with the system's bodies over at most
-// cap / 4 - 1 cells, about 8 live bodies per cell in the two widest directions
-__device__ SortGrid sort_grid(const Dev& d, int sys, const SysInfo& si) {
-    __shared__ SortGrid g;
-    if (threadIdx.x == 0) {
-        float lo[3], hi[3];
-        for (int k = 0; k < 3; k++) {
-            lo[k] = fordinv(d.sbox[3 * sys + k]);
-            hi[k] = fordinv(d.sbox[3 * d.nsys + 3 * sys + k]);
-            if (!(hi[k] >= lo[k])) lo[k] = hi[k] = 0.0f;   // no live body
-            g.lo[k] = lo[k];
-        }
-        double W[3];
-        for (int k = 0; k < 3; k++) W[k] = fmax((double)hi[k] - (double)lo[k], 1e-30);
-        double a = fmax(W[0], W[1]), b = fmin(W[0], W[1]);
-        double wmax = fmax(a, W[2]), wmid = W[2] > a ? a : (W[2] > b ? W[2] : b);
-        double cells = fmax(1.0, (double)si.n / 8.0);
-        double inv_h = sqrt(cells / (wmax * wmid));
-        const double nb = (double)(si.cap / kBucketDiv - 1);
-        double n[3];
-        for (int it = 0; it < 400; it++) {
-            for (int k = 0; k < 3; k++) n[k] = fmin(floor(W[k] * inv_h) + 1.0, 1.0e6);
-            if (n[0] * n[1] * n[2] <= nb) break;
-            inv_h *= 0.8;
-        }
-        // grid_index clamps to these counts, so every key stays in the system's buckets
-        g.inv_h = inv_h;
-        g.nx = (int)n[0];
-        g.ny = (int)n[1];
-        g.nz = (int)n[2];
-        while ((double)g.nx * g.ny * g.nz > nb) {   // only if 400 shrinks were not enough
-            if (g.nx >= g.ny && g.nx >= g.nz) g.nx = max(1, g.nx / 2);
-            else if (g.ny >= g.nz) g.ny = max(1, g.ny / 2);
-            else g.nz = max(1, g.nz / 2);
-        }
+// a grid over the system's box of midpoints: cells of side h, about 8 of the
+// nbody bodies per cell in the two widest directions, at most nbuck cells
+__device__ void sort_grid(const Dev& d, int sys, double nbody, int64_t nbuck, SortGrid& g) {
+    float lo[3], hi[3];
+    for (int k = 0; k < 3; k++) {
+        lo[k] = fordinv(d.sbox[3 * sys + k]);
+        hi[k] = fordinv(d.sbox[3 * d.nsys + 3 * sys + k]);
+        if (!(hi[k] >= lo[k])) lo[k] = hi[k] = 0.0f;   // no live body
+        g.lo[k] = lo[k];
     }
-    __syncthreads();
-    return g;
+    double W[3];
+    for (int k = 0; k < 3; k++) W[k] = fmax((double)hi[k] - (double)lo[k], 1e-30);
+    double a = fmax(W[0], W[1]), b = fmin(W[0], W[1]);
+    double wmax = fmax(a, W[2]), wmid = W[2] > a ? a : (W[2] > b ? W[2] : b);
+    double cells = fmax(1.0, nbody / 8.0);
+    double inv_h = sqrt(cells / (wmax * wmid));
+    const double nb = (double)max((int64_t)1, nbuck);
+    double n[3];
+    for (int it = 0; it < 400; it++) {
+        for (int k = 0; k < 3; k++) n[k] = fmin(floor(W[k] * inv_h) + 1.0, 1.0e6);
+        if (n[0] * n[1] * n[2] <= nb) break;
+        inv_h *= 0.8;
+    }
+    // grid_index clamps to these counts, so every key stays in the grid's buckets
+    g.inv_h = inv_h;
+    g.nx = (int)n[0];
+    g.ny = (int)n[1];
+    g.nz = (int)n[2];
+    while ((double)g.nx * g.ny * g.nz > nb) {   // only if 400 shrinks were not enough
+        if (g.nx >= g.ny && g.nx >= g.nz) g.nx = max(1, g.nx / 2);
+        else if (g.ny >= g.nz) g.ny = max(1, g.ny / 2);
+        else g.nz = max(1, g.nz / 2);
+    }
+}
+
+// The system's cap / 4 buckets: the big bodies' grid first, then the small
+// bodies' (each sized to its own count, so both sorted runs are compact), the
+// last bucket for dead and padding bodies.  The sorted order is thus: live
+// big bodies, live small bodies, dead ones; the kick's sources and the scan's
+// big tiles are its first nb places.
+__device__ __forceinline__ int64_t big_buckets(const SysInfo& si) {
+    const int64_t nbk = si.cap / kBucketDiv - 1;   // buckets of live bodies
+    if (si.nb >= si.n) return nbk;
+    if (si.nb == 0) return 0;
+    return min(nbk - 1, max((int64_t)1, (si.nb * nbk + si.n - 1) / si.n));
 }
 
 __device__ __forceinline__ int grid_index(float c, float lo, double inv_h, int n) {
@@ -114,15 +121,21 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_count(Dev d) {
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int sys = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
     const SysInfo si = d.sys[sys];
-    const SortGrid g = sort_grid(d, sys, si);
+    __shared__ SortGrid grid[2];                   // big bodies, small bodies
+    const int64_t nbb = big_buckets(si);
+    if (threadIdx.x == 0) sort_grid(d, sys, (double)si.nb, nbb, grid[0]);
+    if (threadIdx.x == 32) sort_grid(d, sys, (double)(si.n - si.nb), si.cap / kBucketDiv - 1 - nbb, grid[1]);
+    __syncthreads();
     const int64_t base = si.off / kBucketDiv;      // the system's buckets: cap / 4 from off / 4
     int key;
     if (d.alive[b]) {
+        const bool big = b - si.off < si.nb;
+        const SortGrid& g = grid[big ? 0 : 1];
         const float4 c = d.cen[b];
         int ix = grid_index(c.x, g.lo[0], g.inv_h, g.nx), iy = grid_index(c.y, g.lo[1], g.inv_h, g.ny),
             iz = grid_index(c.z, g.lo[2], g.inv_h, g.nz);
         if (iy & 1) ix = g.nx - 1 - ix;            // serpentine rows keep row ends together
-        key = (int)(base + ((int64_t)iz * g.ny + iy) * g.nx + ix);
+        key = (int)(base + (big ? 0 : nbb) + ((int64_t)iz * g.ny + iy) * g.nx + ix);
     } else {
         key = (int)(base + si.cap / kBucketDiv - 1);   // dead and padding bodies last
     }
@@ -253,7 +266,9 @@ __device__ __forceinline__ bool boxes_overlap(const float* a, const float* b) {
 }
 
 // tile pairs (A, B >= A) of the sorted order whose boxes overlap: pairs that
-// pass |c_j - c_i| < s_i + s_j go to a list for stage 2
+// pass |c_j - c_i| < s_i + s_j go to a list for stage 2.  The tile list has a
+// big tile as A (the big bodies sort first); pairs of two small bodies in it
+// are dropped here.
 __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
     __shared__ float4 sj[kSeg];
     __shared__ int gj[kSeg];
@@ -267,6 +282,8 @@ __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __re
         const int64_t pi = tl.i0 + threadIdx.x;
         const float4 ci = d.cen_sorted[pi];
         const int gi = d.csorted[pi];
+        const int64_t big_end = d.sys[tl.sys].off + d.sys[tl.sys].nb;   // ids below are big bodies
+        const bool ibig = gi < big_end;
         __syncthreads();
         sj[threadIdx.x] = d.cen_sorted[tl.j0 + threadIdx.x];
         gj[threadIdx.x] = d.csorted[tl.j0 + threadIdx.x];
@@ -278,7 +295,8 @@ __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __re
             float dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
             float r2 = dx * dx + dy * dy + dz * dz;
             float Ts = ci.w + cj.w;
-            bool pass = (!diag || jj > (int)threadIdx.x) && (r2 < Ts * Ts);
+            // two small bodies never interact
+            bool pass = (!diag || jj > (int)threadIdx.x) && (r2 < Ts * Ts) && (ibig || gj[jj] < big_end);
             unsigned mask = __ballot_sync(0xffffffffu, pass);
             if (mask) {
                 int leader = __ffs(mask) - 1;
@@ -568,10 +586,15 @@ __global__ void __launch_bounds__(kBodyThreads) k_group_place(Dev d) {
     if (d.ctl->status || d.ctl->nflag == 0) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int r = d.label[b];
-    if (r < 0) return;
-    // the count goes back to zero as the range fills, ready for the next step
-    const int pos = d.gofs[r] + atomicSub(&d.gcount[r], 1) - 1;
-    d.members[pos] = (int)b;
+    if (r >= 0) {
+        // the count goes back to zero as the range fills, ready for the next step
+        const int pos = d.gofs[r] + atomicSub(&d.gcount[r], 1) - 1;
+        d.members[pos] = (int)b;
+    }
+    // big members counted (the cost of patching the kick after the encounters)
+    const SysInfo& si = d.sys[d.body_sys[(int64_t)blockIdx.x * kBodyThreads]];
+    const unsigned bm = __ballot_sync(0xffffffffu, r >= 0 && b - si.off < si.nb);
+    if ((threadIdx.x & 31) == 0 && bm) atomicAdd(&d.ctl->ninv_big, __popc(bm));
 }
 
 __global__ void __launch_bounds__(256) k_group_order(Dev d) {

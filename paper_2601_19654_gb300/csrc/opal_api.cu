@@ -88,6 +88,8 @@ struct opal_sim {
     char kick_desc[256] = {0};
     int time_kick = 0;                       // graph records events around the kick
     int64_t last_involved = 0;               // bodies in encounters in the last step
+    int64_t last_inv_big = 0;                // of them big bodies (sources of force)
+    int64_t n_big = 0;                       // big bodies of all systems
     cudaEvent_t kick_ev[2] = {nullptr, nullptr};
     double* d_vh = nullptr;        // heliocentric velocities for get_state
     double* d_en_body = nullptr;
@@ -141,15 +143,17 @@ bool finite_all(const double* a, int64_t n) {
 // short.  Chunks of one system are of equal length to within a tile.
 void build_kick_items(opal_sim* s, int slots, int itile) {
     double work = 0;
-    for (auto& si : s->sys) work += (double)si.cap * (double)si.n;
+    for (auto& si : s->sys) work += (double)si.cap * (double)si.nb;
     const double target = std::max(1.0, work / (8.0 * std::max(1, slots)));
     s->items.clear();
     int64_t slot = 0;
     for (size_t k = 0; k < s->sys.size(); k++) {
         SysInfo& si = s->sys[k];
         const int64_t itiles = si.cap / itile;
-        const int64_t jtiles = (si.n + kKickJTile - 1) / kKickJTile;
-        const double w_tile = (double)itile * (double)si.n;
+        // only the big bodies are sources: j runs over the first nb (small bodies
+        // follow them, in storage and in the sorted order alike)
+        const int64_t jtiles = (si.nb + kKickJTile - 1) / kKickJTile;
+        const double w_tile = (double)itile * (double)si.nb;
         int64_t nchunk = (int64_t)std::llround(w_tile / target);
         nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, jtiles));
         si.nchunk = (int32_t)nchunk;
@@ -157,7 +161,7 @@ void build_kick_items(opal_sim* s, int slots, int itile) {
         slot += nchunk * si.cap;
         for (int64_t c = 0; c < nchunk; c++) {
             const int64_t t0 = jtiles * c / nchunk, t1 = jtiles * (c + 1) / nchunk;
-            const int64_t j0 = si.off + t0 * kKickJTile, j1 = si.off + std::min(si.n, t1 * kKickJTile);
+            const int64_t j0 = si.off + t0 * kKickJTile, j1 = si.off + std::min(si.nb, t1 * kKickJTile);
             for (int64_t t = 0; t < itiles; t++) {
                 KickItem it{};
                 it.sys = (int32_t)k;
@@ -178,8 +182,10 @@ void build_pair_tiles(opal_sim* s) {
     s->tile_off.assign(1, 0);
     for (size_t k = 0; k < s->sys.size(); k++) {
         const SysInfo& si = s->sys[k];
-        const int64_t nt = (si.n + kSeg - 1) / kSeg;
-        for (int64_t a = 0; a < nt; a++)
+        // tile pairs (A, B >= A) with a big body in A: every pair with a big
+        // member (pairs of two small bodies never interact)
+        const int64_t nt = (si.n + kSeg - 1) / kSeg, ntb = (si.nb + kSeg - 1) / kSeg;
+        for (int64_t a = 0; a < ntb; a++)
             for (int64_t b = a; b < nt; b++) {
                 PairTile t{};
                 t.sys = (int32_t)k;
@@ -231,6 +237,13 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         if (x[3 * i] == 0 && x[3 * i + 1] == 0 && x[3 * i + 2] == 0)
             return set_err(g_err, "body %lld sits on the star", (long long)i), OPAL_EINVAL;
     }
+    // small (zero-mass) bodies follow every big body of their system
+    for (int64_t k = 0, i0 = 0; k < nsys; i0 += nps[k], k++)
+        for (int64_t i = i0 + 1; i < i0 + nps[k]; i++)
+            if (m[i] > 0 && m[i - 1] == 0)
+                return set_err(g_err, "body %lld has mass but follows a small (zero-mass) body of its system",
+                               (long long)i),
+                       OPAL_EINVAL;
     opal_sim* s = new (std::nothrow) opal_sim();
     if (!s) return set_err(g_err, "host allocation failed"), OPAL_ENOMEM;
     opal_status st = OPAL_OK;
@@ -272,16 +285,20 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     P.encounter_capacity = p->encounter_capacity > 0 ? p->encounter_capacity : std::max<int64_t>(4096, 4 * ntot);
 
     // layout
-    int64_t off = 0;
+    int64_t off = 0, in0 = 0;
     for (int32_t k = 0; k < nsys; k++) {
         SysInfo si{};
         si.off = off;
         si.n = nps[k];
+        si.nb = 0;
+        while (si.nb < si.n && m[in0 + si.nb] > 0) si.nb++;
+        in0 += nps[k];
         si.cap = (nps[k] + kPad - 1) / kPad * kPad;
         si.seg0 = off / kSeg;
         si.nseg = si.cap / kSeg;
         s->sys.push_back(si);
         s->n_per_sys.push_back(nps[k]);
+        s->n_big += si.nb;
         off += si.cap;
     }
     const int64_t N = off;
@@ -620,8 +637,12 @@ opal_status capture_graph(opal_sim* s) {
 // Overlap pays while the fix (about three member-sized kicks) stays small
 // against the kick it hides: choose by the share of bodies in encounters in
 // the last step, with some hysteresis.
+// Overlap (kick beside the encounter integrator, then patched) or in order.
+// The patch costs about 2 x bodies x big members involved pair terms against
+// the kick's bodies x big bodies, so the share that decides is that of the
+// big bodies (sources) in encounters.
 opal_status choose_mode(opal_sim* s) {
-    const double share = s->n_total > 0 ? (double)s->last_involved / (double)s->n_total : 0.0;
+    const double share = s->n_big > 0 ? (double)s->last_inv_big / (double)s->n_big : 0.0;
     int want = s->d.overlap;
     if (share < 0.03) want = 1;
     else if (share > 0.08) want = 0;
@@ -636,6 +657,7 @@ opal_status finish_steps(opal_sim* s, int64_t before) {
     Ctl c{};
     CK(cudaMemcpy(&c, s->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
     s->last_involved = c.ninvolved;
+    s->last_inv_big = c.ninv_big;
     if (c.status) {
         set_err(s->err, "step %lld: %s (detail %d)", (long long)(c.steps_done + 1), status_name(c.status),
                 c.detail);

@@ -45,6 +45,7 @@ struct Ctl {
     int nflag;           // flagged pairs (this step)
     int ngroups;         // encounter groups (this step)
     int ninvolved;       // bodies in groups (this step)
+    int ninv_big;        // of them big bodies, the sources of force (this step)
     int nmerge;          // mergers (this step)
     int kepler_max;      // largest drift iteration count (this step)
     int nlarge;          // groups too large for one warp (this step)
@@ -105,6 +106,7 @@ struct SysInfo {
     int64_t off;      // first body
     int64_t cap;      // padded body count (multiple of kPad)
     int64_t n;        // bodies given at create
+    int64_t nb;       // big bodies (m > 0): the first nb; the rest are small (massless)
     int64_t seg0;     // first partial-sum segment (off / kSeg)
     int64_t nseg;     // cap / kSeg
     int64_t slot0;    // first row of the kick's partial-acceleration buffer
@@ -210,6 +212,10 @@ struct Dev {
 __device__ __forceinline__ void set_status(Ctl* c, int code, int detail) {
     if (atomicCAS(&c->status, 0, code) == 0) c->detail = detail;
 }
+
+// Two members of an encounter group can collide unless both are small bodies
+// (zero mass), which never interact (Sec. 2.1).
+__device__ __forceinline__ bool bs_can_touch(double mu, double mw) { return mu > 0.0 || mw > 0.0; }
 
 __device__ __forceinline__ double dot3(double ax, double ay, double az, double bx, double by, double bz) {
     return ax * bx + ay * by + az * bz;

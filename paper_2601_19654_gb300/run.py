@@ -3,8 +3,9 @@
   python -m paper_2601_19654_gb300.run --workload disk --steps 20 --precision 1 --profile
 
 Workloads (opal_ic): tiny (10 bodies), planetesimals (1000 + Jupiter),
-disk (16384 equal masses), heavy (131072 + Jupiter and Saturn), ensemble
-(256 systems of 64-4096 bodies).  Prints steps/s, the encounter counters of
+disk (16384 equal masses), heavy (131072 + Jupiter and Saturn), embryos
+(1023 embryos and Jupiter with 262144 massless planetesimals; --n sets the
+planetesimal count), ensemble (256 systems of 64-4096 bodies).  Prints steps/s, the encounter counters of
 the last step, |dE/E| and, with --profile, the device time of every kernel.
 """
 from __future__ import annotations
@@ -25,6 +26,7 @@ WORKLOADS = {
     "planetesimals": lambda seed, n: ic.planetesimals_jupiter(seed, n or 1000),
     "disk": lambda seed, n: ic.equal_mass_disk(seed, n or 16384),
     "heavy": lambda seed, n: ic.encounter_heavy(seed, n or 131072),
+    "embryos": lambda seed, n: ic.embryos_planetesimals(seed, 1024, n or 262144),
 }
 
 

@@ -55,6 +55,7 @@ def _bodies(n=3):
     (lambda b, p: b[1].__setitem__((2, 0), np.nan), "non-finite"),
     (lambda b, p: b[2].__setitem__((0, 1), np.inf), "non-finite"),
     (lambda b, p: b[1].__setitem__(0, [0.0, 0.0, 0.0]), "on the star"),
+    (lambda b, p: b[0].__setitem__(0, 0.0), "follows a small"),   # small bodies come after the big ones
     (lambda b, p: setattr(p, "dt", 0.0), "dt"),
     (lambda b, p: setattr(p, "dt", float("nan")), "dt"),
     (lambda b, p: setattr(p, "M0", -1.0), "M0"),
