@@ -11,32 +11,6 @@
 
 namespace opal {
 
-// Sum of the system's momentum segments, in a fixed order, broadcast to the
-// block.  Every block of a system gets the same bits.
-__device__ void system_momentum(const Dev& d, const double* part, const SysInfo& si, double* P3) {
-    __shared__ double red[3][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp == 0) {
-        double px = 0.0, py = 0.0, pz = 0.0;
-        for (int64_t k = lane; k < si.nseg; k += 32) {
-            int64_t sg = si.seg0 + k;
-            px += part[sg];
-            py += part[d.nseg_tot + sg];
-            pz += part[2 * d.nseg_tot + sg];
-        }
-        red[0][lane] = px;
-        red[1][lane] = py;
-        red[2][lane] = pz;
-        __syncwarp();
-        if (lane < 3) {
-            double s = 0.0;
-            for (int k = 0; k < 32; k++) s += red[lane][k];
-            P3[lane] = s;
-        }
-    }
-    __syncthreads();
-}
-
 // box of the path midpoints of the system's live bodies (block-reduced,
 // then one atomic per block and bound)
 __device__ void note_box(const Dev& d, int s, int64_t b) {
@@ -145,13 +119,14 @@ __global__ void k_prime(Dev d) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.ntot) return;
     int s = d.body_sys[b];
+    d.hcb[b] = cbrt(d.m[b] / (3.0 * d.p.M0));
     if (!d.alive[b]) {
         d.rc[b] = 0.0;
         park_floats(d, b);
         return;
     }
     double r = sqrt(dot3(d.x[b], d.y[b], d.z[b], d.x[b], d.y[b], d.z[b]));
-    double rc = d.p.rcrit_hill * r * cbrt(d.m[b] / (3.0 * d.p.M0));
+    double rc = d.p.rcrit_hill * r * d.hcb[b];
     d.rc[b] = rc;
     kick_floats(d, b, d.x[b], d.y[b], d.z[b], d.m[b], rc);
     note_rcmax(d, s, rc);
@@ -164,8 +139,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
     const SysInfo si = d.sys[s];
-    __shared__ double P[3];
-    system_momentum(d, d.pP_open, si, P);
+    const double* P = d.Ptot + 3 * s;   // momentum for the opening jump (summed by the last close)
     const double half = 0.5 * d.p.dt, M0 = d.p.M0;
     // undo copy of the start of the step
     double x = d.x[b], y = d.y[b], z = d.z[b], vx = d.vx[b], vy = d.vy[b], vz = d.vz[b];
@@ -192,7 +166,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
         d.x[b] = x; d.y[b] = y; d.z[b] = z;
         d.vx[b] = vx; d.vy[b] = vy; d.vz[b] = vz;
         double r1 = sqrt(dot3(x, y, z, x, y, z));
-        double rc = d.p.rcrit_hill * r1 * cbrt(d.m[b] / (3.0 * M0));
+        double rc = d.p.rcrit_hill * r1 * d.hcb[b];   // R_H = |x| cbrt(m / 3 M0), times f_hill
         d.rc[b] = rc;
         kick_floats(d, b, x, y, z, d.m[b], rc);
         note_rcmax(d, s, rc);
@@ -220,8 +194,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
     const SysInfo si = d.sys[s];
-    __shared__ double P[3];
-    if (!first) system_momentum(d, d.pP_close, si, P);
+    const double* P = d.Ptot + 3 * (d.nsys + s);   // momentum for the closing jump
     const double half = 0.5 * d.p.dt, G = d.p.G;
     const int64_t local = b - si.off;
     // the kick's partial rows, summed in row order; eight rows' loads are
@@ -296,6 +269,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
         d.ax[b] = 0.0; d.ay[b] = 0.0; d.az[b] = 0.0;
     }
     segment_sums(d, (int64_t)blockIdx.x * kBodyThreads, px, py, pz, d.pP_open);
+    system_total(d, d.pP_open, si, s, d.pcnt, d.Ptot + 3 * s);
     if (!first && (int64_t)blockIdx.x * kBodyThreads == si.off && threadIdx.x < 32) {
         // energy removed by this step's mergers in this system: groups come in
         // ascending order of their lowest member, so the system's groups are the
@@ -348,6 +322,7 @@ __global__ void k_finish(Dev d) {
         int b = d.members[k];
         if (d.undo[3 * k + 2] >= 0.0) {   // slot written when the BS results were applied
             d.m[b] = d.undo[3 * k];
+            d.hcb[b] = cbrt(d.m[b] / (3.0 * d.p.M0));
             d.R[b] = d.undo[3 * k + 1];
             d.alive[b] = (int)d.undo[3 * k + 2];
         }

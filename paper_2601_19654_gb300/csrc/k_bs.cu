@@ -50,11 +50,12 @@ struct BsSh {
     double diag[A][kBsRows][6][M];      // T[k][k] of every finished row (the accepted one is kept)
     double raw[A][6][M];                // midpoint result of the sequence finishing this round
     double df2[A][6][M], cur2[A][6][M]; // per component: squared change and squared value
-    double err[A][kBsRows][M];          // squared error ratio of each member, per finished row
+    int ok[A][kBsRows][M];              // each member passes the acceptance test, per finished row
     double m[M], R[M], rc[M];
     // per member: rc^2, 1 / (0.9 rc) and 0.1 rc (a pair uses the member with the larger rc)
     double prc2[M], pinv[M], pc01[M];
     int alive[M], gid[M];
+    int big[M];                         // a big body (a source of force), not a small one
     int kacc[A];                        // accepted row of each attempt, -1 while none
     int gi, kq[4];                      // cluster form: the group taken, every attempt's accepted row
     int decision, collide, nmerge;
@@ -103,14 +104,14 @@ __device__ void bs_merge(SH& S, const Params& p, int b, int q, double& El, int& 
 // (1 - K) weighted attraction of a member at (xb, yb, zb) towards one at
 // (xo, yo, zo) of mass mo, added to (ax, ay, az).  rc, rc2, c01, inv belong to
 // the member with the larger rc (rc_bo = max(rc_b, rc_o)): rc, rc^2, 0.1 rc and
-// 1 / (0.9 rc), so K needs no division by rc.  A small body (mo = 0) pulls
-// nothing (Sec. 2.1: only big bodies are gravity sources).
+// 1 / (0.9 rc), so K needs no division by rc.  Callers pass big members only:
+// a small body pulls nothing (Sec. 2.1: only big bodies are gravity sources).
 __device__ __forceinline__ void bs_pair(const Params& p, double xb, double yb, double zb, double xo, double yo,
                                         double zo, double mo, double rc, double rc2, double c01, double inv,
                                         double& ax, double& ay, double& az) {
     const double dx = xo - xb, dy = yo - yb, dz = zo - zb;
     const double dr2 = dx * dx + dy * dy + dz * dz;
-    if (dr2 >= rc2 || mo == 0.0) return;   // 1 - K = 0 at or beyond rc
+    if (dr2 >= rc2) return;   // 1 - K = 0 at or beyond rc
     const double dri = rsqrt(dr2), dr = dr2 * dri;
     double K;
     if (dr >= rc) {
@@ -139,8 +140,13 @@ __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, 
     ax = s * xb;
     ay = s * yb;
     az = s * zb;
-    for (int o = 0; o < nm; o++) {
-        if (o == b || !S.alive[o]) continue;
+    // the j-th other member in ascending order (the oracle's order): every lane
+    // has nm - 1 of them, so the lanes run each pass together (a loop over all
+    // o that skips o == b would run the FP64 pair code once per member, each
+    // time with a different lane idle)
+    for (int j = 0; j < nm - 1; j++) {
+        const int o = j + (j >= b ? 1 : 0);
+        if (!S.alive[o] || !S.big[o]) continue;   // (integer tests: no FP64 work)
         const int w = S.rc[b] > S.rc[o] ? b : o;   // rc_bo = max(rc_b, rc_o)
         bs_pair(p, xb, yb, zb, S.pos[a][k][0][o], S.pos[a][k][1][o], S.pos[a][k][2][o], S.m[o], S.rc[w],
                 S.prc2[w], S.pc01[w], S.pinv[w], ax, ay, az);
@@ -214,6 +220,8 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
             S.R[tid] = d.R[gb];
             S.rc[tid] = d.rc[gb];
             S.alive[tid] = d.alive[gb];
+            const SysInfo& gs = d.sys[d.body_sys[gb]];
+            S.big[tid] = gb - gs.off < gs.nb;
         }
         if (tid == 0) {
             S.El = 0.0;
@@ -304,33 +312,26 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                     }
                     __syncthreads();
                     if (lt < nm) {
-                        // this member passes (0) or fails (HUGE_VAL) the acceptance test
-                        double e2 = 0.0;
+                        // this member passes the acceptance test: |dX|^2 <= tol^2 |X|^2
+                        // and the same for V (the test without its divisions); a NaN fails
+                        int pass = 1;
                         if (kr >= 1 && S.alive[lt]) {
-                            double dsq_x = 0.0, dsq_v = 0.0, nx = 0.0, nv = 0.0;
-                            for (int c = 0; c < 3; c++) {
-                                dsq_x += S.df2[a][c][lt];
-                                nx += S.cur2[a][c][lt];
-                            }
-                            for (int c = 3; c < 6; c++) {
-                                dsq_v += S.df2[a][c][lt];
-                                nv += S.cur2[a][c][lt];
-                            }
-                            // |dX|^2 <= tol^2 |X|^2 and the same for V (the test without its
-                            // divisions); a NaN fails it.  0 passes, HUGE_VAL does not.
-                            e2 = (dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308)) ? 0.0
-                                                                                                         : HUGE_VAL;
+                            const double dsq_x = S.df2[a][0][lt] + S.df2[a][1][lt] + S.df2[a][2][lt];
+                            const double nx = S.cur2[a][0][lt] + S.cur2[a][1][lt] + S.cur2[a][2][lt];
+                            const double dsq_v = S.df2[a][3][lt] + S.df2[a][4][lt] + S.df2[a][5][lt];
+                            const double nv = S.cur2[a][3][lt] + S.cur2[a][4][lt] + S.cur2[a][5][lt];
+                            pass = dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308);
                         }
-                        S.err[a][kr][lt] = e2;
+                        S.ok[a][kr][lt] = pass;
                     }
                 }
                 __syncthreads();
                 if (r >= 4 && (r & 1) == 0) {
                     const int kr = r / 2 - 1;           // row finished this round
-                    if (lt == 0 && S.kacc[a] < 0) {
-                        double e2 = 0.0;
-                        for (int q = 0; q < nm; q++) e2 = fmax(e2, S.err[a][kr][q]);
-                        if (e2 <= tol2) S.kacc[a] = kr;
+                    if (lt == 0 && S.kacc[a] < 0 && kr >= 1) {
+                        int all = 1;
+                        for (int q = 0; q < nm; q++) all &= S.ok[a][kr][q];
+                        if (all) S.kacc[a] = kr;
                     }
                     if (CA > 1) {
                         // every attempt's row of this round is in place; each block reads all
@@ -461,9 +462,9 @@ struct PkWarp {
     double row[kBsRows][6][32];          // each lane's extrapolation tableau (in place)
     double y[6][32];                     // states at a substep's end (contacts, mergers)
     double px[32], py[32], pz[32];       // positions of the current evaluation
-    double err[32];
     double m[32], R[32], rc[32], prc2[32], pinv[32], pc01[32];
     int alive[32], gid[32];
+    int big[32];                         // a big body (a source of force), not a small one
     int seg_g[16];                       // group each segment took from the queue
 };
 
@@ -498,6 +499,7 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
                 g = W.seg_g[seg];
                 sz = g >= 0 ? d.goff[g + 1] - d.goff[g] : 0;
                 W.alive[lane] = 0;
+                W.big[lane] = 0;
                 if (sl < sz) {
                     mslot = d.goff[g] + sl;
                     const int gb = d.members[mslot];
@@ -512,6 +514,8 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
                     W.pc01[lane] = 0.1 * rc;
                     W.pinv[lane] = 1.0 / (0.9 * rc);
                     W.alive[lane] = d.alive[gb];
+                    const SysInfo& gs = d.sys[d.body_sys[gb]];
+                    W.big[lane] = gb - gs.off < gs.nb;
                 }
                 t = 0.0;
                 H = dt;
@@ -548,8 +552,9 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
                 const double r2 = P0 * P0 + P1 * P1 + P2 * P2, ri = rsqrt(r2);
                 const double sk = -GM0 * (ri * ri * ri);
                 double ax = sk * P0, ay = sk * P1, az = sk * P2;
-                for (int o = base; o < base + Wc; o++) {
-                    if (o == lane || !W.alive[o]) continue;
+                for (int j = 0; j < Wc - 1; j++) {   // the j-th other lane of the segment, ascending
+                    const int o = base + j + (j >= sl ? 1 : 0);
+                    if (!W.alive[o] || !W.big[o]) continue;
                     const int w = W.rc[lane] > W.rc[o] ? lane : o;
                     bs_pair(p, P0, P1, P2, W.px[o], W.py[o], W.pz[o], W.m[o], W.rc[w], W.prc2[w], W.pc01[w],
                             W.pinv[w], ax, ay, az);
@@ -562,7 +567,7 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
             const double h = H / n;
             const int stage = ms == 0 ? 0 : (ms < n ? 1 : 2);
             double cur[6] = {0, 0, 0, 0, 0, 0};
-            double e2 = 0.0;
+            bool pass = true;   // lanes without a live member never hold a segment back
             if (stage < 2) {
                 // first step z1 = y + h f; then z0 <- z1, z1 <- z0 + 2 h f
                 for (int q = 0; q < 6; q++) {
@@ -594,17 +599,15 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
                 }
                 if (k >= 1 && W.alive[lane]) {
                     // |dX|^2 <= tol^2 |X|^2 and the same for V; a NaN fails it
-                    e2 = (dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308)) ? 0.0 : HUGE_VAL;
+                    pass = dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308);
                 }
             }
-            W.err[lane] = e2;
-            __syncwarp();
+            // the segment's members all pass (a ballot: no FP64 work)
+            const bool seg_pass = (__ballot_sync(0xffffffffu, pass) & segmask) == segmask;
             // 0: on with the sequence, 1: next sequence, 2: accept row k, 3: reject the substep
             int decision = 0;
             if (active && stage == 2) {
-                double gerr = 0.0;
-                for (int o = base; o < base + Wc; o++) gerr = fmax(gerr, W.err[o]);
-                const bool acc = k >= 1 && gerr <= tol2;
+                const bool acc = k >= 1 && seg_pass;
                 decision = acc ? 2 : (k == kBsRows - 1 ? 3 : 1);
             }
             if (decision == 2 && live)

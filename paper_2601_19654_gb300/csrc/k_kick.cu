@@ -434,6 +434,7 @@ __global__ void __launch_bounds__(256) k_kick_apply(Dev d) {
         d.x[g] = o[0]; d.y[g] = o[1]; d.z[g] = o[2];
         d.vx[g] = o[3]; d.vy[g] = o[4]; d.vz[g] = o[5];
         d.m[g] = o[6];
+        d.hcb[g] = cbrt(o[6] / (3.0 * d.p.M0));
         d.R[g] = o[7];
         const int al = (int)o[8];
         d.alive[g] = al;
@@ -462,6 +463,7 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
         {
             const double m = al ? d.m[b] : 0.0;
             segment_sums(d, (int64_t)blockIdx.x * kFixThreads, m * d.vx[b], m * d.vy[b], m * d.vz[b], d.pP_close);
+            system_total(d, d.pP_close, d.sys[s], s, d.pcnt + d.nsys, d.Ptot + 3 * (d.nsys + s));
         }
         if (nm == 0 || !d.overlap) return;
         const int k0 = d.mlo[s], k1 = d.mhi[s];

@@ -373,7 +373,10 @@ __device__ __forceinline__ double dot3p(const double* a, const double* b) {
 // 16, evaluating d.d' at its two ends exactly as the sequential scan does,
 // and refines its bracket when the sign changes from - to +; the minimum over
 // the ends and the lanes' interior minima is the sequential result (a
-// minimum does not depend on the order its terms are visited in).
+// minimum does not depend on the order its terms are visited in).  Newton
+// starts from the secant point rather than the middle of the interval: the
+// iteration reaches the same root of g (to its 1e-12 stopping step), where
+// |d|^2 is flat, so the minimum agrees to rounding.
 __device__ double interval_min2(double T, int k, const double* d0, const double* u0, const double* d1,
                                 const double* u1) {
     double dd[3], dp[3], d2[3];
@@ -382,7 +385,11 @@ __device__ double interval_min2(double T, int k, const double* d0, const double*
     hermite_rel((k + 1) / 16.0, T, d0, u0, d1, u1, dd, dp, d2);
     const double gb = dot3p(dd, dp);
     if (!(ga < 0.0 && gb >= 0.0)) return HUGE_VAL;
-    double lo = k / 16.0, hi = (k + 1) / 16.0, s = 0.5 * (lo + hi);
+    // start at the secant root of g on the interval (close to the root, so
+    // Newton needs few steps); the minimum found is the same one
+    double lo = k / 16.0, hi = (k + 1) / 16.0;
+    double s = lo + (hi - lo) * (ga / (ga - gb));
+    if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
     for (int it = 0; it < 60; it++) {
         hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
         double g = dot3p(dd, dp), gp = dot3p(dp, dp) + dot3p(dd, d2);

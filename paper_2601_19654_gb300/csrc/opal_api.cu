@@ -332,7 +332,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
 
     double** f64[] = {&d.x, &d.y, &d.z, &d.vx, &d.vy, &d.vz, &d.ax, &d.ay, &d.az, &d.x0, &d.y0, &d.z0,
                       &d.vx0, &d.vy0, &d.vz0, &d.xs, &d.ys, &d.zs, &d.vxs, &d.vys, &d.vzs, &d.rcs,
-                      &d.m, &d.R, &d.rc};
+                      &d.m, &d.R, &d.rc, &d.hcb};
     for (auto pp : f64) TRYF(dalloc(s, pp, N));
     TRYF(dalloc(s, &d.alive, N));
     TRYF(dalloc(s, &d.body_sys, N));
@@ -355,6 +355,9 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.pacc_z, slots));
     TRYF(dalloc(s, &d.pP_close, 3 * d.nseg_tot));
     TRYF(dalloc(s, &d.pP_open, 3 * d.nseg_tot));
+    TRYF(dalloc(s, &d.Ptot, 6 * (int64_t)nsys));
+    TRYF(dalloc(s, &d.pcnt, 2 * (int64_t)nsys));
+    CKF(cudaMemsetAsync(d.pcnt, 0, 2 * nsys * sizeof(int), s->stream));
     d.flag_cap = P.encounter_capacity;
     d.cand_cap = std::max<int64_t>(1 << 16, 8 * d.flag_cap);
     d.near_cap = std::max<int64_t>(1 << 20, 64 * N);
@@ -560,6 +563,7 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
             cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), st);
             cudaMemsetAsync(d.gcount, 0, d.ntot * sizeof(int), st);
             cudaMemsetAsync(d.hctl, 0, sizeof(HugeCtl), st);
+            cudaMemsetAsync(d.pcnt, 0, 2 * d.nsys * sizeof(int), st);
             reset_scan_order(s);
             prof_mark("memsets");
             break;

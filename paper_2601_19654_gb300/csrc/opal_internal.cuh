@@ -148,6 +148,7 @@ struct Dev {
     double *x0, *y0, *z0, *vx0, *vy0, *vz0;      // start of drift
     double *xs, *ys, *zs, *vxs, *vys, *vzs, *rcs; // start of step (undo)
     double *m, *R, *rc;
+    double* hcb;                        // cbrt(m / 3 M0): the mass factor of the Hill radius
     int32_t* alive;
     // float copies for the pair kernels
     float4* kh;    // (x_hi, y_hi, z_hi, m) after drift / BS
@@ -164,6 +165,8 @@ struct Dev {
     double *pacc_x, *pacc_y, *pacc_z;   // kick partials [slot rows]
     double *pP_close;                   // [3][nseg_tot] momentum before the closing jump
     double *pP_open;                    // [3][nseg_tot] momentum before the opening jump
+    double* Ptot;                       // [2][nsys][3] those momenta summed: 0 opening, 1 closing jump
+    int* pcnt;                          // [2][nsys] blocks done with their segments (see system_total)
     int64_t nseg_tot;
     // spatial order of the scan: each system's bodies counting-sorted by the
     // cell of their path midpoint, and the box of every 64-body tile
@@ -247,6 +250,43 @@ __device__ __forceinline__ void segment_sums(const Dev& d, int64_t first_body, d
 }
 
 
+// After segment_sums into part: the last block of system s to get here sums
+// all the system's segments in a fixed order (each thread a strided set, then
+// a tree over the block) and stores the total in out[0..2], so the kernel
+// that needs it reads three numbers.  counter[s] is back at zero afterwards
+// (the step's memsets clear it too, in case a failing step left it behind).
+__device__ __forceinline__ void system_total(const Dev& d, const double* part, const SysInfo& si, int s,
+                                             int* counter, double* out) {
+    __shared__ int last;
+    __shared__ double red[3][kBodyThreads];
+    __syncthreads();   // this block's segment partials are written
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&counter[s], 1) == (int)(si.cap / kBodyThreads) - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double px = 0.0, py = 0.0, pz = 0.0;
+    for (int64_t k = threadIdx.x; k < si.nseg; k += kBodyThreads) {
+        const int64_t sg = si.seg0 + k;
+        px += __ldcg(part + sg);
+        py += __ldcg(part + d.nseg_tot + sg);
+        pz += __ldcg(part + 2 * d.nseg_tot + sg);
+    }
+    red[0][threadIdx.x] = px;
+    red[1][threadIdx.x] = py;
+    red[2][threadIdx.x] = pz;
+    __syncthreads();
+    for (int w = kBodyThreads / 2; w >= 1; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int c = 0; c < 3; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[threadIdx.x] = red[threadIdx.x][0];
+    if (threadIdx.x == 0) counter[s] = 0;
+}
+
 // Changeover weight K(r; rc): the rational form y^2/(2y^2-2y+1) or the
 // quintic 10y^3-15y^4+6y^5, y = (r - 0.1 rc)/(0.9 rc); 1 beyond rc, 0 below 0.1 rc.
 __device__ __forceinline__ double changeover(double r, double rc, int form) {
@@ -265,24 +305,30 @@ __device__ __forceinline__ float changeover_f(float r, float rc, int form) {
     return y * y * y * (10.0f - 15.0f * y + 6.0f * y * y);
 }
 
-// Stumpff functions c0..c3: at an argument quartered until |z| <= 0.1, c2 and
-// c3 by ten nested series terms (multiplying by the reciprocal of
-// (k+2j-1)(k+2j)), c0 = 1 - z c2 and c1 = 1 - z c3; then the double-angle
+// Stumpff functions c0..c3: at an argument quartered until |z| <= 0.1,
+//   c2 = sum_j (-z)^j / (2j+2)!,  c3 = sum_j (-z)^j / (2j+3)!,
+// by Horner's rule in -z over j = 0..6 (the next terms are below 1e-23 of the
+// sums there), c0 = 1 - z c2 and c1 = 1 - z c3; then the double-angle
 // relations undo the quartering.
 __device__ __forceinline__ void stumpff(double z, double& c0, double& c1, double& c2, double& c3) {
+    constexpr double k2[7] = {1.0 / 2, 1.0 / 24, 1.0 / 720, 1.0 / 40320, 1.0 / 3628800, 1.0 / 479001600,
+                              1.0 / 87178291200.0};
+    constexpr double k3[7] = {1.0 / 6, 1.0 / 120, 1.0 / 5040, 1.0 / 362880, 1.0 / 39916800, 1.0 / 6227020800.0,
+                              1.0 / 1307674368000.0};
     int nq = 0;
     while (fabs(z) > 0.1) {
         z *= 0.25;
         nq++;
     }
-    double s2 = 1.0, s3 = 1.0;
+    const double w = -z;
+    double s2 = k2[6], s3 = k3[6];
 #pragma unroll
-    for (int j = 10; j >= 1; j--) {
-        s2 = 1.0 - z * s2 * (1.0 / (double)((2 * j + 1) * (2 * j + 2)));
-        s3 = 1.0 - z * s3 * (1.0 / (double)((2 * j + 2) * (2 * j + 3)));
+    for (int j = 5; j >= 0; j--) {
+        s2 = fma(s2, w, k2[j]);
+        s3 = fma(s3, w, k3[j]);
     }
-    c2 = s2 * 0.5;
-    c3 = s3 * (1.0 / 6.0);
+    c2 = s2;
+    c3 = s3;
     c0 = 1.0 - z * c2;
     c1 = 1.0 - z * c3;
     for (; nq > 0; nq--) {
@@ -297,31 +343,38 @@ __device__ __forceinline__ void stumpff(double z, double& c0, double& c1, double
 // F(chi) = r0 G1 + eta G2 + mu G3 - dt (F increasing, root in [0, dt/q] with q
 // the pericentre distance), bisecting when a Newton step leaves the bracket;
 // bound orbits first drop whole periods from dt and start from dt / r0,
-// unbound ones start from the logarithmic value of Vallado's Algorithm 8.  Returns iterations used, or
-// -1 on non-convergence (state untouched).
+// unbound ones start from the logarithmic value of Vallado's Algorithm 8.
+// Returns iterations used, or -1 on non-convergence (state untouched).
+// Divisions are few: 1/r0 (from a reciprocal square root), 1/mu, one for the
+// bracket, one per Newton step and 1/r at the end; the period is only
+// formed when the step may exceed it.
 __device__ __forceinline__ int kepler_drift(double mu, double dt, int max_iter, double& x, double& y, double& z,
                                             double& vx, double& vy, double& vz) {
-    double r0 = sqrt(dot3(x, y, z, x, y, z));
+    const double rr = dot3(x, y, z, x, y, z);
+    const double ir0 = rsqrt(rr), r0 = rr * ir0;
     double v2 = dot3(vx, vy, vz, vx, vy, vz);
     double eta = dot3(x, y, z, vx, vy, vz);
-    double beta = 2.0 * mu / r0 - v2;
+    double beta = 2.0 * mu * ir0 - v2;
     if (beta > 0.0) {
-        double period = 2.0 * 3.14159265358979323846 * mu / (beta * sqrt(beta));
-        if (fabs(dt) > period) dt = fmod(dt, period);
+        // |dt| > period = 2 pi mu / beta^1.5, tested on the squares
+        const double tpm = 2.0 * 3.14159265358979323846 * mu;
+        if (dt * dt * (beta * beta * beta) > tpm * tpm) dt = fmod(dt, tpm / (beta * sqrt(beta)));
     }
+    const double imu = 1.0 / mu;
     double hx = y * vz - z * vy, hy = z * vx - x * vz, hz = x * vy - y * vx;
-    double p = dot3(hx, hy, hz, hx, hy, hz) / mu;
-    double ecc2 = 1.0 - p * beta / mu;
-    double q = p / (1.0 + sqrt(ecc2 > 0.0 ? ecc2 : 0.0));
+    double p = dot3(hx, hy, hz, hx, hy, hz) * imu;
+    double ecc2 = 1.0 - p * beta * imu;
+    // dt / q with q = p / (1 + e), the pericentre distance
+    const double dtq = dt * (1.0 + sqrt(ecc2 > 0.0 ? ecc2 : 0.0)) / p;
     double lo, hi;
     if (dt >= 0.0) {
         lo = 0.0;
-        hi = q > 0.0 ? dt / q : HUGE_VAL;
+        hi = p > 0.0 ? dtq : HUGE_VAL;
     } else {
-        lo = q > 0.0 ? dt / q : -HUGE_VAL;
+        lo = p > 0.0 ? dtq : -HUGE_VAL;
         hi = 0.0;
     }
-    double chi = dt / r0;
+    double chi = dt * ir0;
     if (beta < 0.0) {
         // unbound orbit: logarithmic starting value (Vallado, Algorithm 8)
         double a = mu / beta, sg = dt >= 0.0 ? 1.0 : -1.0;
@@ -355,8 +408,9 @@ __device__ __forceinline__ int kepler_drift(double mu, double dt, int max_iter, 
     stumpff(beta * chi * chi, c0, c1, c2, c3);
     double G0 = c0, G1 = chi * c1, G2 = chi * chi * c2, G3 = chi * chi * chi * c3;
     double r = r0 * G0 + eta * G1 + mu * G2;
-    double f = 1.0 - mu * G2 / r0, g = dt - mu * G3;
-    double fd = -mu * G1 / (r * r0), gd = 1.0 - mu * G2 / r;
+    const double ir = 1.0 / r;
+    double f = 1.0 - mu * G2 * ir0, g = dt - mu * G3;
+    double fd = -mu * G1 * (ir * ir0), gd = 1.0 - mu * G2 * ir;
     double nx = f * x + g * vx, ny = f * y + g * vy, nz = f * z + g * vz;
     double nvx = fd * x + gd * vx, nvy = fd * y + gd * vy, nvz = fd * z + gd * vz;
     x = nx; y = ny; z = nz;
