@@ -58,7 +58,8 @@ struct BsSh {
     int big[M];                         // a big body (a source of force), not a small one
     int kacc[A];                        // accepted row of each attempt, -1 while none
     int gi, kq[4];                      // cluster form: the group taken, every attempt's accepted row
-    int decision, collide, nmerge;
+    int decision, collide, nmerge;      // (cluster form: decision holds the substep attempt 0 accepted)
+    int dec;                            // cluster form: the attempt taken after a substep
     double El;
 };
 
@@ -182,7 +183,13 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
     const int a = tid / TA, lt = tid % TA;
     const int cap = p.bs_max_substeps;
     const double tol2 = p.bs_tol * p.bs_tol;
+    static_assert(CA == 1 || NT == 32, "the cluster form has one warp per attempt");
     __shared__ int s_gi;
+    // cluster form: substeps are numbered (the same in every block); attempt 0
+    // announces an acceptance by writing its substep number into every block's
+    // decision, so no stale announcement can be taken for a later substep
+    int epoch = 0;
+    if (tid == 0) S.decision = -1;
     for (;;) {
         // blocks take groups from a queue, so a long group holds up only its own block
         __syncthreads();
@@ -254,7 +261,8 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
             if (act)
                 for (int c = 0; c < 6; c++) za[c] = zb[c] = S.y[c][b];
             if (lt == 0) S.kacc[a] = -1;
-            if (tid == 0) S.decision = -1;
+            if (CA == 1 && tid == 0) S.decision = -1;
+            epoch++;
             __syncthreads();
             for (int r = 0; r <= 2 * kBsRows; r++) {
                 const bool live = act && r <= n;
@@ -334,18 +342,16 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                         if (all) S.kacc[a] = kr;
                     }
                     if (CA > 1) {
-                        // every attempt's row of this round is in place; each block reads all
-                        // of them, then waits until all have read before any moves on
-                        cg::this_cluster().sync();
-                        if (tid == 0)
-                            for (int q = 0; q < CA; q++) S.kq[q] = cg::this_cluster().map_shared_rank(&S, q)->kacc[0];
-                        cg::this_cluster().sync();
+                        // attempt 0 accepted: every block of the cluster learns it
+                        __syncthreads();
+                        if (arank == 0 && tid == 0 && S.kacc[0] >= 0)
+                            for (int q = 0; q < CA; q++) cg::this_cluster().map_shared_rank(&S, q)->decision = epoch;
                     } else {
                         __syncthreads();
                         if (tid == 0)
                             for (int q = 0; q < A; q++) S.kq[q] = S.kacc[q];
                     }
-                    if (tid == 0) {
+                    if (CA == 1 && tid == 0) {
                         // attempt 0 accepted: done; at the last round every attempt has
                         // decided and the first accepted one (in halving order) is taken
                         constexpr int NA = CA > 1 ? CA : A;
@@ -357,11 +363,33 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                             S.decision = dcs;
                         }
                     }
-                    __syncthreads();
-                    if (S.decision >= 0) break;
+                    if (CA == 1) {
+                        __syncthreads();
+                        if (S.decision >= 0) break;
+                    }
+                }
+                if (CA > 1) {
+                    // every round: has attempt 0 announced this substep?  (one warp)
+                    int seen = 0;
+                    if (tid == 0) seen = *reinterpret_cast<volatile int*>(&S.decision) == epoch;
+                    if (__shfl_sync(0xffffffffu, seen, 0)) break;
                 }
             }
-            const int dec = S.decision;
+            if (CA > 1) {
+                // every block is out of its rounds; each reads every attempt's row
+                // and takes the first accepted one in halving order (all alike)
+                cg::this_cluster().sync();
+                if (tid == 0) {
+                    int dcs = CA;
+                    for (int q = CA - 1; q >= 0; q--) {
+                        S.kq[q] = cg::this_cluster().map_shared_rank(&S, q)->kacc[0];
+                        if (S.kq[q] >= 0) dcs = q;
+                    }
+                    S.dec = dcs;
+                }
+                __syncthreads();
+            }
+            const int dec = CA > 1 ? S.dec : S.decision;
             // replay the sequential control flow over the attempts just made
             constexpr int NA = CA > 1 ? CA : A;
             for (int q = 0; q < NA; q++) {
@@ -370,11 +398,11 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                 if (q == dec) {
                     const int kacc = S.kq[q];
                     if (CA > 1) {
-                        // the accepted state from attempt q's block; all copy before it moves on
+                        // the accepted state from attempt q's block (the cluster barrier
+                        // after the replay keeps it there until every block has it)
                         if (lt < 6 * nm)
                             S.y[lt / nm][lt % nm] =
                                 cg::this_cluster().map_shared_rank(&S, q)->diag[0][kacc][lt / nm][lt % nm];
-                        cg::this_cluster().sync();
                     } else if (a == q && lt < 6 * nm) {
                         S.y[lt / nm][lt % nm] = S.diag[q][kacc][lt / nm][lt % nm];
                     }
@@ -419,6 +447,9 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                 }
             }
             if (dec == NA && !failed) H = ldexp(H, -NA);   // every attempt rejected
+            // cluster form: no block resets its accepted row or overwrites its
+            // tableau before every block has read them
+            if (CA > 1) cg::this_cluster().sync();
             __syncthreads();
         }
         if (failed) {
