@@ -394,7 +394,36 @@ __global__ void __launch_bounds__(kBodyThreads) k_order_prep(Dev d) {
     note_box(d, s, b);   // every thread of the block, from this one call site
 }
 
+// Start of a step: the counters, bounds and scratch the step's kernels
+// accumulate into, zeroed or preset in one launch (rather than ten memsets).
+__global__ void __launch_bounds__(256) k_step_reset(Dev d) {
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    int* c = reinterpret_cast<int*>(reinterpret_cast<char*>(d.ctl) + offsetof(Ctl, ncand));
+    constexpr int nc = (int)((offsetof(Ctl, steps_done) - offsetof(Ctl, ncand)) / sizeof(int));
+    int* h = reinterpret_cast<int*>(d.hctl);
+    constexpr int nh = (int)(sizeof(HugeCtl) / sizeof(int));
+    for (int64_t i = i0; i < d.ntot; i += st) d.gcount[i] = 0;
+    for (int64_t i = i0; i < d.ncell; i += st) d.cstart[i] = 0;
+    for (int64_t i = i0; i < nc; i += st) c[i] = 0;
+    for (int64_t i = i0; i < nh; i += st) h[i] = 0;
+    for (int64_t i = i0; i < d.nsys; i += st) {
+        d.rcmax[i] = 0.0f;
+        d.mlo[i] = 0x7f7f7f7f;                     // above any member slot
+        d.mhi[i] = 0;
+        d.pcnt[i] = 0;
+        d.pcnt[d.nsys + i] = 0;
+    }
+    for (int64_t i = i0; i < 3 * d.nsys; i += st) {
+        d.sbox[i] = 0x7f7f7f7f;                    // order-mapped +huge: the min starts above everything
+        d.sbox[3 * d.nsys + i] = (int)0x80808080;  // and the max below
+    }
+}
+
 // ---------------------------------------------------------------------------
+void launch_step_reset(const Dev& d, int nsm, cudaStream_t s) {
+    k_step_reset<<<2 * nsm, 256, 0, s>>>(d);
+    prof_mark("memsets");
+}
 void launch_order_prep(const Dev& d, cudaStream_t s) {
     k_order_prep<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d);
 }

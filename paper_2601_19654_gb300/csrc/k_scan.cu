@@ -272,6 +272,7 @@ __device__ __forceinline__ bool boxes_overlap(const float* a, const float* b) {
 __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
     __shared__ float4 sj[kSeg];
     __shared__ int gj[kSeg];
+    __shared__ unsigned smask[kSeg / 32][kSeg];
     if (d.ctl->status) return;
     const int lane = threadIdx.x & 31;
     for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
@@ -289,6 +290,11 @@ __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __re
         gj[threadIdx.x] = d.csorted[tl.j0 + threadIdx.x];
         __syncthreads();
         const bool diag = tl.i0 == tl.j0;
+        // pass 1: each warp's ballots of the tile pair, and their total; pass 2:
+        // one atomic reserves the warp's room in the list, then every passing
+        // lane writes its pair (one atomic per warp and tile pair, not per column)
+        const int warp = threadIdx.x >> 5;
+        int cnt = 0;
 #pragma unroll 4
         for (int jj = 0; jj < kSeg; jj++) {
             const float4 cj = sj[jj];
@@ -297,18 +303,24 @@ __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __re
             float Ts = ci.w + cj.w;
             // two small bodies never interact
             bool pass = (!diag || jj > (int)threadIdx.x) && (r2 < Ts * Ts) && (ibig || gj[jj] < big_end);
-            unsigned mask = __ballot_sync(0xffffffffu, pass);
-            if (mask) {
-                int leader = __ffs(mask) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&d.ctl->nnear, __popc(mask));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (pass) {
-                    int idx = base + __popc(mask & ((1u << lane) - 1u));
-                    int a = gi, b = gj[jj];
-                    if (idx < d.near_cap) d.near[idx] = make_int2(min(a, b), max(a, b));
-                }
+            const unsigned mask = __ballot_sync(0xffffffffu, pass);
+            if (lane == 0) smask[warp][jj] = mask;
+            cnt += __popc(mask);
+        }
+        if (cnt == 0) continue;                     // the same for the whole warp
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&d.ctl->nnear, cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        __syncwarp();
+        const unsigned below = (1u << lane) - 1u;
+        for (int jj = 0; jj < kSeg; jj++) {
+            const unsigned mask = smask[warp][jj];
+            if ((mask >> lane) & 1u) {
+                const int idx = base + __popc(mask & below);
+                const int b2 = gj[jj];
+                if (idx < d.near_cap) d.near[idx] = make_int2(min(gi, b2), max(gi, b2));
             }
+            base += __popc(mask);
         }
     }
 }

@@ -138,7 +138,7 @@ bool finite_all(const double* a, int64_t n) {
 }
 
 // The kick's work list: i-tiles of itile bodies against j-chunks of the system's
-// first n places, chunk edges on whole j-tiles.  The kick takes items from a
+// first nb places (its big bodies), chunk edges on whole j-tiles.  The kick takes items from a
 // queue, largest first; about eight items per resident block keep the tail
 // short.  Chunks of one system are of equal length to within a tile.
 void build_kick_items(opal_sim* s, int slots, int itile) {
@@ -555,18 +555,7 @@ constexpr int kStageBs = 5, kStageKick = 6, kStageApply = 7;
 void launch_stage(opal_sim* s, int k, cudaStream_t st) {
     const Dev& d = s->d;
     switch (k) {
-        case 0:
-            cudaMemsetAsync(reinterpret_cast<char*>(d.ctl) + offsetof(Ctl, ncand), 0,
-                            offsetof(Ctl, steps_done) - offsetof(Ctl, ncand), st);
-            cudaMemsetAsync(d.rcmax, 0, d.nsys * sizeof(float), st);
-            cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), st);
-            cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), st);
-            cudaMemsetAsync(d.gcount, 0, d.ntot * sizeof(int), st);
-            cudaMemsetAsync(d.hctl, 0, sizeof(HugeCtl), st);
-            cudaMemsetAsync(d.pcnt, 0, 2 * d.nsys * sizeof(int), st);
-            reset_scan_order(s);
-            prof_mark("memsets");
-            break;
+        case 0: launch_step_reset(d, s->nsm, st); break;
         case 1: launch_open(d, st); break;
         case 2: launch_scan(d, s->d_tiles, (int64_t)s->tiles.size(), s->scan_grid, st); break;
         case 3: launch_confirm(d, s->confirm_grid, st); break;

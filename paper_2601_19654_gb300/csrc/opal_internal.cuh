@@ -482,6 +482,7 @@ void launch_open(const Dev& d, cudaStream_t s);
 // caller resets the buckets and notes the boxes first
 void launch_sort_bodies(const Dev& d, cudaStream_t s);
 void launch_order_prep(const Dev& d, cudaStream_t s);
+void launch_step_reset(const Dev& d, int nsm, cudaStream_t s);
 void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s);
 void launch_confirm(const Dev& d, int grid, cudaStream_t s);
 void launch_group(const Dev& d, int nsm, cudaStream_t s);
