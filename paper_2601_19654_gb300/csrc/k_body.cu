@@ -235,9 +235,16 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
                 ay = d.cfy[b];
                 az = d.cfz[b];
             } else {
-                ax += d.cfx[b];
-                ay += d.cfy[b];
-                az += d.cfz[b];
+                double cx = d.cfx[b], cy = d.cfy[b], cz = d.cfz[b];
+#pragma unroll
+                for (int q = 1; q < kFixParts; q++) {
+                    cx += d.cfx[q * d.ntot + b];
+                    cy += d.cfy[q * d.ntot + b];
+                    cz += d.cfz[q * d.ntot + b];
+                }
+                ax += cx;
+                ay += cy;
+                az += cz;
             }
         }
     }

@@ -456,17 +456,21 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
     const int nm = d.ctl->ninvolved;
     const int form = d.p.changeover;
     const bool mixed = d.p.precision == 1;
-    if ((int)blockIdx.x < nbody_blocks) {
-        const int64_t b = (int64_t)blockIdx.x * kFixThreads + threadIdx.x;
-        const int s = d.body_sys[(int64_t)blockIdx.x * kFixThreads];
+    if ((int)blockIdx.x < nbody_blocks * kFixParts) {
+        // body block bb, part q of the system's members (q = 0 also sums momenta)
+        const int bb = (int)blockIdx.x % nbody_blocks, q = (int)blockIdx.x / nbody_blocks;
+        const int64_t b = (int64_t)bb * kFixThreads + threadIdx.x;
+        const int s = d.body_sys[(int64_t)bb * kFixThreads];
         const bool al = d.alive[b] != 0;
-        {
+        if (q == 0) {
             const double m = al ? d.m[b] : 0.0;
-            segment_sums(d, (int64_t)blockIdx.x * kFixThreads, m * d.vx[b], m * d.vy[b], m * d.vz[b], d.pP_close);
+            segment_sums(d, (int64_t)bb * kFixThreads, m * d.vx[b], m * d.vy[b], m * d.vz[b], d.pP_close);
             system_total(d, d.pP_close, d.sys[s], s, d.pcnt + d.nsys, d.Ptot + 3 * (d.nsys + s));
         }
         if (nm == 0 || !d.overlap) return;
-        const int k0 = d.mlo[s], k1 = d.mhi[s];
+        const int ka = d.mlo[s], kz = d.mhi[s];
+        const int k0 = ka + (int)((int64_t)(kz - ka) * q / kFixParts);
+        const int k1 = ka + (int)((int64_t)(kz - ka) * (q + 1) / kFixParts);
         const int64_t big_end = d.sys[s].off + d.sys[s].nb;
         const bool want = al && d.label[b] < 0;   // members get their full rows below
         const float rcm = d.rcmax[s];
@@ -545,15 +549,17 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
                 cy = (double)hy + (double)ly;
                 cz = (double)hz + (double)lz;
             }
-            d.cfx[b] = cx;
-            d.cfy[b] = cy;
-            d.cfz[b] = cz;
+            const int64_t o = (int64_t)q * d.ntot + b;   // this part's share of the correction
+            d.cfx[o] = cx;
+            d.cfy[o] = cy;
+            d.cfz[o] = cz;
         }
         return;
     }
     // member rows, one block per member at a time
     if (!d.overlap) return;
-    for (int k = (int)blockIdx.x - nbody_blocks; k < nm; k += (int)gridDim.x - nbody_blocks) {
+    const int first = nbody_blocks * kFixParts;
+    for (int k = (int)blockIdx.x - first; k < nm; k += (int)gridDim.x - first) {
         const int g = d.members[k];
         const int s = d.body_sys[g];
         const SysInfo si = d.sys[s];
@@ -647,7 +653,7 @@ void launch_bs_apply(const Dev& d, int nsm, cudaStream_t s) {
 
 void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s) {
     const int nb = (int)(d.ntot / kFixThreads);
-    k_kick_fix<<<nb + 2 * nsm, kFixThreads, 0, s>>>(d, nb);
+    k_kick_fix<<<nb * kFixParts + 2 * nsm, kFixThreads, 0, s>>>(d, nb);
     prof_mark("kick fix: member rows and corrections");
 }
 

@@ -407,9 +407,9 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     CKF(cudaMemsetAsync(d.gcount, 0, N * sizeof(int), s->stream));
     TRYF(dalloc(s, &d.mlo, nsys));
     TRYF(dalloc(s, &d.mhi, nsys));
-    TRYF(dalloc(s, &d.cfx, N));
-    TRYF(dalloc(s, &d.cfy, N));
-    TRYF(dalloc(s, &d.cfz, N));
+    TRYF(dalloc(s, &d.cfx, kFixParts * N));
+    TRYF(dalloc(s, &d.cfy, kFixParts * N));
+    TRYF(dalloc(s, &d.cfz, kFixParts * N));
     TRYF(dalloc(s, &d.E_lost, nsys));
     TRYF(dalloc(s, &d.ctl, 1));
     TRYF(dalloc(s, &d.sys, nsys));

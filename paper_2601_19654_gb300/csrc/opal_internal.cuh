@@ -21,6 +21,7 @@ constexpr int kKickJTile = 256;     // j-bodies the kick stages in shared memory
 constexpr int kBsManyGroups = 608;  // above this many groups a step integrates them packed, lane per member
 constexpr int kBucketDiv = 4;       // body slots per bucket of the spatial sort (cap / 4 buckets a system)
 constexpr int kBsOut = 9;           // doubles per member slot of the BS side buffer: x, V, m, R, alive
+constexpr int kFixParts = 4;        // the kick's correction after the encounters: member ranges per body
 constexpr int kBsRows = 8;          // extrapolation rows: n_k = 2, 4, ..., 16
 constexpr float kFar = 1.0e18f;     // parking coordinate of ghost and dead bodies (float copies)
 
@@ -204,7 +205,7 @@ struct Dev {
     D4* okx;                            // per member slot: x, y, z, m before it
     int* mlo;                           // [nsys] first member slot of the system (or a large value)
     int* mhi;                           // [nsys] one past its last member slot (or 0)
-    double *cfx, *cfy, *cfz;            // per body: kick correction (others) or full row (members)
+    double *cfx, *cfy, *cfz;            // [kFixParts][ntot]: kick correction parts (others), full row in part 0 (members)
     double* E_lost;                     // per system running sum
     Ctl* ctl;
 };
