@@ -726,14 +726,344 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Groups of up to four members (nearly every encounter): the four attempts
+// (step sizes H, H/2, H/4, H/8) are the four blocks of a cluster, and each
+// block splits a round's FP64 work between two warps, which the SM issues
+// from two of its schedulers, each with its own FP64 unit:
+//   warp 0: the stellar term, the midpoint step, and on even rounds the new
+//           row of the extrapolation tableau, the acceptance test and the
+//           decision;
+//   warp 1: the (1 - K) mutual terms.
+// On this chip a warp pays about the same for an FP64 instruction whatever
+// its dependences, so a round costs what its longer warp issues.  Two named
+// barriers hand over each round: the positions of the next evaluation
+// (warp 0 -> 1) and the mutual terms (1 -> 0).  Warp 0 hands over the
+// positions before it extrapolates, so the extrapolation overlaps the next
+// round's mutual terms; a stop is then seen by warp 1 one round late, and
+// the terms of that round are dropped.  Lanes of both warps: k * nm + b
+// (sequence k, member b).  Attempt 0 announces its acceptance to the other
+// blocks through distributed shared memory, as in the one-warp cluster form.
+struct WsSh {
+    static constexpr int M = 4;
+    double y[6][M];                      // current state, component-major
+    double pos[kBsRows][3][M];           // positions of the round's evaluation, per sequence
+    double pacc[kBsRows][3][M];          // mutual terms of the round, per sequence
+    double row[kBsRows][6][M];           // the last extrapolated row of each member
+    double diag[kBsRows][6][M];          // T[k][k] of every finished row
+    double raw[6][M];                    // midpoint result of the sequence finishing this round
+    double df2[6][M], cur2[6][M];
+    double m[M], R[M], rc[M], prc2[M], pinv[M], pc01[M];
+    int alive[M], gid[M], big[M], ok[M];
+    int kacc;                            // this block's attempt: accepted row, -1 while none
+    int stop;                            // warp 0 tells warp 1 that the rounds are over
+    int decision;                        // the substep number attempt 0 announced
+    int dec, gi, collide, nmerge;
+    int kq[4];
+    double El;
+};
+
+constexpr int kWsThreads = 64;
+constexpr int kBarPos = 1;    // named barrier: next positions written (warp 0 arrives, warp 1 waits)
+constexpr int kBarPair = 2;   // named barrier: mutual terms written (warp 1 arrives, warp 0 waits)
+
+__device__ __forceinline__ void ws_bar_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kWsThreads) : "memory");
+}
+__device__ __forceinline__ void ws_bar_arrive(int id) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "n"(kWsThreads) : "memory");
+}
+
+__global__ void __launch_bounds__(kWsThreads) k_bs_ws(Dev d) {
+    __shared__ WsSh S;
+    __shared__ int s_gi;
+    constexpr int CA = 4, M = WsSh::M;
+    cg::cluster_group cl = cg::this_cluster();
+    const int arank = (int)cl.block_rank();
+    // (no status check: every block of a cluster must take the same path, and
+    // another kernel may set the status while the cluster's blocks start)
+    const Params p = d.p;
+    const bool many = d.ctl->ngroups > kBsManyGroups;
+    const int* list = many ? d.ghard : nullptr;
+    const int ng = many ? d.ctl->nhard : d.ctl->ngroups;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool w0 = tid < 32;
+    const int cap = p.bs_max_substeps;
+    const double tol2 = p.bs_tol * p.bs_tol, GM0 = p.G * p.M0;
+    int epoch = 0;
+    if (tid == 0) S.decision = -1;
+    for (;;) {
+        __syncthreads();
+        if (arank == 0 && tid == 0) S.gi = atomicAdd(&d.ctl->qlock[0], 1);
+        cl.sync();
+        if (tid == 0) s_gi = cl.map_shared_rank(&S, 0)->gi;
+        cl.sync();
+        const int gi = s_gi;
+        if (gi >= ng) break;
+        const int g = list ? list[gi] : gi;
+        const int mb = d.goff[g], nm = d.goff[g + 1] - mb;
+        if (nm > M) continue;                // a larger group: the other lockstep kernels'
+        const int k = lane / nm, b = lane % nm;
+        const bool act = k < kBsRows;
+        if (tid < nm) {
+            const int gb = d.members[mb + tid];
+            S.gid[tid] = gb;
+            S.y[0][tid] = d.x0[gb];
+            S.y[1][tid] = d.y0[gb];
+            S.y[2][tid] = d.z0[gb];
+            S.y[3][tid] = d.vx0[gb];
+            S.y[4][tid] = d.vy0[gb];
+            S.y[5][tid] = d.vz0[gb];
+            S.m[tid] = d.m[gb];
+            S.R[tid] = d.R[gb];
+            const double rcp = d.rc[gb];
+            S.rc[tid] = rcp;
+            S.prc2[tid] = rcp * rcp;
+            S.pc01[tid] = 0.1 * rcp;
+            S.pinv[tid] = 1.0 / (0.9 * rcp);
+            S.alive[tid] = d.alive[gb];
+            const SysInfo& gs = d.sys[d.body_sys[gb]];
+            S.big[tid] = gb - gs.off < gs.nb;
+        }
+        if (tid == 0) {
+            S.El = 0.0;
+            S.nmerge = 0;
+        }
+        __syncthreads();
+        const double dt = p.dt;
+        const int n = 2 * (k + 1);
+        double t = 0.0, H = dt;
+        int nsub = 0, failed = 0, finished = 0;
+        while (!finished && !failed) {
+            double rem = dt - t;
+            int last0 = 0;
+            if (fabs(H) >= fabs(rem)) {
+                H = rem;
+                last0 = 1;
+            }
+            const double h = ldexp(H, -arank) / n;
+            epoch++;
+            if (w0) {
+                // ---- warp 0: stellar terms, midpoint steps, extrapolation, decision
+                double za[6], zb[6];
+                if (act) {
+                    for (int c = 0; c < 6; c++) za[c] = zb[c] = S.y[c][b];
+                    S.pos[k][0][b] = za[0];
+                    S.pos[k][1][b] = za[1];
+                    S.pos[k][2][b] = za[2];
+                }
+                if (lane == 0) {
+                    S.kacc = -1;
+                    S.stop = 0;
+                }
+                ws_bar_arrive(kBarPos);          // round 0's positions
+                for (int r = 0;; r++) {
+                    const bool live = act && r <= n && S.alive[b];
+                    double sx = 0.0, sy = 0.0, sz = 0.0;
+                    const double px = r == 0 ? za[0] : zb[0], py = r == 0 ? za[1] : zb[1],
+                                 pz = r == 0 ? za[2] : zb[2];
+                    if (live) {
+                        const double r2 = px * px + py * py + pz * pz, ri = rsqrt(r2);
+                        const double sk = -GM0 * (ri * ri * ri);
+                        sx = sk * px;
+                        sy = sk * py;
+                        sz = sk * pz;
+                    }
+                    ws_bar_sync(kBarPair);       // the mutual terms of round r
+                    if (act && r <= n) {
+                        double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                        if (live) {
+                            f[0] = r == 0 ? za[3] : zb[3];
+                            f[1] = r == 0 ? za[4] : zb[4];
+                            f[2] = r == 0 ? za[5] : zb[5];
+                            f[3] = sx + S.pacc[k][0][b];
+                            f[4] = sy + S.pacc[k][1][b];
+                            f[5] = sz + S.pacc[k][2][b];
+                        }
+                        if (r == 0) {
+                            for (int c = 0; c < 6; c++) zb[c] = za[c] + h * f[c];
+                        } else if (r < n) {
+                            for (int c = 0; c < 6; c++) {
+                                const double znew = za[c] + 2.0 * h * f[c];
+                                za[c] = zb[c];
+                                zb[c] = znew;
+                            }
+                        } else {
+                            for (int c = 0; c < 6; c++) S.raw[c][b] = 0.5 * (zb[c] + za[c] + h * f[c]);
+                        }
+                        if (r < n) {
+                            S.pos[k][0][b] = zb[0];
+                            S.pos[k][1][b] = zb[1];
+                            S.pos[k][2][b] = zb[2];
+                        }
+                    }
+                    ws_bar_arrive(kBarPos);      // warp 1 goes on with round r + 1
+                    if (r >= 2 && (r & 1) == 0) {
+                        // row kr of the tableau: sequence kr finished this round
+                        const int kr = r / 2 - 1;
+                        __syncwarp();
+                        if (lane < 6 * nm) {
+                            const int c = lane / nm, bb = lane % nm;
+                            double cur = S.raw[c][bb], prev_col = 0.0;
+                            for (int j = 1; j <= kr; j++) {
+                                const double up = S.row[j - 1][c][bb];
+                                S.row[j - 1][c][bb] = cur;
+                                prev_col = cur;
+                                cur = cur + (cur - up) * kNeville[kr][j];
+                            }
+                            S.row[kr][c][bb] = cur;
+                            S.diag[kr][c][bb] = cur;
+                            const double df = cur - prev_col;
+                            S.df2[c][bb] = df * df;
+                            S.cur2[c][bb] = cur * cur;
+                        }
+                        __syncwarp();
+                        if (lane < nm) {
+                            int pass = 1;
+                            if (kr >= 1 && S.alive[lane]) {
+                                const double dsq_x = S.df2[0][lane] + S.df2[1][lane] + S.df2[2][lane];
+                                const double nx = S.cur2[0][lane] + S.cur2[1][lane] + S.cur2[2][lane];
+                                const double dsq_v = S.df2[3][lane] + S.df2[4][lane] + S.df2[5][lane];
+                                const double nv = S.cur2[3][lane] + S.cur2[4][lane] + S.cur2[5][lane];
+                                pass = dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308);
+                            }
+                            S.ok[lane] = pass;
+                        }
+                        __syncwarp();
+                        if (lane == 0 && kr >= 1 && S.kacc < 0) {
+                            int all = 1;
+                            for (int q = 0; q < nm; q++) all &= S.ok[q];
+                            if (all) {
+                                S.kacc = kr;
+                                if (arank == 0)
+                                    for (int q = 0; q < CA; q++) cl.map_shared_rank(&S, q)->decision = epoch;
+                            }
+                        }
+                    }
+                    // stop: this attempt accepted, attempt 0 announced, or every row done
+                    int st = 0;
+                    if (lane == 0)
+                        st = S.kacc >= 0 || *reinterpret_cast<volatile int*>(&S.decision) == epoch ||
+                             r == 2 * kBsRows;
+                    if (__shfl_sync(0xffffffffu, st, 0)) {
+                        ws_bar_sync(kBarPair);   // warp 1's terms of round r + 1, dropped
+                        if (lane == 0) S.stop = 1;
+                        ws_bar_arrive(kBarPos);
+                        break;
+                    }
+                }
+            } else {
+                // ---- warp 1: the mutual terms of each round
+                for (int r = 0;; r++) {
+                    ws_bar_sync(kBarPos);
+                    if (*reinterpret_cast<volatile int*>(&S.stop)) break;
+                    if (act && r <= n && S.alive[b]) {
+                        const double px = S.pos[k][0][b], py = S.pos[k][1][b], pz = S.pos[k][2][b];
+                        double ax = 0.0, ay = 0.0, az = 0.0;
+                        for (int j = 0; j < nm - 1; j++) {   // the other members, ascending
+                            const int o = j + (j >= b ? 1 : 0);
+                            if (!S.alive[o] || !S.big[o]) continue;
+                            const int w = S.rc[b] > S.rc[o] ? b : o;
+                            bs_pair(p, px, py, pz, S.pos[k][0][o], S.pos[k][1][o], S.pos[k][2][o], S.m[o], S.rc[w],
+                                    S.prc2[w], S.pc01[w], S.pinv[w], ax, ay, az);
+                        }
+                        S.pacc[k][0][b] = ax;
+                        S.pacc[k][1][b] = ay;
+                        S.pacc[k][2][b] = az;
+                    }
+                    ws_bar_arrive(kBarPair);
+                }
+            }
+            __syncthreads();
+            // every block is out of its rounds: the first accepted attempt in
+            // halving order is taken, the same in every block
+            cl.sync();
+            if (tid == 0) {
+                int dcs = CA;
+                for (int q = CA - 1; q >= 0; q--) {
+                    S.kq[q] = cl.map_shared_rank(&S, q)->kacc;
+                    if (S.kq[q] >= 0) dcs = q;
+                }
+                S.dec = dcs;
+            }
+            __syncthreads();
+            const int dec = S.dec;
+            // replay the sequential control flow over the attempts just made
+            for (int q = 0; q < CA; q++) {
+                nsub++;
+                const double Hq = ldexp(H, -q);
+                if (q == dec) {
+                    const int kacc = S.kq[q];
+                    if (tid < 6 * nm) S.y[tid / nm][tid % nm] = cl.map_shared_rank(&S, q)->diag[kacc][tid / nm][tid % nm];
+                    const int lastq = (q == 0) ? last0 : 0;
+                    t = lastq ? dt : t + Hq;
+                    if (tid == 0) S.collide = 0;
+                    __syncthreads();
+                    // any pair in contact?  (exact sequential resolution only if so)
+                    for (int e = tid; e < nm * nm; e += kWsThreads) {
+                        const int u = e / nm, w = e % nm;
+                        if (w > u && S.alive[u] && S.alive[w] && bs_can_touch(S.m[u], S.m[w])) {
+                            const double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
+                                         dz = S.y[2][w] - S.y[2][u];
+                            if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w]) S.collide = 1;
+                        }
+                    }
+                    __syncthreads();
+                    if (S.collide && tid == 0) {
+                        for (int u = 0; u < nm; u++)
+                            for (int w = u + 1; w < nm && S.alive[u]; w++) {
+                                if (!S.alive[w] || !bs_can_touch(S.m[u], S.m[w])) continue;
+                                const double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
+                                             dz = S.y[2][w] - S.y[2][u];
+                                if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w])
+                                    bs_merge(S, p, u, w, S.El, S.nmerge);
+                            }
+                    }
+                    __syncthreads();
+                    if (lastq) {
+                        finished = 1;
+                        break;
+                    }
+                    H = Hq;
+                    if (kacc <= 2) H *= 2.0;
+                    else if (kacc >= 6) H *= 0.5;
+                    if (nsub >= cap) failed = 1;
+                    break;
+                }
+                if (nsub >= cap) {   // attempt q rejected
+                    failed = 1;
+                    break;
+                }
+            }
+            if (dec == CA && !failed) H = ldexp(H, -CA);   // every attempt rejected
+            // no block resets its accepted row or overwrites its tableau before
+            // every block has read them
+            cl.sync();
+        }
+        if (failed) {
+            if (tid == 0 && arank == 0) set_status(d.ctl, kEbs, g);
+            return;
+        }
+        if (tid < nm && arank == 0) {
+            double* o = d.bsout + (int64_t)kBsOut * (mb + tid);
+            for (int c = 0; c < 6; c++) o[c] = S.y[c][tid];
+            o[6] = S.m[tid];
+            o[7] = S.R[tid];
+            o[8] = (double)S.alive[tid];
+        }
+        if (tid == 0 && arank == 0) {
+            d.glost[g] = S.El;
+            if (S.nmerge) atomicAdd(&d.ctl->nmerge, S.nmerge);
+            atomicAdd(&d.ctl->nsub, (unsigned long long)nsub);
+        }
+    }
+}
+
 constexpr int kBsLargeThreads = 256;   // groups of up to 32 members: one attempt
 constexpr int kBsLargerThreads = 512;  // groups of up to 64 members: one attempt
 
 cudaError_t bs_setup() {
-    cudaError_t e = cudaFuncSetAttribute(k_bs<32, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(BsSh<32, 1>));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_bs_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_bs_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kPkWarps * sizeof(PkWarp)));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_bs<kBsLargeThreads, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -746,8 +1076,8 @@ cudaError_t bs_setup() {
 // registers one small-group block holds (the kick leaves room for one per SM)
 int bs_block_regs() {
     cudaFuncAttributes a{};
-    if (cudaFuncGetAttributes(&a, k_bs<32, 1, 4>) != cudaSuccess) return 65536;
-    return a.numRegs * 32;
+    if (cudaFuncGetAttributes(&a, k_bs_ws) != cudaSuccess) return 65536;
+    return a.numRegs * kWsThreads;
 }
 
 void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
@@ -768,11 +1098,11 @@ void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent
     launch_bs_huge(d, nsm, s2);
     if (s2 == s) prof_mark("bs: groups of 33-64");
     {
-        // groups of up to 4 members: clusters of four one-warp blocks, one attempt each
+        // groups of up to 4 members: clusters of four two-warp blocks, one attempt each
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(4 * 2 * nsm));
-        cfg.blockDim = dim3(32);
-        cfg.dynamicSmemBytes = sizeof(BsSh<32, 1>);
+        cfg.blockDim = dim3(kWsThreads);
+        cfg.dynamicSmemBytes = 0;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -781,7 +1111,7 @@ void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, k_bs<32, 1, 4>, d, 0);
+        cudaLaunchKernelEx(&cfg, k_bs_ws, d);
     }
     prof_mark("bs: groups <= 4");
     if (s2 != s) {
