@@ -71,16 +71,25 @@ void opal_default_params(opal_params* p);
 /* Create a simulation of one system of n bodies.
  *   m[n] masses (>= 0), x[3n] heliocentric positions (nonzero), v[3n]
  *   heliocentric velocities, radius[n] physical radii (>= 0).
+ * Bodies of zero mass are small bodies (Sec. 2.1: massless particles that
+ * feel the star and the big bodies): they are the source of no force, and
+ * two small bodies never interact (no encounter, no collision); a small body
+ * that touches a big one merges into it.  Every small body must come after
+ * every big body (mass > 0), as in Mercury's separate big and small lists;
+ * the kick and the encounter scan then cost (N_big + N_small) x N_big.
  * Computes the accelerations of the first kick and captures the per-step
  * CUDA graph.  Body i gets id i.  On success *out owns the simulation.
- * Errors: OPAL_EINVAL (bad argument), OPAL_ENOMEM, OPAL_ECUDA. */
+ * Errors: OPAL_EINVAL (bad argument, or a big body after a small one),
+ * OPAL_ENOMEM, OPAL_ECUDA. */
 opal_status opal_create(const opal_params* p, int64_t n, const double* m, const double* x,
                         const double* v, const double* radius, opal_sim** out);
 
 /* Create an ensemble of nsys independent systems sharing the parameters.
  * n_per_sys[nsys] body counts; m, x, v, radius hold the systems one after
  * another (system s starts at body sum_{t<s} n_per_sys[t]).  All systems
- * advance together: one opal_step call steps every system. */
+ * advance together: one opal_step call steps every system.  Within each
+ * system the small bodies (zero mass) follow the big ones, as for
+ * opal_create. */
 opal_status opal_ensemble_create(const opal_params* p, int32_t nsys, const int64_t* n_per_sys,
                                  const double* m, const double* x, const double* v,
                                  const double* radius, opal_sim** out);
