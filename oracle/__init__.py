@@ -42,13 +42,15 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("M0", C.c_double), ("dt", C.c_double),
                 ("rcrit_hill", C.c_double), ("bs_tol", C.c_double),
                 ("changeover", C.c_int32), ("kepler_max_iter", C.c_int32),
-                ("bs_max_substeps", C.c_int32), ("pad", C.c_int32)]
+                ("bs_max_substeps", C.c_int32), ("pad", C.c_int32),
+                ("r_star", C.c_double), ("r_eject", C.c_double), ("eject_every", C.c_int64),
+                ("steps_done", C.c_int64)]
 
 
 class Stats(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_groups", C.c_int64), ("n_mergers", C.c_int64),
                 ("bs_substeps", C.c_int64), ("kepler_iter_max", C.c_int64),
-                ("n_candidates", C.c_int64)]
+                ("n_candidates", C.c_int64), ("n_accreted", C.c_int64), ("n_ejected", C.c_int64)]
 
 
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -71,6 +73,8 @@ def lib():
             L.orc_kepler_drift.argtypes = [C.c_double, C.c_double, _D, _D, C.c_int32,
                                            C.POINTER(C.c_int32)]
             L.orc_kepler_drift.restype = C.c_int32
+            L.orc_drift_min_r.argtypes = [C.c_double, C.c_double, _D, _D, _D, _D]
+            L.orc_drift_min_r.restype = C.c_double
             L.orc_min_sep2.argtypes = [C.c_double, _D, _D, _D, _D]
             L.orc_min_sep2.restype = C.c_double
             L.orc_scan.argtypes = [_i64, C.c_double, _D, _D, _D, _D, _D, _I, C.c_void_p, _i64, _I, _I,
@@ -102,8 +106,9 @@ def _alive(n, alive=None):
 
 
 def make_params(G=1.0, M0=1.0, dt=0.01 * 2 * np.pi, rcrit_hill=3.0, bs_tol=1e-12, changeover=0,
-                kepler_max_iter=0, bs_max_substeps=0) -> Params:
-    return Params(G, M0, dt, rcrit_hill, bs_tol, changeover, kepler_max_iter, bs_max_substeps, 0)
+                kepler_max_iter=0, bs_max_substeps=0, r_star=0.0, r_eject=0.0, eject_every=0) -> Params:
+    return Params(G, M0, dt, rcrit_hill, bs_tol, changeover, kepler_max_iter, bs_max_substeps, 0,
+                  r_star, r_eject, eject_every, 0)
 
 
 # --- function-level views ---------------------------------------------------
@@ -151,6 +156,11 @@ def kepler_drift(mu, dt, x, v, max_iter=0):
     it = C.c_int32(0)
     st = lib().orc_kepler_drift(mu, dt, x, v, max_iter, C.byref(it))
     return st, x, v, it.value
+
+
+def drift_min_r(mu, dt, x0, V0, x1, V1):
+    """Closest approach to the star during a drift from (x0, V0) to (x1, V1)."""
+    return lib().orc_drift_min_r(mu, dt, _d(x0), _d(V0), _d(x1), _d(V1))
 
 
 def min_sep2(dt, d0, u0, d1, u1):
@@ -206,9 +216,10 @@ class Sim:
     """Whole-step oracle state (heliocentric input, DH state inside)."""
 
     def __init__(self, m, x, v_helio, R, G=1.0, M0=1.0, dt=0.01 * 2 * np.pi, rcrit_hill=3.0,
-                 bs_tol=1e-12, changeover=0, kepler_max_iter=0, bs_max_substeps=0):
+                 bs_tol=1e-12, changeover=0, kepler_max_iter=0, bs_max_substeps=0, r_star=0.0,
+                 r_eject=0.0, eject_every=0):
         self.p = make_params(G, M0, dt, rcrit_hill, bs_tol, changeover, kepler_max_iter,
-                             bs_max_substeps)
+                             bs_max_substeps, r_star, r_eject, eject_every)
         self.n = int(np.asarray(m).size)
         self.m = _d(m).copy()
         self.R = _d(R).copy()
@@ -232,9 +243,13 @@ class Sim:
         st = lib().orc_step(C.byref(self.p), self.n, self.m, self.R, self.x, self.V, self.a, self.rc,
                             self.alive, C.byref(self.have_a), C.byref(self.E_lost), int(nsteps),
                             C.byref(self.stats))
-        if st == OK:
-            self.steps_done += int(nsteps)
+        self.steps_done = int(self.p.steps_done)
         return st
+
+    @property
+    def M0(self) -> float:
+        """The star's mass (grows by the mass of every body it accretes)."""
+        return float(self.p.M0)
 
     def energy(self):
         E, L, P = energy(self.p.G, self.p.M0, self.m, self.x, self.V, self.alive)

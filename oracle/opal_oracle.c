@@ -23,6 +23,12 @@
  *     saved start-of-drift state, with collisions: Sec. 2.1.1 footnote 2,
  *     Sec. 3.2 data-management listing, Sec. 2.1.2 (mce_coll);
  *   - energy and momentum: Sec. 2.1.1 item (7);
+ *   - star collisions and ejections (Sec. 2.1.2: mce_cent, and bodies beyond
+ *     400 au removed every 200 yr): a body whose Kepler drift passes within
+ *     the star's radius is accreted at the end of the step (M0 grows by its
+ *     mass, the heliocentric frame moves to the merged star); every
+ *     eject_every steps, bodies beyond r_eject are removed.  The energy each
+ *     removal takes out of the Hamiltonian is added to E_lost;
  *   - small bodies (Sec. 2.1): bodies of zero mass are massless particles
  *     that feel the star and the big bodies (mass > 0) but are the source of
  *     no force; two small bodies never interact, so a pair of them is never
@@ -254,6 +260,48 @@ int32_t orc_kepler_drift(double mu, double dt, double x[3], double v[3], int32_t
         v[k] = vn[k];
     }
     return ORC_OK;
+}
+
+/* Closest approach to the star during a body's drift from (x0, V0) to
+ * (x1, V1) over dt on its Kepler orbit about mu (the star-collision test,
+ * Sec. 2.1.2 mce_cent): the pericentre distance q = p / (1 + e) when the
+ * pericentre is passed within the drift, else the nearer end.  The passage
+ * is read off the mean anomaly, which advances uniformly: on an ellipse
+ * (beta = 2 mu / r - v^2 > 0, a = mu / beta) M = E - e sin E with
+ * e cos E = 1 - r / a and e sin E = x.V / sqrt(mu a), and the pericentre is at
+ * M = 2 pi k; on a hyperbola M = e sinh F - F with e sinh F = x.V / sqrt(-mu a),
+ * and the pericentre is at M = 0.  The swept interval is [M0, M0 + n dt]. */
+double orc_drift_min_r(double mu, double dt, const double x0[3], const double V0[3], const double x1[3],
+                       const double V1[3]) {
+    const double r0 = norm3(x0), r1 = norm3(x1);
+    double rmin = r0 < r1 ? r0 : r1;
+    const double eta0 = dot3(x0, V0);
+    const double beta = 2.0 * mu / r0 - dot3(V0, V0);
+    const double h[3] = {x0[1] * V0[2] - x0[2] * V0[1], x0[2] * V0[0] - x0[0] * V0[2],
+                         x0[0] * V0[1] - x0[1] * V0[0]};
+    const double p = dot3(h, h) / mu;
+    const double e2 = 1.0 - p * beta / mu;
+    const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
+    const double q = p / (1.0 + e);
+    int passed = 0;
+    (void)V1;
+    if (beta > 0.0) {
+        const double a = mu / beta, n = sqrt(mu / (a * a * a));
+        const double ecE = 1.0 - r0 / a, esE = eta0 / sqrt(mu * a);
+        const double M0 = atan2(esE, ecE) - esE, M1 = M0 + n * dt;
+        const double lo = M0 < M1 ? M0 : M1, hi = M0 < M1 ? M1 : M0;
+        passed = 2.0 * M_PI * ceil(lo / (2.0 * M_PI)) <= hi;
+    } else if (beta < 0.0) {
+        const double a = mu / beta, n = sqrt(mu / (-a * a * a));
+        const double esF = eta0 / sqrt(-mu * a);
+        const double F0 = e > 0.0 ? asinh(esF / e) : 0.0;
+        const double M0 = esF - F0, M1 = M0 + n * dt;
+        passed = (M0 <= 0.0 && M1 >= 0.0) || (M0 >= 0.0 && M1 <= 0.0);
+    } else {
+        passed = (dt * eta0 < 0.0) && (dt * dot3(x1, V1) >= 0.0);   /* parabolic: x.V turns outward */
+    }
+    if (passed && q < rmin) rmin = q;
+    return rmin;
 }
 
 /* ---------------------------------------------------------------------- */
@@ -713,22 +761,47 @@ void orc_energy(int64_t n, double G, double M0, const double* m, const double* x
  * The closing a is kept for the next step's opening kick (both are
  * evaluated at the same positions and masses).  On error the state is put
  * back to the start of the failed step and the status is returned. */
-int32_t orc_step(const orc_params* p, int64_t n, double* m, double* R, double* x, double* V, double* a,
+/* Removal of body i at the end of a step: accreted by the star (the merged
+ * star, at the centre of mass of the star and the body, becomes the origin of
+ * the heliocentric frame, so every other position moves by -m_i x_i / M0';
+ * barycentric velocities are unchanged) or ejected.  E_lost gets the
+ * Hamiltonian's drop, from the energy before and after. */
+static void remove_body(orc_params* p, int64_t n, double* m, double* x, double* V, int32_t* alive, int64_t i,
+                        int accrete, double* E_lost) {
+    double Eb, Ea, L[3], P[3];
+    orc_energy(n, p->G, p->M0, m, x, V, alive, &Eb, L, P);
+    if (accrete) {
+        const double M0n = p->M0 + m[i];
+        const double Xc[3] = {m[i] * x[3 * i] / M0n, m[i] * x[3 * i + 1] / M0n, m[i] * x[3 * i + 2] / M0n};
+        for (int64_t j = 0; j < n; j++)
+            if (alive[j] && j != i)
+                for (int k = 0; k < 3; k++) x[3 * j + k] -= Xc[k];
+        p->M0 = M0n;
+    }
+    alive[i] = 0;
+    m[i] = 0.0;
+    orc_energy(n, p->G, p->M0, m, x, V, alive, &Ea, L, P);
+    *E_lost += Eb - Ea;
+}
+
+int32_t orc_step(orc_params* p, int64_t n, double* m, double* R, double* x, double* V, double* a,
                  double* rc, int32_t* alive, int32_t* have_accel, double* E_lost, int64_t nsteps,
                  orc_stats* st) {
-    const double G = p->G, M0 = p->M0, dt = p->dt, half = 0.5 * p->dt;
+    const double G = p->G, dt = p->dt, half = 0.5 * p->dt;
     size_t n3 = sizeof(double) * (size_t)(3 * n + 1), n1 = sizeof(double) * (size_t)(n + 1);
     double *x0 = malloc(n3), *V0 = malloc(n3), *xs = malloc(n3), *Vs = malloc(n3), *as = malloc(n3);
     double *ms = malloc(n1), *Rs = malloc(n1), *rcs = malloc(n1);
     int32_t* als = malloc(sizeof(int32_t) * (size_t)(n + 1));
     int32_t* label = malloc(sizeof(int32_t) * (size_t)(n + 1));
     int32_t* members = malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t* accf = malloc(sizeof(int32_t) * (size_t)(n + 1));
     int64_t cap = 4 * n + 64;
     int32_t* pi = malloc(sizeof(int32_t) * (size_t)cap);
     int32_t* pj = malloc(sizeof(int32_t) * (size_t)cap);
     int32_t status = ORC_OK;
     for (int64_t step = 0; step < nsteps && status == ORC_OK; step++) {
-        orc_stats s = {0, 0, 0, 0, 0, 0};
+        orc_stats s = {0, 0, 0, 0, 0, 0, 0, 0};
+        const double M0 = p->M0;   /* the star's mass this step (accretions change it at the end) */
         if (!*have_accel) {
             orc_hill_rcrit(n, M0, p->rcrit_hill, m, x, alive, rc);
             orc_accel(n, G, p->changeover, m, x, rc, alive, a);
@@ -756,13 +829,16 @@ int32_t orc_step(const orc_params* p, int64_t n, double* m, double* R, double* x
                 for (int k = 0; k < 3; k++) x[3 * i + k] += half * P[k] / M0;
         memcpy(x0, x, n3 - sizeof(double));
         memcpy(V0, V, n3 - sizeof(double));
-        /* drift */
+        /* drift; a drift passing within the star's radius marks the body for accretion */
         for (int64_t i = 0; i < n && status == ORC_OK; i++) {
+            accf[i] = 0;
             if (!alive[i]) continue;
             int32_t it = 0;
             if (orc_kepler_drift(G * M0, dt, x + 3 * i, V + 3 * i, p->kepler_max_iter, &it) != ORC_OK)
                 status = ORC_EKEPLER;
             if (it > s.kepler_iter_max) s.kepler_iter_max = it;
+            if (p->r_star > 0.0 && orc_drift_min_r(G * M0, dt, x0 + 3 * i, V0 + 3 * i, x + 3 * i, V + 3 * i) <= p->r_star)
+                accf[i] = 1;
         }
         if (status == ORC_OK) {
             orc_hill_rcrit(n, M0, p->rcrit_hill, m, x, alive, rc);
@@ -804,6 +880,21 @@ int32_t orc_step(const orc_params* p, int64_t n, double* m, double* R, double* x
             for (int64_t i = 0; i < n; i++)
                 if (alive[i])
                     for (int k = 0; k < 3; k++) V[3 * i + k] += half * a[3 * i + k];
+            /* end of the step: accretions in ascending index (a body merged away
+             * in its encounter is gone already), then ejections when due */
+            for (int64_t i = 0; i < n; i++)
+                if (accf[i] && alive[i]) {
+                    remove_body(p, n, m, x, V, alive, i, 1, E_lost);
+                    s.n_accreted++;
+                }
+            if (p->r_eject > 0.0 && p->eject_every > 0 && (p->steps_done + 1) % p->eject_every == 0)
+                for (int64_t i = 0; i < n; i++)
+                    if (alive[i] && norm3(x + 3 * i) > p->r_eject) {
+                        remove_body(p, n, m, x, V, alive, i, 0, E_lost);
+                        s.n_ejected++;
+                    }
+            if (s.n_accreted + s.n_ejected > 0) *have_accel = 0;   /* the next step evaluates a afresh */
+            p->steps_done++;
         } else {
             memcpy(x, xs, n3 - sizeof(double));
             memcpy(V, Vs, n3 - sizeof(double));
@@ -817,6 +908,6 @@ int32_t orc_step(const orc_params* p, int64_t n, double* m, double* R, double* x
         if (st) *st = s;
     }
     free(x0); free(V0); free(xs); free(Vs); free(as); free(ms); free(Rs); free(rcs);
-    free(als); free(label); free(members); free(pi); free(pj);
+    free(als); free(label); free(members); free(accf); free(pi); free(pj);
     return status;
 }

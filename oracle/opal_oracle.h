@@ -32,6 +32,10 @@ typedef struct {
     int32_t kepler_max_iter;/* cap on universal-variable iterations (0: default 50) */
     int32_t bs_max_substeps;/* cap on BS substeps per group per step (0: default 1<<20) */
     int32_t pad;
+    double r_star;          /* radius of the star: a drift passing within it is accreted (0: off) */
+    double r_eject;         /* ejection distance from the star (0: off) */
+    int64_t eject_every;    /* steps between ejection checks (Sec. 2.1.2: every 200 yr) */
+    int64_t steps_done;     /* state: steps completed (the ejection check counts them) */
 } orc_params;
 
 typedef struct {
@@ -41,6 +45,8 @@ typedef struct {
     int64_t bs_substeps;    /* accepted + rejected BS substeps in the last step */
     int64_t kepler_iter_max;/* largest iteration count of the drift in the last step */
     int64_t n_candidates;   /* pairs that reached the exact minimum-separation test */
+    int64_t n_accreted;     /* bodies accreted by the star in the last step */
+    int64_t n_ejected;      /* bodies ejected at the end of the last step */
 } orc_stats;
 
 /* helio <-> democratic-heliocentric velocities (Sec. 2.1.1, footnote on coordinates) */
@@ -56,6 +62,8 @@ void orc_accel(int64_t n, double G, int32_t form, const double* m, const double*
 void orc_stumpff(double z, double c[4]);
 int32_t orc_kepler_drift(double mu, double dt, double x[3], double v[3], int32_t max_iter,
                          int32_t* iters);
+double orc_drift_min_r(double mu, double dt, const double x0[3], const double V0[3], const double x1[3],
+                       const double V1[3]);
 
 double orc_min_sep2(double dt, const double d0[3], const double u0[3], const double d1[3],
                     const double u1[3]);
@@ -72,7 +80,7 @@ int32_t orc_bs_group(const orc_params* p, int64_t nmem, const int32_t* members, 
 void orc_energy(int64_t n, double G, double M0, const double* m, const double* x,
                 const double* V, const int32_t* alive, double* E, double L[3], double P[3]);
 
-int32_t orc_step(const orc_params* p, int64_t n, double* m, double* R, double* x, double* V,
+int32_t orc_step(orc_params* p, int64_t n, double* m, double* R, double* x, double* V,
                  double* a, double* rc, int32_t* alive, int32_t* have_accel, double* E_lost,
                  int64_t nsteps, orc_stats* st);
 
