@@ -62,10 +62,27 @@ typedef struct {
     int32_t kepler_max_iter;   /* cap on drift iterations; 0 = default (50) */
     int32_t bs_max_substeps;   /* cap on BS substeps per group per step; 0 = default (1<<20) */
     int64_t encounter_capacity;/* max flagged pairs per step; 0 = default (max(4096, 4 n)) */
+    double r_star;       /* the star's radius (>= 0; 0 = off): a body whose Kepler drift passes
+                            within it is accreted at the end of the step (Sec. 2.1.2, mce_cent) */
+    double r_eject;      /* ejection distance (>= 0; 0 = off): bodies farther from the star are
+                            removed at the end of every eject_every-th step (Sec. 2.1.2: 400 au) */
+    int64_t eject_every; /* steps between ejection checks (>= 1 when r_eject > 0; Sec. 2.1.2:
+                            every 200 yr, i.e. 200 yr / dt) */
 } opal_params;
 
 /* Fill *p with the defaults: G = M0 = 1, dt = 0.01 yr (2 pi / 100),
- * rcrit_hill = 3, bs_tol = 1e-12, precision = 1, changeover = 0, caps 0. */
+ * rcrit_hill = 3, bs_tol = 1e-12, precision = 1, changeover = 0, caps 0,
+ * no star collisions and no ejections (r_star = r_eject = eject_every = 0).
+ *
+ * Removals (r_star or r_eject > 0).  At the end of a step, in ascending id
+ * order, every live body whose drift passed within r_star of the star (its
+ * Kepler orbit's pericentre inside the drift, or an end nearer) is accreted:
+ * the star's mass grows by the body's, and the heliocentric frame moves to
+ * the merged star (every other position shifts by -m x / M0'; barycentric
+ * velocities are unchanged).  Then, on every eject_every-th step, every live
+ * body farther than r_eject is removed.  The energy each removal takes from
+ * the Hamiltonian is added to E_merged_lost, and the next step evaluates the
+ * accelerations afresh. */
 void opal_default_params(opal_params* p);
 
 /* Create a simulation of one system of n bodies.
@@ -104,6 +121,9 @@ opal_status opal_step(opal_sim* sim, int64_t nsteps);
  * would have (a failed step stops the rest and is undone, as there). */
 opal_status opal_step_async(opal_sim* sim, int64_t nsteps);
 opal_status opal_wait(opal_sim* sim);
+
+/* The star's mass of system sys (M0 at create, plus what it has accreted). */
+opal_status opal_central_mass(const opal_sim* sim, int32_t sys, double* M0);
 
 /* Number of systems and total body capacity (sum of the n given at create). */
 int32_t opal_num_systems(const opal_sim* sim);
@@ -161,8 +181,9 @@ opal_status opal_energy_momentum_noalloc(int64_t n, double G, double M0, const d
 /* Counters of the last completed step, summed over systems:
  * out[0] flagged pairs, out[1] groups, out[2] mergers, out[3] BS substeps,
  * out[4] pairs that reached the exact minimum-separation test,
- * out[5] largest drift iteration count. */
-opal_status opal_last_step_stats(const opal_sim* sim, int64_t out[6]);
+ * out[5] largest drift iteration count, out[6] bodies accreted by the star,
+ * out[7] bodies ejected. */
+opal_status opal_last_step_stats(const opal_sim* sim, int64_t out[8]);
 
 /* The CUDA stream every kernel of this simulation runs on (a cudaStream_t). */
 void* opal_stream(const opal_sim* sim);

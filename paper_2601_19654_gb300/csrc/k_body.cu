@@ -103,7 +103,7 @@ __global__ void k_to_dh(Dev d) {
             for (int c = 0; c < 4; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
         __syncthreads();
     }
-    double Mt = d.p.M0 + red[3][0];
+    double Mt = d.M0s[blockIdx.x] + red[3][0];
     double cx = red[0][0] / Mt, cy = red[1][0] / Mt, cz = red[2][0] / Mt;
     for (int64_t k = threadIdx.x; k < si.cap; k += blockDim.x) {
         int64_t b = si.off + k;
@@ -116,10 +116,11 @@ __global__ void k_to_dh(Dev d) {
 
 // create time: critical radii and float copies at the initial positions
 __global__ void k_prime(Dev d) {
+    if (d.gated && (d.ctl->status || !d.ctl->reprime)) return;
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= d.ntot) return;
     int s = d.body_sys[b];
-    d.hcb[b] = cbrt(d.m[b] / (3.0 * d.p.M0));
+    d.hcb[b] = cbrt(d.m[b] / (3.0 * d.M0s[s]));
     if (!d.alive[b]) {
         d.rc[b] = 0.0;
         park_floats(d, b);
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
     const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
     const SysInfo si = d.sys[s];
     const double* P = d.Ptot + 3 * s;   // momentum for the opening jump (summed by the last close)
-    const double half = 0.5 * d.p.dt, M0 = d.p.M0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.ctl->reprime = 0;   // any re-evaluation has run
+    const double half = 0.5 * d.p.dt, M0 = d.M0s[s];
     // undo copy of the start of the step
     double x = d.x[b], y = d.y[b], z = d.z[b], vx = d.vx[b], vy = d.vy[b], vz = d.vz[b];
     d.xs[b] = x; d.ys[b] = y; d.zs[b] = z;
@@ -162,6 +164,12 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
         if (iters < 0) {
             set_status(d.ctl, kEkepler, (int)b);
             iters = d.p.kepler_max_iter;
+        }
+        // a drift passing within the star's radius: accreted at the end of the step
+        if (d.p.r_star > 0.0 && drift_min_r(d.p.G * M0, d.p.dt, ox, oy, oz, ovx, ovy, ovz, x, y, z, vx, vy, vz) <=
+                                    d.p.r_star) {
+            d.accf[b] = 1;
+            atomicAdd(&d.ctl->naccf, 1);
         }
         d.x[b] = x; d.y[b] = y; d.z[b] = z;
         d.vx[b] = vx; d.vy[b] = vy; d.vz[b] = vz;
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
 // step's jump needs (of V + dt/2 a, the velocities after its opening kick).
 // first != 0 (create time): only a and the partials, no jump or kick.
 __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
-    if (d.ctl->status) return;
+    if (d.ctl->status || (d.gated && !d.ctl->reprime)) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
     const SysInfo si = d.sys[s];
@@ -255,9 +263,9 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     if (d.alive[b]) {
         double x = d.x[b], y = d.y[b], z = d.z[b], vx = d.vx[b], vy = d.vy[b], vz = d.vz[b];
         if (!first) {
-            x += half * P[0] / d.p.M0;
-            y += half * P[1] / d.p.M0;
-            z += half * P[2] / d.p.M0;
+            x += half * P[0] / d.M0s[s];
+            y += half * P[1] / d.M0s[s];
+            z += half * P[2] / d.M0s[s];
             vx += half * ax;
             vy += half * ay;
             vz += half * az;
@@ -329,7 +337,7 @@ __global__ void k_finish(Dev d) {
         int b = d.members[k];
         if (d.undo[3 * k + 2] >= 0.0) {   // slot written when the BS results were applied
             d.m[b] = d.undo[3 * k];
-            d.hcb[b] = cbrt(d.m[b] / (3.0 * d.p.M0));
+            d.hcb[b] = cbrt(d.m[b] / (3.0 * d.M0s[d.body_sys[b]]));
             d.R[b] = d.undo[3 * k + 1];
             d.alive[b] = (int)d.undo[3 * k + 2];
         }
@@ -357,7 +365,8 @@ __global__ void k_export(Dev d, double* vh) {
             for (int c = 0; c < 3; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
         __syncthreads();
     }
-    double cx = red[0][0] / d.p.M0, cy = red[1][0] / d.p.M0, cz = red[2][0] / d.p.M0;
+    const double M0 = d.M0s[blockIdx.x];
+    double cx = red[0][0] / M0, cy = red[1][0] / M0, cz = red[2][0] / M0;
     for (int64_t k = threadIdx.x; k < si.cap; k += blockDim.x) {
         int64_t b = si.off + k;
         vh[3 * b] = d.vx[b] + cx;
@@ -401,7 +410,121 @@ __global__ void __launch_bounds__(kBodyThreads) k_order_prep(Dev d) {
     note_box(d, s, b);   // every thread of the block, from this one call site
 }
 
-// Start of a step: the counters, bounds and scratch the step's kernels
+// ---------------------------------------------------------------------------
+// End of a step with star collisions or ejections on (Sec. 2.1.2): one block
+// per system removes, in ascending index, every live body whose drift passed
+// within the star's radius (accreted: the star's mass grows by the body's and
+// the heliocentric frame moves to the merged star, every other position by
+// -m_i x_i / M0'; barycentric velocities stay), then, on every eject_every-th
+// step, every live body beyond r_eject.  Each removal adds the drop of the
+// Hamiltonian (kinetic, stellar, mutual and |P|^2 / 2 M0 terms: O(N) sums) to
+// the system's E_lost, and any removal makes the next step evaluate the
+// accelerations afresh.
+constexpr int kRemThreads = 256;
+
+__device__ void remove_body(const Dev& d, const SysInfo& si, int s, int64_t i, bool accrete,
+                            double (*red)[kRemThreads]) {
+    const double G = d.p.G, M0 = d.M0s[s];
+    const double mi = d.m[i], xi = d.x[i], yi = d.y[i], zi = d.z[i];
+    const double vxi = d.vx[i], vyi = d.vy[i], vzi = d.vz[i];
+    const double M0n = accrete ? M0 + mi : M0;
+    const double cx = accrete ? mi * xi / M0n : 0.0, cy = accrete ? mi * yi / M0n : 0.0,
+                 cz = accrete ? mi * zi / M0n : 0.0;
+    // s1 = sum m/|x|, s2 = the same after (i gone, frame moved), s3 = sum m/|x - x_i|, P
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t k = threadIdx.x; k < si.n; k += kRemThreads) {
+        const int64_t j = si.off + k;
+        if (!d.alive[j] || d.m[j] == 0.0) continue;   // (a small body adds no such term)
+        const double mj = d.m[j], xj = d.x[j], yj = d.y[j], zj = d.z[j];
+        v[0] += mj / sqrt(xj * xj + yj * yj + zj * zj);
+        v[3] += mj * d.vx[j];
+        v[4] += mj * d.vy[j];
+        v[5] += mj * d.vz[j];
+        if (j != i) {
+            const double ax = xj - cx, ay = yj - cy, az = zj - cz;
+            const double bx = xj - xi, by = yj - yi, bz = zj - zi;
+            v[1] += mj / sqrt(ax * ax + ay * ay + az * az);
+            v[2] += mj / sqrt(bx * bx + by * by + bz * bz);
+        }
+    }
+    __syncthreads();
+    for (int c = 0; c < 6; c++) red[c][threadIdx.x] = v[c];
+    __syncthreads();
+    for (int w = kRemThreads / 2; w >= 1; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int c = 0; c < 6; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double px = red[3][0], py = red[4][0], pz = red[5][0];
+        const double qx = px - mi * vxi, qy = py - mi * vyi, qz = pz - mi * vzi;
+        const double dE = 0.5 * mi * (vxi * vxi + vyi * vyi + vzi * vzi) - G * M0 * red[0][0] +
+                          G * M0n * red[1][0] + (px * px + py * py + pz * pz) / (2.0 * M0) -
+                          (qx * qx + qy * qy + qz * qz) / (2.0 * M0n) - G * mi * red[2][0];
+        d.E_lost[s] += dE;
+    }
+    if (accrete)
+        for (int64_t k = threadIdx.x; k < si.n; k += kRemThreads) {
+            const int64_t j = si.off + k;
+            if (!d.alive[j] || j == i) continue;
+            d.x[j] -= cx;
+            d.y[j] -= cy;
+            d.z[j] -= cz;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d.alive[i] = 0;
+        d.m[i] = 0.0;
+        park_floats(d, i);
+        if (accrete) d.M0s[s] = M0n;
+        atomicAdd(accrete ? &d.ctl->nacc : &d.ctl->nej, 1);
+        d.ctl->reprime = 1;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kRemThreads) k_remove(Dev d) {
+    __shared__ double red[6][kRemThreads];
+    __shared__ int lst[kRemThreads];
+    __shared__ int wsum[kRemThreads / 32];
+    if (d.ctl->status) return;
+    const int s = blockIdx.x;
+    const SysInfo si = d.sys[s];
+    const bool eject = d.p.r_eject > 0.0 && d.p.eject_every > 0 && d.ctl->steps_done % d.p.eject_every == 0;
+    const bool accrete_any = d.ctl->naccf > 0;
+    if (!accrete_any && !eject) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int pass = 0; pass < 2; pass++) {
+        if ((pass == 0 && !accrete_any) || (pass == 1 && !eject)) continue;
+        for (int64_t c0 = 0; c0 < si.n; c0 += kRemThreads) {
+            const int64_t b = si.off + c0 + threadIdx.x;
+            bool want = false;
+            if (c0 + (int64_t)threadIdx.x < si.n && d.alive[b]) {
+                if (pass == 0) {
+                    want = d.accf[b] != 0;
+                } else {
+                    const double x = d.x[b], y = d.y[b], z = d.z[b];
+                    want = sqrt(x * x + y * y + z * z) > d.p.r_eject;
+                }
+            }
+            // this chunk's bodies to remove, in ascending index
+            const unsigned bm = __ballot_sync(0xffffffffu, want);
+            if (lane == 0) wsum[warp] = __popc(bm);
+            __syncthreads();
+            int off = __popc(bm & ((1u << lane) - 1u)), total = 0;
+            for (int w = 0; w < kRemThreads / 32; w++) {
+                if (w < warp) off += wsum[w];
+                total += wsum[w];
+            }
+            if (want) lst[off] = (int)b;
+            __syncthreads();
+            for (int q = 0; q < total; q++) remove_body(d, si, s, lst[q], pass == 0, red);
+            __syncthreads();
+        }
+    }
+}
+
+// Start of a step: the counters, bounds and scratch the step's kernels// Start of a step: the counters, bounds and scratch the step's kernels
 // accumulate into, zeroed or preset in one launch (rather than ten memsets).
 __global__ void __launch_bounds__(256) k_step_reset(Dev d) {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
@@ -409,7 +532,10 @@ __global__ void __launch_bounds__(256) k_step_reset(Dev d) {
     constexpr int nc = (int)((offsetof(Ctl, steps_done) - offsetof(Ctl, ncand)) / sizeof(int));
     int* h = reinterpret_cast<int*>(d.hctl);
     constexpr int nh = (int)(sizeof(HugeCtl) / sizeof(int));
-    for (int64_t i = i0; i < d.ntot; i += st) d.gcount[i] = 0;
+    for (int64_t i = i0; i < d.ntot; i += st) {
+        d.gcount[i] = 0;
+        d.accf[i] = 0;
+    }
     for (int64_t i = i0; i < d.ncell; i += st) d.cstart[i] = 0;
     for (int64_t i = i0; i < nc; i += st) c[i] = 0;
     for (int64_t i = i0; i < nh; i += st) h[i] = 0;
@@ -430,6 +556,10 @@ __global__ void __launch_bounds__(256) k_step_reset(Dev d) {
 void launch_step_reset(const Dev& d, int nsm, cudaStream_t s) {
     k_step_reset<<<2 * nsm, 256, 0, s>>>(d);
     prof_mark("memsets");
+}
+void launch_remove(const Dev& d, cudaStream_t s) {
+    k_remove<<<d.nsys, kRemThreads, 0, s>>>(d);
+    prof_mark("removals: star collisions and ejections");
 }
 void launch_order_prep(const Dev& d, cudaStream_t s) {
     k_order_prep<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d);

@@ -64,11 +64,11 @@ struct BsSh {
 };
 
 // Perfect merger of members b and q of a group held in S (y[6][.], m, R, gid,
-// alive): mass, momentum and centre of mass kept, R = cbrt(R_b^3 + R_q^3),
+// alive), M0 the star's mass: mass, momentum and centre of mass kept, R = cbrt(R_b^3 + R_q^3),
 // the heavier body (lower id on a tie) survives; El gets the energy removed.
 template <class SH>
-__device__ void bs_merge(SH& S, const Params& p, int b, int q, double& El, int& nmerge) {
-    const double G = p.G, M0 = p.M0;
+__device__ void bs_merge(SH& S, const Params& p, double M0, int b, int q, double& El, int& nmerge) {
+    const double G = p.G;
     double mb = S.m[b], mq = S.m[q], M = mb + mq;
     double d[3] = {S.y[0][q] - S.y[0][b], S.y[1][q] - S.y[1][b], S.y[2][q] - S.y[2][b]};
     double xn[3], vn[3];
@@ -133,11 +133,10 @@ __device__ __forceinline__ void bs_pair(const Params& p, double xb, double yb, d
 
 // acceleration of member b of sequence k at its position (x, y, z)
 template <int NT, int A>
-__device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, int nm, int a, int k, int b,
-                                         double xb, double yb, double zb, double& ax, double& ay, double& az) {
-    const double G = p.G, M0 = p.M0;
+__device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, double GM0, int nm, int a, int k,
+                                         int b, double xb, double yb, double zb, double& ax, double& ay, double& az) {
     double r2 = xb * xb + yb * yb + zb * zb, ri = rsqrt(r2);
-    double s = -G * M0 * (ri * ri * ri);
+    double s = -GM0 * (ri * ri * ri);
     ax = s * xb;
     ay = s * yb;
     az = s * zb;
@@ -214,6 +213,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
         }
         const int k = lt / nm, b = lt % nm;       // sequence and member of this thread
         const bool act = k < kBsRows;
+        const double M0g = d.M0s[d.body_sys[d.members[mb]]];   // the star of the group's system
         if (tid < nm) {
             int gb = d.members[mb + tid];
             S.gid[tid] = gb;
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                         f[0] = zp[3];
                         f[1] = zp[4];
                         f[2] = zp[5];
-                        bs_accel<NT, A>(S, p, nm, a, k, b, zp[0], zp[1], zp[2], f[3], f[4], f[5]);
+                        bs_accel<NT, A>(S, p, p.G * M0g, nm, a, k, b, zp[0], zp[1], zp[2], f[3], f[4], f[5]);
                     } else {
                         for (int c = 0; c < 6; c++) f[c] = 0.0;
                     }
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                                 double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
                                        dz = S.y[2][w] - S.y[2][u];
                                 if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w])
-                                    bs_merge(S, p, u, w, S.El, S.nmerge);
+                                    bs_merge(S, p, M0g, u, w, S.El, S.nmerge);
                             }
                     }
                     __syncthreads();
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
     if (d.ctl->status) return;
     if (d.ctl->ngroups <= kBsManyGroups) return;   // few groups: the lockstep kernels take them
     const Params p = d.p;
-    const double tol2 = p.bs_tol * p.bs_tol, dt = p.dt, GM0 = p.G * p.M0;
+    const double tol2 = p.bs_tol * p.bs_tol, dt = p.dt;
     const int cap = p.bs_max_substeps;
     for (int c = 3; c >= 0; c--) {
         const int Wc = 2 << c;                      // 16, 8, 4, 2 lanes a segment
@@ -514,6 +514,7 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
         const int seg = lane / Wc, sl = lane % Wc, base = seg * Wc;
         const unsigned segmask = (Wc == 32 ? 0xffffffffu : ((1u << Wc) - 1u)) << base;
         int g = -1, sz = 0, mslot = 0;
+        double M0g = p.M0, GM0 = p.G * p.M0;   // the star of the segment's group
         double yv[6] = {0, 0, 0, 0, 0, 0}, z0[6] = {0, 0, 0, 0, 0, 0}, z1[6] = {0, 0, 0, 0, 0, 0};
         double t = 0.0, H = 0.0, El = 0.0;
         int k = 0, ms = 0, nsub = 0, last = 0, nmerge = 0;
@@ -529,6 +530,10 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
                 need = false;
                 g = W.seg_g[seg];
                 sz = g >= 0 ? d.goff[g + 1] - d.goff[g] : 0;
+                if (g >= 0) {
+                    M0g = d.M0s[d.body_sys[d.members[d.goff[g]]]];
+                    GM0 = p.G * M0g;
+                }
                 W.alive[lane] = 0;
                 W.big[lane] = 0;
                 if (sl < sz) {
@@ -662,7 +667,7 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
                         const double ddx = W.y[0][w] - W.y[0][u], ddy = W.y[1][w] - W.y[1][u],
                                      ddz = W.y[2][w] - W.y[2][u];
                         if (sqrt(ddx * ddx + ddy * ddy + ddz * ddz) <= W.R[u] + W.R[w])
-                            bs_merge(W, p, u, w, El, nmerge);
+                            bs_merge(W, p, M0g, u, w, El, nmerge);
                     }
             }
             __syncwarp();
@@ -789,7 +794,7 @@ __global__ void __launch_bounds__(kWsThreads) k_bs_ws(Dev d) {
     const int tid = threadIdx.x, lane = tid & 31;
     const bool w0 = tid < 32;
     const int cap = p.bs_max_substeps;
-    const double tol2 = p.bs_tol * p.bs_tol, GM0 = p.G * p.M0;
+    const double tol2 = p.bs_tol * p.bs_tol;
     int epoch = 0;
     if (tid == 0) S.decision = -1;
     for (;;) {
@@ -803,6 +808,7 @@ __global__ void __launch_bounds__(kWsThreads) k_bs_ws(Dev d) {
         const int g = list ? list[gi] : gi;
         const int mb = d.goff[g], nm = d.goff[g + 1] - mb;
         if (nm > M) continue;                // a larger group: the other lockstep kernels'
+        const double M0g = d.M0s[d.body_sys[d.members[mb]]], GM0 = p.G * M0g;   // the group's star
         const int k = lane / nm, b = lane % nm;
         const bool act = k < kBsRows;
         if (tid < nm) {
@@ -1016,7 +1022,7 @@ __global__ void __launch_bounds__(kWsThreads) k_bs_ws(Dev d) {
                                 const double dx = S.y[0][w] - S.y[0][u], dy = S.y[1][w] - S.y[1][u],
                                              dz = S.y[2][w] - S.y[2][u];
                                 if (sqrt(dx * dx + dy * dy + dz * dz) <= S.R[u] + S.R[w])
-                                    bs_merge(S, p, u, w, S.El, S.nmerge);
+                                    bs_merge(S, p, M0g, u, w, S.El, S.nmerge);
                             }
                     }
                     __syncthreads();

@@ -144,10 +144,10 @@ __device__ __forceinline__ bool huge_touch(const HugeBuf& H, int u, int w) {
 }
 
 // perfect merger of members u and w (as the small-group kernels merge)
-__device__ void huge_merge(const Dev& d, const Params& p, int b, int q, double& El, int& survivor) {
+__device__ void huge_merge(const Dev& d, const Params& p, double M0, int b, int q, double& El, int& survivor) {
     const HugeBuf& H = d.hb;
     const int64_t c = H.cap;
-    const double G = p.G, M0 = p.M0;
+    const double G = p.G;
     const double mb = H.m[b], mq = H.m[q], M = mb + mq;
     double X[2][6];
     for (int k = 0; k < 6; k++) {
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
     const Params p = d.p;
     const HugeBuf& H = d.hb;
     const int64_t c = H.cap;
-    const double dt = p.dt, tol2 = p.bs_tol * p.bs_tol, GM0 = p.G * p.M0;
+    const double dt = p.dt, tol2 = p.bs_tol * p.bs_tol;
     const int cap = p.bs_max_substeps;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
         const int g = d.ghuge[hi];
         const int m0 = d.goff[g], M = d.goff[g + 1] - m0;
         const int nch = (M + kHugeChunk - 1) / kHugeChunk;
+        const double M0g = d.M0s[d.body_sys[d.members[m0]]], GM0 = p.G * M0g;   // the group's star
         for (int64_t b = gt; b < M; b += nt) {
             const int gb = d.members[m0 + b];
             H.gid[b] = gb;
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
                         if (!H.alive[pr.x] || !H.alive[pr.y] || !huge_touch(H, pr.x, pr.y)) continue;
                         double El = hc->El;
                         int sv = -1;
-                        huge_merge(d, p, pr.x, pr.y, El, sv);
+                        huge_merge(d, p, M0g, pr.x, pr.y, El, sv);
                         hc->El = El;
                         hc->nmerge++;
                         for (int x = 0; x < M; x++) {

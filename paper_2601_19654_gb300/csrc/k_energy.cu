@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kEnThreads) k_energy_body(Dev d, double* body_
     double v[7] = {0, 0, 0, 0, 0, 0, 0};
     if (d.alive[b]) {
         double m = d.m[b], x = d.x[b], y = d.y[b], z = d.z[b], vx = d.vx[b], vy = d.vy[b], vz = d.vz[b];
-        v[0] = 0.5 * m * (vx * vx + vy * vy + vz * vz) - d.p.G * d.p.M0 * m / sqrt(x * x + y * y + z * z);
+        v[0] = 0.5 * m * (vx * vx + vy * vy + vz * vz) - d.p.G * d.M0s[d.body_sys[b]] * m / sqrt(x * x + y * y + z * z);
         v[1] = m * vx;
         v[2] = m * vy;
         v[3] = m * vz;
@@ -93,7 +93,7 @@ __global__ void k_energy_final(Dev d, const double* body_part, const double* pai
     }
     if (threadIdx.x == 0) {
         double Px = red[1][0], Py = red[2][0], Pz = red[3][0];
-        double E = red[0][0] + (Px * Px + Py * Py + Pz * Pz) / (2.0 * d.p.M0) + red[7][0];
+        double E = red[0][0] + (Px * Px + Py * Py + Pz * Pz) / (2.0 * d.M0s[s]) + red[7][0];
         double* o = out + 8 * s;
         o[0] = E;
         o[1] = red[4][0]; o[2] = red[5][0]; o[3] = red[6][0];

@@ -157,6 +157,7 @@ __device__ __forceinline__ void box_add(const float4& p, bool& have, float (&bl)
 // path and the tile runs without the per-pair test.
 template <int T, int NI, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_kick_mixed(Dev d, const KickItem* __restrict__ items, int64_t nitems) {
+    if (d.gated && !d.ctl->reprime) return;   // the re-evaluation after a removal, with none
     constexpr int JPT = kJTile / T;   // j records each thread stages
     __shared__ float4 sj[kJTile];
     __shared__ int sid[kJTile];
@@ -313,6 +314,7 @@ __global__ void __launch_bounds__(T, MINB) k_kick_mixed(Dev d, const KickItem* _
 
 template <int T>
 __global__ void __launch_bounds__(T) k_kick_fp64(Dev d, const KickItem* __restrict__ items, int64_t nitems) {
+    if (d.gated && !d.ctl->reprime) return;   // the re-evaluation after a removal, with none
     __shared__ D4 sj[kJTile];
     __shared__ int s_item;
     if (d.ctl->status) return;
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(256) k_kick_apply(Dev d) {
         d.x[g] = o[0]; d.y[g] = o[1]; d.z[g] = o[2];
         d.vx[g] = o[3]; d.vy[g] = o[4]; d.vz[g] = o[5];
         d.m[g] = o[6];
-        d.hcb[g] = cbrt(o[6] / (3.0 * d.p.M0));
+        d.hcb[g] = cbrt(o[6] / (3.0 * d.M0s[s]));
         d.R[g] = o[7];
         const int al = (int)o[8];
         d.alive[g] = al;

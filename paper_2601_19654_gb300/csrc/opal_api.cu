@@ -206,6 +206,11 @@ opal_status validate(const opal_params* p, char* err) {
         return set_err(err, "rcrit_hill must be finite and >= 0"), OPAL_EINVAL;
     if (!(std::isfinite(p->bs_tol) && p->bs_tol > 0)) return set_err(err, "bs_tol must be > 0"), OPAL_EINVAL;
     if (p->precision != 0 && p->precision != 1) return set_err(err, "precision must be 0 or 1"), OPAL_EINVAL;
+    if (!(std::isfinite(p->r_star) && p->r_star >= 0)) return set_err(err, "r_star must be finite and >= 0"), OPAL_EINVAL;
+    if (!(std::isfinite(p->r_eject) && p->r_eject >= 0))
+        return set_err(err, "r_eject must be finite and >= 0"), OPAL_EINVAL;
+    if (p->eject_every < 0 || (p->r_eject > 0 && p->eject_every < 1))
+        return set_err(err, "eject_every must be >= 1 when r_eject > 0"), OPAL_EINVAL;
     if (p->changeover != 0 && p->changeover != 1) return set_err(err, "changeover must be 0 or 1"), OPAL_EINVAL;
     if (p->kepler_max_iter < 0 || p->bs_max_substeps < 0 || p->encounter_capacity < 0)
         return set_err(err, "caps must be >= 0"), OPAL_EINVAL;
@@ -283,6 +288,9 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     P.kepler_max_iter = p->kepler_max_iter > 0 ? p->kepler_max_iter : 50;
     P.bs_max_substeps = p->bs_max_substeps > 0 ? p->bs_max_substeps : (1 << 20);
     P.encounter_capacity = p->encounter_capacity > 0 ? p->encounter_capacity : std::max<int64_t>(4096, 4 * ntot);
+    P.r_star = p->r_star;
+    P.r_eject = p->r_eject;
+    P.eject_every = p->eject_every;
 
     // layout
     int64_t off = 0, in0 = 0;
@@ -411,6 +419,14 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.cfy, kFixParts * N));
     TRYF(dalloc(s, &d.cfz, kFixParts * N));
     TRYF(dalloc(s, &d.E_lost, nsys));
+    TRYF(dalloc(s, &d.M0s, nsys));
+    {
+        std::vector<double> m0(nsys, p->M0);
+        CKF(cudaMemcpyAsync(d.M0s, m0.data(), nsys * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        CKF(cudaStreamSynchronize(s->stream));
+    }
+    TRYF(dalloc(s, &d.accf, N));
+    CKF(cudaMemsetAsync(d.accf, 0, N * sizeof(int), s->stream));
     TRYF(dalloc(s, &d.ctl, 1));
     TRYF(dalloc(s, &d.sys, nsys));
     size_t max_items = 0;
@@ -547,8 +563,10 @@ void reset_scan_order(opal_sim* s) {
 
 // the kernels of one step; names for profiling
 const char* kKernelNames[] = {"counters", "open(kick+jump+drift)", "scan", "confirm", "group", "bs", "kick",
-                              "apply bs", "kick fix", "close(jump+kick)", "finish"};
-constexpr int kNumKernels = 11;
+                              "apply bs", "kick fix", "close(jump+kick)", "finish", "accelerations afresh",
+                              "removals"};
+constexpr int kNumKernels = 13;
+constexpr int kStageReprime = 11, kStageRemove = 12;
 constexpr int kStageBs = 5, kStageKick = 6, kStageApply = 7;
 
 // stage k of a step on stream st
@@ -571,6 +589,18 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
         case 8: launch_kick_fix(d, s->nsm, st); break;
         case 9: launch_close(d, st); break;
         case 10: launch_finish(d, st); break;
+        case kStageReprime: {
+            // after a removal: critical radii, kick and accelerations at the current
+            // positions (each kernel returns at once when nothing was removed)
+            Dev g = d;
+            g.gated = 1;
+            launch_prime(g, st);
+            launch_kick(g, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
+            launch_first_accel_finish(g, st);
+            prof_mark("accelerations afresh after a removal");
+            break;
+        }
+        case kStageRemove: launch_remove(d, st); break;
     }
 }
 void launch_stage(opal_sim* s, int k) { launch_stage(s, k, s->stream); }
@@ -579,12 +609,20 @@ void launch_stage(opal_sim* s, int k) { launch_stage(s, k, s->stream); }
 // after the drift and the fix puts the members right afterwards.  In order:
 // the BS results are applied first and the kick sees them (the fix only sums
 // the momentum), which is cheaper when many bodies are in encounters.
+// With star collisions or ejections on, the step ends with the removals and
+// starts with the accelerations afresh (both return at once when idle).
 int stage_order(const opal_sim* s, int* out) {
     static const int ov[] = {0, 1, 2, 3, 4, kStageBs, kStageKick, kStageApply, 8, 9, 10};
     static const int sq[] = {0, 1, 2, 3, 4, kStageBs, kStageApply, kStageKick, 8, 9, 10};
     const int* o = s->d.overlap ? ov : sq;
-    for (int k = 0; k < kNumKernels; k++) out[k] = o[k];
-    return kNumKernels;
+    const bool removals = s->d.p.r_star > 0 || s->d.p.r_eject > 0;
+    int n = 0;
+    for (int k = 0; k < 11; k++) {
+        out[n++] = o[k];
+        if (removals && o[k] == 0) out[n++] = kStageReprime;
+    }
+    if (removals) out[n++] = kStageRemove;
+    return n;
 }
 
 opal_status capture_graph(opal_sim* s) {
@@ -627,9 +665,6 @@ opal_status capture_graph(opal_sim* s) {
     return OPAL_OK;
 }
 
-// Overlap pays while the fix (about three member-sized kicks) stays small
-// against the kick it hides: choose by the share of bodies in encounters in
-// the last step, with some hysteresis.
 // Overlap (kick beside the encounter integrator, then patched) or in order.
 // The patch costs about 2 x bodies x big members involved pair terms against
 // the kick's bodies x big bodies, so the share that decides is that of the
@@ -773,7 +808,7 @@ opal_status opal_energy_momentum(const opal_sim* cs, int32_t sys, double* E, dou
     return OPAL_OK;
 }
 
-opal_status opal_last_step_stats(const opal_sim* cs, int64_t out[6]) {
+opal_status opal_last_step_stats(const opal_sim* cs, int64_t out[8]) {
     opal_sim* s = const_cast<opal_sim*>(cs);
     if (!s || !out) return set_err(g_err, "NULL argument"), OPAL_EINVAL;
     Ctl c{};
@@ -785,6 +820,17 @@ opal_status opal_last_step_stats(const opal_sim* cs, int64_t out[6]) {
     out[3] = (int64_t)c.nsub;
     out[4] = c.ncand;
     out[5] = c.kepler_max;
+    out[6] = c.nacc;
+    out[7] = c.nej;
+    return OPAL_OK;
+}
+
+opal_status opal_central_mass(const opal_sim* cs, int32_t sys, double* M0) {
+    opal_sim* s = const_cast<opal_sim*>(cs);
+    if (!s || !M0) return set_err(g_err, "NULL argument"), OPAL_EINVAL;
+    if (sys < 0 || sys >= s->d.nsys) return set_err(s->err, "no system %d", sys), OPAL_EINVAL;
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(M0, s->d.M0s + sys, sizeof(double), cudaMemcpyDeviceToHost));
     return OPAL_OK;
 }
 

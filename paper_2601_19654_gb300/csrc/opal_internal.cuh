@@ -47,6 +47,8 @@ struct Ctl {
     int ngroups;         // encounter groups (this step)
     int ninvolved;       // bodies in groups (this step)
     int ninv_big;        // of them big bodies, the sources of force (this step)
+    int naccf;           // bodies whose drift passed within the star's radius (this step)
+    int nacc, nej;       // bodies accreted and ejected at the end of the step (this step)
     int nmerge;          // mergers (this step)
     int kepler_max;      // largest drift iteration count (this step)
     int nlarge;          // groups too large for one warp (this step)
@@ -58,7 +60,7 @@ struct Ctl {
     unsigned long long nsub;  // BS substeps (this step)
     long long steps_done;
     int cand_overflow;   // candidates lost to a full candidate list (forces a status)
-    int pad;
+    int reprime;         // a removal happened: the next step evaluates the accelerations afresh
     // work queue of the kick: next item, blocks done; the last block out puts
     // both back to zero, so every launch starts from an empty queue
     int kick_next;
@@ -134,6 +136,9 @@ struct Params {
     double G, M0, dt, rcrit_hill, bs_tol;
     int precision, changeover, kepler_max_iter, bs_max_substeps;
     int64_t encounter_capacity;
+    double r_star;       // star's radius: a drift passing within it is accreted (0: off)
+    double r_eject;      // ejection distance (0: off)
+    int64_t eject_every; // steps between ejection checks
 };
 
 // All device pointers of one simulation (passed by value to kernels).
@@ -141,7 +146,10 @@ struct Dev {
     int64_t ntot;
     int nsys;
     int overlap;       // 1: the kick runs beside the BS and is fixed afterwards; 0: after it
+    int gated;         // the launch belongs to the re-evaluation after a removal: run only if one happened
     Params p;
+    double* M0s;       // [nsys] the star's mass of each system (it grows by what it accretes)
+    int* accf;         // [ntot] the body's drift passed within the star's radius this step
     SysInfo* sys;
     int32_t* body_sys;
     // FP64 state
@@ -419,6 +427,45 @@ __device__ __forceinline__ int kepler_drift(double mu, double dt, int max_iter, 
     return it;
 }
 
+// Closest approach to the star during a drift from (x0, v0) to (x1, v1) over
+// dt on the Kepler orbit about mu (the star-collision test, Sec. 2.1.2
+// mce_cent): the pericentre distance q = p / (1 + e) when the pericentre is
+// passed, else the nearer end.  The passage is read off the mean anomaly,
+// which advances uniformly: on an ellipse M = E - e sin E (e cos E = 1 - r/a,
+// e sin E = x.v / sqrt(mu a)), pericentres at M = 2 pi k; on a hyperbola
+// M = e sinh F - F (e sinh F = x.v / sqrt(-mu a)), the pericentre at M = 0.
+__device__ __forceinline__ double drift_min_r(double mu, double dt, double x0, double y0, double z0, double vx0,
+                                              double vy0, double vz0, double x1, double y1, double z1, double vx1,
+                                              double vy1, double vz1) {
+    const double r0 = sqrt(dot3(x0, y0, z0, x0, y0, z0)), r1 = sqrt(dot3(x1, y1, z1, x1, y1, z1));
+    double rmin = fmin(r0, r1);
+    const double eta0 = dot3(x0, y0, z0, vx0, vy0, vz0);
+    const double beta = 2.0 * mu / r0 - dot3(vx0, vy0, vz0, vx0, vy0, vz0);
+    const double hx = y0 * vz0 - z0 * vy0, hy = z0 * vx0 - x0 * vz0, hz = x0 * vy0 - y0 * vx0;
+    const double p = dot3(hx, hy, hz, hx, hy, hz) / mu;
+    const double e2 = 1.0 - p * beta / mu;
+    const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
+    const double q = p / (1.0 + e);
+    bool passed;
+    if (beta > 0.0) {
+        const double a = mu / beta, n = sqrt(mu / (a * a * a));
+        const double ecE = 1.0 - r0 / a, esE = eta0 / sqrt(mu * a);
+        const double M0 = atan2(esE, ecE) - esE, M1 = M0 + n * dt;
+        const double lo = fmin(M0, M1), hi = fmax(M0, M1);
+        const double tp = 2.0 * 3.14159265358979323846;
+        passed = tp * ceil(lo / tp) <= hi;
+    } else if (beta < 0.0) {
+        const double a = mu / beta, n = sqrt(mu / (-a * a * a));
+        const double esF = eta0 / sqrt(-mu * a);
+        const double F0 = e > 0.0 ? asinh(esF / e) : 0.0;
+        const double M0 = esF - F0, M1 = M0 + n * dt;
+        passed = (M0 <= 0.0 && M1 >= 0.0) || (M0 >= 0.0 && M1 <= 0.0);
+    } else {
+        passed = dt * eta0 < 0.0 && dt * dot3(x1, y1, z1, vx1, vy1, vz1) >= 0.0;   // parabolic
+    }
+    return passed ? fmin(rmin, q) : rmin;
+}
+
 // float hi/lo split of a double: hi = rn(x), lo = rn(x - hi)
 __device__ __forceinline__ void split_hl(double v, float& hi, float& lo) {
     hi = __double2float_rn(v);
@@ -484,6 +531,7 @@ void launch_open(const Dev& d, cudaStream_t s);
 void launch_sort_bodies(const Dev& d, cudaStream_t s);
 void launch_order_prep(const Dev& d, cudaStream_t s);
 void launch_step_reset(const Dev& d, int nsm, cudaStream_t s);
+void launch_remove(const Dev& d, cudaStream_t s);
 void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, cudaStream_t s);
 void launch_confirm(const Dev& d, int grid, cudaStream_t s);
 void launch_group(const Dev& d, int nsm, cudaStream_t s);

@@ -29,7 +29,8 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("M0", C.c_double), ("dt", C.c_double), ("rcrit_hill", C.c_double),
                 ("bs_tol", C.c_double), ("precision", C.c_int32), ("changeover", C.c_int32),
                 ("kepler_max_iter", C.c_int32), ("bs_max_substeps", C.c_int32),
-                ("encounter_capacity", C.c_int64)]
+                ("encounter_capacity", C.c_int64), ("r_star", C.c_double), ("r_eject", C.c_double),
+                ("eject_every", C.c_int64)]
 
 
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -56,6 +57,7 @@ def _declare(L):
     L.opal_get_state.argtypes = [_P, C.c_int32, C.POINTER(C.c_int64), _I64, _D, _D, _D, _D]
     L.opal_energy_momentum.argtypes = [_P, C.c_int32, C.POINTER(C.c_double), _D, _D, C.POINTER(C.c_double)]
     L.opal_last_step_stats.argtypes = [_P, _I64]
+    L.opal_central_mass.argtypes = [_P, C.c_int32, C.POINTER(C.c_double)]
     L.opal_stream.argtypes = [_P]
     L.opal_stream.restype = C.c_void_p
     L.opal_profile_steps.argtypes = [_P, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _D,
@@ -81,7 +83,7 @@ def _declare(L):
     L.opal_energy_momentum_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, _P, _P, _P, _P, _P]
     for name in ("opal_create", "opal_ensemble_create", "opal_step", "opal_step_async", "opal_wait", "opal_get_state", "opal_energy_momentum",
                  "opal_last_step_stats", "opal_profile_steps", "opal_debug_accel", "opal_debug_drift",
-                 "opal_debug_scan", "opal_debug_bs_group", "opal_energy_momentum_noalloc"):
+                 "opal_debug_scan", "opal_debug_bs_group", "opal_energy_momentum_noalloc", "opal_central_mass"):
         getattr(L, name).restype = C.c_int
 
 
@@ -214,10 +216,17 @@ class Simulation:
         return E.value, L, P, El.value
 
     def stats(self) -> dict:
-        out = np.zeros(6, np.int64)
+        out = np.zeros(8, np.int64)
         _check(lib().opal_last_step_stats(self.ptr, out), self.ptr)
         return dict(n_pairs=int(out[0]), n_groups=int(out[1]), n_mergers=int(out[2]), bs_substeps=int(out[3]),
-                    n_candidates=int(out[4]), kepler_iter_max=int(out[5]))
+                    n_candidates=int(out[4]), kepler_iter_max=int(out[5]), n_accreted=int(out[6]),
+                    n_ejected=int(out[7]))
+
+    def central_mass(self, sys: int = 0) -> float:
+        """The star's mass of system sys (grows by every body it accretes)."""
+        M0 = C.c_double(0.0)
+        _check(lib().opal_central_mass(self.ptr, sys, C.byref(M0)), self.ptr)
+        return M0.value
 
     @property
     def graph_kernels(self) -> int:

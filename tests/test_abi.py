@@ -63,6 +63,9 @@ def _bodies(n=3):
     (lambda b, p: setattr(p, "bs_tol", 0.0), "bs_tol"),
     (lambda b, p: setattr(p, "precision", 2), "precision"),
     (lambda b, p: setattr(p, "changeover", 5), "changeover"),
+    (lambda b, p: setattr(p, "r_star", -1.0), "r_star"),
+    (lambda b, p: setattr(p, "r_eject", float("inf")), "r_eject"),
+    (lambda b, p: setattr(p, "r_eject", 400.0), "eject_every"),          # no interval given
 ])
 def test_invalid_inputs_are_rejected_before_any_device_call(lib, mutate, needle):
     b = list(_bodies())
