@@ -61,6 +61,7 @@ def parse_args(argv=None):
     ap.add_argument("--ensemble-steps", type=int, default=10)
     ap.add_argument("--no-small", action="store_true", help="skip the small-body (planetesimal) workload")
     ap.add_argument("--small-steps", type=int, default=50)
+    ap.add_argument("--no-removals", action="store_true", help="skip the star-collision / ejection run")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args(argv)
 
@@ -243,6 +244,22 @@ def ensemble_rates(seed: int, steps: int, warmup: int):
             "timing": "host clock around opal_step calls (each call ends in a device sync)"}
 
 
+def removal_rates(system, steps: int, warmup: int, flush, plain_ms: float):
+    """The headline workload with star collisions and ejections on, at the
+    paper's settings (Sec. 2.1.2: bodies beyond 400 au removed every 200 yr;
+    the star's radius 0.00465 au): the cost of the removal stages, which run
+    every step (and return at once when nothing is removed)."""
+    from paper_2601_19654_gb300 import opal
+    every = int(round(200.0 / 0.01))
+    sim = opal.Simulation.from_system(system, precision=1, r_star=0.00465, r_eject=400.0, eject_every=every)
+    step_ms, _ = time_steps(sim, steps, warmup, flush)
+    kernels = sim.graph_kernels
+    sim.close()
+    ms = float(np.mean(step_ms))
+    return {"r_star_au": 0.00465, "r_eject_au": 400.0, "eject_every": every, "steps_per_s": 1e3 / ms,
+            "ms_per_step": ms, "overhead_vs_value": ms / plain_ms - 1.0, "kernels_per_step": kernels}
+
+
 def small_body_rates(seed: int, steps: int, warmup: int, flush):
     """The production regime of the paper's Sec. 2.1: 1023 embryos and Jupiter
     (big bodies) with 262144 massless planetesimals (small bodies), mixed
@@ -388,6 +405,8 @@ def run_ours(args, rank, world, local):
             line["ensemble"] = ensemble_rates(args.seed, args.ensemble_steps, 3)
         if not args.no_small:
             line["small_bodies"] = small_body_rates(args.seed, args.small_steps, 5, flush)
+        if not args.no_removals:
+            line["removals"] = removal_rates(system, min(args.steps, 100), 5, flush, ms_per_step)
         if not args.no_cpu_baseline:
             v, done, el, threads, dE = oracle_rate(system, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
