@@ -733,27 +733,30 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
 
 // ---------------------------------------------------------------------------
 // Groups of up to four members (nearly every encounter): the four attempts
-// (step sizes H, H/2, H/4, H/8) are the four blocks of a cluster, and each
-// block splits a round's FP64 work between two warps, which the SM issues
-// from two of its schedulers, each with its own FP64 unit:
-//   warp 0: the stellar term, the midpoint step, and on even rounds the new
-//           row of the extrapolation tableau, the acceptance test and the
-//           decision;
-//   warp 1: the (1 - K) mutual terms.
-// On this chip a warp pays about the same for an FP64 instruction whatever
-// its dependences, so a round costs what its longer warp issues.  Two named
-// barriers hand over each round: the positions of the next evaluation
-// (warp 0 -> 1) and the mutual terms (1 -> 0).  Warp 0 hands over the
-// positions before it extrapolates, so the extrapolation overlaps the next
-// round's mutual terms; a stop is then seen by warp 1 one round late, and
-// the terms of that round are dropped.  Lanes of both warps: k * nm + b
+// (step sizes H, H/2, H/4, H/8) are the four blocks of a cluster.  Inside a
+// block, three warps, which the SM issues from three of its schedulers, each
+// with its own FP64 unit (on this chip a warp pays about the same for an FP64
+// instruction whatever its dependences, so what shortens a round is fewer
+// instructions on the warp that waits):
+//   warp 0 keeps each (sequence, member) state and takes the midpoint steps,
+//          then the extrapolation, acceptance test and decision;
+//   warps 1 and 2 evaluate the accelerations (stellar and (1 - K) mutual
+//          terms) of the even and of the odd evaluation points.
+// In the midpoint sequence x_{m+1} = x_{m-1} + 2h v_m, v_{m+1} = v_{m-1} +
+// 2h a(x_m), the position x_{m+2} needs a(x_m) but not a(x_{m+1}), so the
+// accelerations at two successive points are computed at once: as soon as
+// a(x_m) arrives, warp 0 forms v_{m+1} and x_{m+2} and hands x_{m+2} to the
+// warp of its parity while the other warp is still on a(x_{m+1}).  The
+// arithmetic, and so every result, is that of the sequential scheme.  Four
+// named barriers hand over positions and accelerations, one pair per
+// evaluating warp; buffers are doubled by parity.  Lanes: k * nm + b
 // (sequence k, member b).  Attempt 0 announces its acceptance to the other
-// blocks through distributed shared memory, as in the one-warp cluster form.
+// blocks through distributed shared memory.
 struct WsSh {
     static constexpr int M = 4;
     double y[6][M];                      // current state, component-major
-    double pos[kBsRows][3][M];           // positions of the round's evaluation, per sequence
-    double pacc[kBsRows][3][M];          // mutual terms of the round, per sequence
+    double pos[2][kBsRows][3][M];        // evaluation points, by parity of the round
+    double acc[2][kBsRows][3][M];        // accelerations there
     double row[kBsRows][6][M];           // the last extrapolated row of each member
     double diag[kBsRows][6][M];          // T[k][k] of every finished row
     double raw[6][M];                    // midpoint result of the sequence finishing this round
@@ -761,25 +764,21 @@ struct WsSh {
     double m[M], R[M], rc[M], prc2[M], pinv[M], pc01[M];
     int alive[M], gid[M], big[M], ok[M];
     int kacc;                            // this block's attempt: accepted row, -1 while none
-    int stop;                            // warp 0 tells warp 1 that the rounds are over
+    int stop;                            // warp 0 tells the evaluating warps that the rounds are over
     int decision;                        // the substep number attempt 0 announced
     int dec, gi, collide, nmerge;
     int kq[4];
     double El;
 };
 
-constexpr int kWsThreads = 64;
-constexpr int kBarPos = 1;    // named barrier: next positions written (warp 0 arrives, warp 1 waits)
-constexpr int kBarPair = 2;   // named barrier: mutual terms written (warp 1 arrives, warp 0 waits)
+constexpr int kWsThreads = 96;
+constexpr int kBarPos0 = 1, kBarPos1 = 2;   // named barriers: evaluation points written (warp 0 -> 1, 2)
+constexpr int kBarAcc0 = 3, kBarAcc1 = 4;   // accelerations written (warp 1, 2 -> 0)
 
-__device__ __forceinline__ void ws_bar_sync(int id) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kWsThreads) : "memory");
-}
-__device__ __forceinline__ void ws_bar_arrive(int id) {
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "n"(kWsThreads) : "memory");
-}
+__device__ __forceinline__ void ws_bar_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void ws_bar_arrive(int id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); }
 
-__global__ void __launch_bounds__(kWsThreads) k_bs_ws(Dev d) {
+__global__ void __launch_bounds__(kWsThreads, 8) k_bs_ws(Dev d) {
     __shared__ WsSh S;
     __shared__ int s_gi;
     constexpr int CA = 4, M = WsSh::M;
@@ -791,8 +790,7 @@ __global__ void __launch_bounds__(kWsThreads) k_bs_ws(Dev d) {
     const bool many = d.ctl->ngroups > kBsManyGroups;
     const int* list = many ? d.ghard : nullptr;
     const int ng = many ? d.ctl->nhard : d.ctl->ngroups;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const bool w0 = tid < 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cap = p.bs_max_substeps;
     const double tol2 = p.bs_tol * p.bs_tol;
     int epoch = 0;
@@ -849,64 +847,56 @@ __global__ void __launch_bounds__(kWsThreads) k_bs_ws(Dev d) {
             }
             const double h = ldexp(H, -arank) / n;
             epoch++;
-            if (w0) {
-                // ---- warp 0: stellar terms, midpoint steps, extrapolation, decision
-                double za[6], zb[6];
-                if (act) {
-                    for (int c = 0; c < 6; c++) za[c] = zb[c] = S.y[c][b];
-                    S.pos[k][0][b] = za[0];
-                    S.pos[k][1][b] = za[1];
-                    S.pos[k][2][b] = za[2];
-                }
+            if (warp == 0) {
+                // ---- warp 0: states, midpoint steps, extrapolation, decision.  At
+                // iteration m a lane holds x_{m-1}, x_m, x_{m+1} and v_{m-1}, v_m.
+                double Xm[3], X0[3], X1[3], Vm[3], V0[3];
+                if (act)
+                    for (int c = 0; c < 3; c++) {
+                        X0[c] = Xm[c] = S.y[c][b];
+                        V0[c] = Vm[c] = S.y[3 + c][b];
+                        S.pos[0][k][c][b] = X0[c];
+                        X1[c] = X0[c] + h * V0[c];   // x_1 = x_0 + h v_0
+                        S.pos[1][k][c][b] = X1[c];
+                    }
                 if (lane == 0) {
                     S.kacc = -1;
                     S.stop = 0;
                 }
-                ws_bar_arrive(kBarPos);          // round 0's positions
-                for (int r = 0;; r++) {
-                    const bool live = act && r <= n && S.alive[b];
-                    double sx = 0.0, sy = 0.0, sz = 0.0;
-                    const double px = r == 0 ? za[0] : zb[0], py = r == 0 ? za[1] : zb[1],
-                                 pz = r == 0 ? za[2] : zb[2];
-                    if (live) {
-                        const double r2 = px * px + py * py + pz * pz, ri = rsqrt(r2);
-                        const double sk = -GM0 * (ri * ri * ri);
-                        sx = sk * px;
-                        sy = sk * py;
-                        sz = sk * pz;
-                    }
-                    ws_bar_sync(kBarPair);       // the mutual terms of round r
-                    if (act && r <= n) {
-                        double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-                        if (live) {
-                            f[0] = r == 0 ? za[3] : zb[3];
-                            f[1] = r == 0 ? za[4] : zb[4];
-                            f[2] = r == 0 ? za[5] : zb[5];
-                            f[3] = sx + S.pacc[k][0][b];
-                            f[4] = sy + S.pacc[k][1][b];
-                            f[5] = sz + S.pacc[k][2][b];
-                        }
-                        if (r == 0) {
-                            for (int c = 0; c < 6; c++) zb[c] = za[c] + h * f[c];
-                        } else if (r < n) {
-                            for (int c = 0; c < 6; c++) {
-                                const double znew = za[c] + 2.0 * h * f[c];
-                                za[c] = zb[c];
-                                zb[c] = znew;
+                ws_bar_arrive(kBarPos0);             // points 0 and 1
+                ws_bar_arrive(kBarPos1);
+                for (int m = 0;; m++) {
+                    const int par = m & 1;
+                    ws_bar_sync(par ? kBarAcc1 : kBarAcc0);   // a(x_m)
+                    if (act && m <= n) {
+                        double a[3] = {0.0, 0.0, 0.0};
+                        if (S.alive[b])
+                            for (int c = 0; c < 3; c++) a[c] = S.acc[par][k][c][b];
+                        if (m < n) {
+                            double vn[3];
+                            for (int c = 0; c < 3; c++) vn[c] = m == 0 ? V0[c] + h * a[c] : Vm[c] + 2.0 * h * a[c];
+                            // the point two ahead: x_{m+2} = x_m + 2h v_{m+1}
+                            for (int c = 0; c < 3; c++) {
+                                const double x2 = X0[c] + 2.0 * h * vn[c];
+                                if (m + 2 <= n) S.pos[par][k][c][b] = x2;
+                                Xm[c] = X0[c];
+                                X0[c] = X1[c];
+                                X1[c] = x2;
+                                Vm[c] = V0[c];
+                                V0[c] = vn[c];
                             }
                         } else {
-                            for (int c = 0; c < 6; c++) S.raw[c][b] = 0.5 * (zb[c] + za[c] + h * f[c]);
-                        }
-                        if (r < n) {
-                            S.pos[k][0][b] = zb[0];
-                            S.pos[k][1][b] = zb[1];
-                            S.pos[k][2][b] = zb[2];
+                            // sequence k done: its midpoint result 1/2 (z_n + z_{n-1} + h f(z_n))
+                            for (int c = 0; c < 3; c++) {
+                                S.raw[c][b] = 0.5 * (X0[c] + Xm[c] + h * V0[c]);
+                                S.raw[3 + c][b] = 0.5 * (V0[c] + Vm[c] + h * a[c]);
+                            }
                         }
                     }
-                    ws_bar_arrive(kBarPos);      // warp 1 goes on with round r + 1
-                    if (r >= 2 && (r & 1) == 0) {
-                        // row kr of the tableau: sequence kr finished this round
-                        const int kr = r / 2 - 1;
+                    ws_bar_arrive(par ? kBarPos1 : kBarPos0);   // point m + 2
+                    if (m >= 2 && (m & 1) == 0) {
+                        // row kr of the tableau: sequence kr finished at this point
+                        const int kr = m / 2 - 1;
                         __syncwarp();
                         if (lane < 6 * nm) {
                             const int c = lane / nm, bb = lane % nm;
@@ -950,34 +940,41 @@ __global__ void __launch_bounds__(kWsThreads) k_bs_ws(Dev d) {
                     int st = 0;
                     if (lane == 0)
                         st = S.kacc >= 0 || *reinterpret_cast<volatile int*>(&S.decision) == epoch ||
-                             r == 2 * kBsRows;
+                             m == 2 * kBsRows;
                     if (__shfl_sync(0xffffffffu, st, 0)) {
-                        ws_bar_sync(kBarPair);   // warp 1's terms of round r + 1, dropped
+                        // the evaluations of points m + 1 and m + 2 are under way: take
+                        // (and drop) them, then release both warps with the stop flag
+                        ws_bar_sync(par ? kBarAcc0 : kBarAcc1);
+                        ws_bar_sync(par ? kBarAcc1 : kBarAcc0);
                         if (lane == 0) S.stop = 1;
-                        ws_bar_arrive(kBarPos);
+                        ws_bar_arrive(kBarPos0);
+                        ws_bar_arrive(kBarPos1);
                         break;
                     }
                 }
             } else {
-                // ---- warp 1: the mutual terms of each round
-                for (int r = 0;; r++) {
-                    ws_bar_sync(kBarPos);
+                // ---- warps 1 and 2: accelerations at the points of their parity
+                const int par = warp - 1;
+                for (int m = par;; m += 2) {
+                    ws_bar_sync(par ? kBarPos1 : kBarPos0);
                     if (*reinterpret_cast<volatile int*>(&S.stop)) break;
-                    if (act && r <= n && S.alive[b]) {
-                        const double px = S.pos[k][0][b], py = S.pos[k][1][b], pz = S.pos[k][2][b];
-                        double ax = 0.0, ay = 0.0, az = 0.0;
+                    if (act && m <= n && S.alive[b]) {
+                        const double px = S.pos[par][k][0][b], py = S.pos[par][k][1][b], pz = S.pos[par][k][2][b];
+                        const double r2 = px * px + py * py + pz * pz, ri = rsqrt(r2);
+                        const double sk = -GM0 * (ri * ri * ri);
+                        double ax = sk * px, ay = sk * py, az = sk * pz;
                         for (int j = 0; j < nm - 1; j++) {   // the other members, ascending
                             const int o = j + (j >= b ? 1 : 0);
                             if (!S.alive[o] || !S.big[o]) continue;
                             const int w = S.rc[b] > S.rc[o] ? b : o;
-                            bs_pair(p, px, py, pz, S.pos[k][0][o], S.pos[k][1][o], S.pos[k][2][o], S.m[o], S.rc[w],
-                                    S.prc2[w], S.pc01[w], S.pinv[w], ax, ay, az);
+                            bs_pair(p, px, py, pz, S.pos[par][k][0][o], S.pos[par][k][1][o], S.pos[par][k][2][o],
+                                    S.m[o], S.rc[w], S.prc2[w], S.pc01[w], S.pinv[w], ax, ay, az);
                         }
-                        S.pacc[k][0][b] = ax;
-                        S.pacc[k][1][b] = ay;
-                        S.pacc[k][2][b] = az;
+                        S.acc[par][k][0][b] = ax;
+                        S.acc[par][k][1][b] = ay;
+                        S.acc[par][k][2][b] = az;
                     }
-                    ws_bar_arrive(kBarPair);
+                    ws_bar_arrive(par ? kBarAcc1 : kBarAcc0);
                 }
             }
             __syncthreads();
@@ -1083,7 +1080,7 @@ cudaError_t bs_setup() {
 int bs_block_regs() {
     cudaFuncAttributes a{};
     if (cudaFuncGetAttributes(&a, k_bs_ws) != cudaSuccess) return 65536;
-    return a.numRegs * kWsThreads;
+    return ((a.numRegs + 7) / 8 * 8) * kWsThreads;
 }
 
 void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {

@@ -722,9 +722,11 @@ int kick_itile(int precision, int v) {
     const KickVariant& k = precision == 1 ? kMixed[v] : kFp64[v];
     return k.threads * k.ni;
 }
+// registers one block holds as the SM allocates them (per warp, in units of
+// 8 per thread)
 int kick_block_regs(int precision, int v) {
     const KickVariant& k = precision == 1 ? kMixed[v] : kFp64[v];
-    return k.threads * k.regs();
+    return k.threads * ((k.regs() + 7) / 8 * 8);
 }
 int kick_occupancy(int precision, int v) { return precision == 1 ? kMixed[v].occupancy() : kFp64[v].occupancy(); }
 void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int v,

@@ -521,13 +521,14 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         s->kick_variant = best;
         s->items = var_items[best];
         s->sys = var_sys[best];
-        // the kick runs beside the encounter integrator: leave each SM room for one of its blocks
+        // the kick runs beside the encounter integrator: as many kick blocks an
+        // SM as leave the registers of one encounter block free
         {
             const int occ = std::max(1, kick_occupancy(p->precision, best));
             const int kr = std::max(1, kick_block_regs(p->precision, best));
-            const int room = (bs_block_regs() + kr - 1) / kr;
+            const int fit = (65536 - bs_block_regs()) / kr;
             s->kick_grid = (int)std::min<int64_t>((int64_t)var_items[best].size(),
-                                                  (int64_t)s->nsm * std::max(1, occ - room));
+                                                  (int64_t)s->nsm * std::max(1, std::min(occ, fit)));
         }
         snprintf(s->kick_desc, sizeof(s->kick_desc), "%s, grid %d, %zu items, %d j-chunks (system 0)%s",
                  kick_variant_name(p->precision, best), s->kick_grid, s->items.size(), s->sys[0].nchunk,
