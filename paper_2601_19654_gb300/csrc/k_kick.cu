@@ -87,7 +87,7 @@ __device__ __forceinline__ void kick_tile(const float4* sj, const float4* sl, co
     // NJ > 0: a full tile, the trip count known at compile time.  Near tiles
     // are few: a rolled loop keeps their registers down.
     const int n = NJ > 0 ? NJ : nj;
-#pragma unroll(NEAR ? 1 : 4)
+#pragma unroll(NEAR ? 2 : 8)
     for (int jj = 0; jj < n; jj++) {
         const float4 pj = sj[jj];
 #pragma unroll
