@@ -131,20 +131,24 @@ __device__ __forceinline__ void bs_pair(const Params& p, double xb, double yb, d
     az += t * dz;
 }
 
-// acceleration of member b of sequence k at its position (x, y, z)
+// acceleration of member b of sequence k at its position (x, y, z): the part
+// of lane si of the sp lanes that share (k, b) -- the stellar term (si = 0)
+// and the mutual terms of every sp-th other member from the si-th; the
+// caller sums the sp parts
 template <int NT, int A>
 __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, double GM0, int nm, int a, int k,
-                                         int b, double xb, double yb, double zb, double& ax, double& ay, double& az) {
+                                         int b, int si, int sp, double xb, double yb, double zb, double& ax,
+                                         double& ay, double& az) {
     double r2 = xb * xb + yb * yb + zb * zb, ri = rsqrt(r2);
-    double s = -GM0 * (ri * ri * ri);
+    double s = si == 0 ? -GM0 * (ri * ri * ri) : 0.0;
     ax = s * xb;
     ay = s * yb;
     az = s * zb;
-    // the j-th other member in ascending order (the oracle's order): every lane
-    // has nm - 1 of them, so the lanes run each pass together (a loop over all
-    // o that skips o == b would run the FP64 pair code once per member, each
-    // time with a different lane idle)
-    for (int j = 0; j < nm - 1; j++) {
+    // the j-th other member in ascending order (the oracle's order when sp = 1):
+    // every lane has the same number of them, so the lanes run each pass
+    // together (a loop over all o that skips o == b would run the FP64 pair
+    // code once per member, each time with a different lane idle)
+    for (int j = si; j < nm - 1; j += sp) {
         const int o = j + (j >= b ? 1 : 0);
         if (!S.alive[o] || !S.big[o]) continue;   // (integer tests: no FP64 work)
         const int w = S.rc[b] > S.rc[o] ? b : o;   // rc_bo = max(rc_b, rc_o)
@@ -211,7 +215,18 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
             if (tid == 0 && arank == 0) set_status(d.ctl, kEoverflow, 1000000 + g);
             return;
         }
-        const int k = lt / nm, b = lt % nm;       // sequence and member of this thread
+        // sp lanes a (sequence, member), adjacent, split its mutual terms (a
+        // power of two, so that a warp's shuffles sum them; no more parts than
+        // the group has big members, the only sources)
+        int nbg = 0;
+        for (int q = 0; q < nm; q++) {
+            const int gb = d.members[mb + q];
+            const SysInfo& gs = d.sys[d.body_sys[gb]];
+            nbg += gb - gs.off < gs.nb ? 1 : 0;
+        }
+        int sp = 1;
+        while (2 * sp * kBsRows * nm <= TA && sp < 32 && 2 * sp <= nbg) sp *= 2;
+        const int si = lt % sp, k = (lt / sp) / nm, b = (lt / sp) % nm;   // part, sequence, member
         const bool act = k < kBsRows;
         const double M0g = d.M0s[d.body_sys[d.members[mb]]];   // the star of the group's system
         if (tid < nm) {
@@ -273,17 +288,21 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int k
                     S.pos[a][k][2][b] = zp[2];
                 }
                 __syncthreads();
-                if (live) {
-                    double f[6];
+                double f[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                if (live && S.alive[b]) {
                     const double* zp = (r == 0) ? za : zb;
-                    if (S.alive[b]) {
-                        f[0] = zp[3];
-                        f[1] = zp[4];
-                        f[2] = zp[5];
-                        bs_accel<NT, A>(S, p, p.G * M0g, nm, a, k, b, zp[0], zp[1], zp[2], f[3], f[4], f[5]);
-                    } else {
-                        for (int c = 0; c < 6; c++) f[c] = 0.0;
-                    }
+                    f[0] = zp[3];
+                    f[1] = zp[4];
+                    f[2] = zp[5];
+                    bs_accel<NT, A>(S, p, p.G * M0g, nm, a, k, b, si, sp, zp[0], zp[1], zp[2], f[3], f[4], f[5]);
+                }
+                // sum the sp parts (every lane of the block takes part)
+                for (int o = sp >> 1; o >= 1; o >>= 1) {
+                    f[3] += __shfl_xor_sync(0xffffffffu, f[3], o);
+                    f[4] += __shfl_xor_sync(0xffffffffu, f[4], o);
+                    f[5] += __shfl_xor_sync(0xffffffffu, f[5], o);
+                }
+                if (live) {
                     if (r == 0) {
                         for (int c = 0; c < 6; c++) zb[c] = za[c] + h * f[c];
                     } else if (r < n) {
