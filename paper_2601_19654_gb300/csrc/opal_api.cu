@@ -272,11 +272,16 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     } while (0)
     CKF(cudaGetDevice(&s->dev));
     CKF(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
-    CKF(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
-    CKF(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+    // the encounter kernels' streams outrank the kick's: when both are ready
+    // (the fork of the step graph) the encounter blocks, which hold the
+    // critical path, are placed first and the kick fills the rest
+    int prio_lo = 0, prio_hi = 0;
+    CKF(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    CKF(cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, prio_hi));
+    CKF(cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, prio_lo));
     CKF(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
     CKF(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
-    CKF(cudaStreamCreateWithFlags(&s->side2, cudaStreamNonBlocking));
+    CKF(cudaStreamCreateWithPriority(&s->side2, cudaStreamNonBlocking, prio_hi));
     CKF(cudaEventCreateWithFlags(&s->fork2_ev, cudaEventDisableTiming));
     CKF(cudaEventCreateWithFlags(&s->join2_ev, cudaEventDisableTiming));
     CKF(bs_setup());
