@@ -1118,9 +1118,8 @@ void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent
     k_bs<kBsLargerThreads, 1, 1><<<nsm, kBsLargerThreads, sizeof(BsSh<kBsLargerThreads, 1>), s2>>>(d, 2);
     if (s2 == s) prof_mark("bs: groups of 33-64");
     launch_bs_huge(d, nsm, s2);
-    if (s2 == s) prof_mark("bs: groups of 33-64");
     {
-        // groups of up to 4 members: clusters of four two-warp blocks, one attempt each
+        // groups of up to 4 members: clusters of four three-warp blocks, one attempt each
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(4 * 2 * nsm));
         cfg.blockDim = dim3(kWsThreads);
