@@ -45,7 +45,8 @@ FLOPS_PER_INTERACTION = 18
 # DRAM bytes (read + written) of one launch of the kick variants the autotuner
 # picks on this workload, from ncu captures of the current kernel (the
 # summaries are committed beside the profiles); another variant reports none
-KICK_TRAFFIC = {"mixed t128 i1 r": 1.559552e6 + 0.71936e6, "mixed t128 i1": 3.064064e6 + 2.145792e6}
+KICK_TRAFFIC = {"mixed t128 i1 r": 1.559552e6 + 0.71936e6, "mixed t128 i1": 3.064064e6 + 2.145792e6,
+               "mixed t128 i1 5": 1.570048e6 + 0.690944e6}
 
 
 def parse_args(argv=None):
