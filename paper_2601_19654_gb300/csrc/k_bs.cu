@@ -1102,22 +1102,36 @@ int bs_block_regs() {
     return ((a.numRegs + 7) / 8 * 8) * kWsThreads;
 }
 
-void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
+void launch_bs_packed(const Dev& d, int nsm, cudaStream_t s) {
     // two warps an SM: FP64 issues about one warp instruction per 17 cycles an
     // SM, so fewer warps sharing it finish their groups' chains sooner
     k_bs_packed<<<nsm, 32 * kPkWarps, kPkWarps * sizeof(PkWarp), s>>>(d);
     prof_mark("bs: many groups, packed");
-    // the small- and large-group kernels side by side (two small blocks and one
-    // large one fill an SM's registers); s2 == s runs them one after the other
+}
+
+// The lockstep kernels: groups of up to 4 members on s, the larger groups on
+// the branch s2 (s2 == s: one after the other).  Within a stream priority,
+// blocks are placed in launch order, and a kernel whose blocks do not fit yet
+// holds back the kernels launched after it.  small_first (the kick runs
+// beside, on a stream of lower priority than s2, which is lower than s): the
+// small-group kernel goes first, since beside the kick's blocks only its
+// blocks fit (a larger-group block takes half an SM's registers or more).
+// Otherwise the larger-group kernels go first, on a branch of the same
+// priority, and the small-group blocks fill the room they leave.
+void launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join,
+                        bool small_first) {
     if (s2 != s) {
         cudaEventRecord(fork, s);
         cudaStreamWaitEvent(s2, fork, 0);
     }
-    k_bs<kBsLargeThreads, 1, 1><<<nsm, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s2>>>(d, 1);
-    if (s2 == s) prof_mark("bs: groups of 5-32");
-    k_bs<kBsLargerThreads, 1, 1><<<nsm, kBsLargerThreads, sizeof(BsSh<kBsLargerThreads, 1>), s2>>>(d, 2);
-    if (s2 == s) prof_mark("bs: groups of 33-64");
-    launch_bs_huge(d, nsm, s2);
+    auto larger = [&] {
+        k_bs<kBsLargeThreads, 1, 1><<<nsm, kBsLargeThreads, sizeof(BsSh<kBsLargeThreads, 1>), s2>>>(d, 1);
+        if (s2 == s) prof_mark("bs: groups of 5-32");
+        k_bs<kBsLargerThreads, 1, 1><<<nsm, kBsLargerThreads, sizeof(BsSh<kBsLargerThreads, 1>), s2>>>(d, 2);
+        if (s2 == s) prof_mark("bs: groups of 33-64");
+        launch_bs_huge(d, nsm, s2);
+    };
+    if (!small_first) larger();
     {
         // groups of up to 4 members: clusters of four three-warp blocks, one attempt each
         cudaLaunchConfig_t cfg = {};
@@ -1135,6 +1149,7 @@ void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent
         cudaLaunchKernelEx(&cfg, k_bs_ws, d);
     }
     prof_mark("bs: groups <= 4");
+    if (small_first) larger();
     if (s2 != s) {
         cudaEventRecord(join, s2);
         cudaStreamWaitEvent(s, join, 0);

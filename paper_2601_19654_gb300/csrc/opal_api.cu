@@ -71,7 +71,8 @@ struct opal_sim {
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;             // the kick's branch of the step graph
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-    cudaStream_t side2 = nullptr;            // the large-group BS kernel's branch
+    cudaStream_t side2 = nullptr;            // the large-group BS kernels' branch (in order)
+    cudaStream_t side3 = nullptr;            // the same beside the kick, one priority lower
     cudaEvent_t fork2_ev = nullptr, join2_ev = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -274,14 +275,19 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     CKF(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
     // the encounter kernels' streams outrank the kick's: when both are ready
     // (the fork of the step graph) the encounter blocks, which hold the
-    // critical path, are placed first and the kick fills the rest
+    // critical path, are placed first and the kick fills the rest.  Beside
+    // the kick the larger-group branch runs one priority below the main
+    // stream, so that its blocks, which wait for room, hold back no
+    // small-group block.
     int prio_lo = 0, prio_hi = 0;
     CKF(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    const int prio_mid = prio_hi < prio_lo ? prio_hi + 1 : prio_hi;
     CKF(cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, prio_hi));
     CKF(cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, prio_lo));
     CKF(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
     CKF(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming));
     CKF(cudaStreamCreateWithPriority(&s->side2, cudaStreamNonBlocking, prio_hi));
+    CKF(cudaStreamCreateWithPriority(&s->side3, cudaStreamNonBlocking, prio_mid));
     CKF(cudaEventCreateWithFlags(&s->fork2_ev, cudaEventDisableTiming));
     CKF(cudaEventCreateWithFlags(&s->join2_ev, cudaEventDisableTiming));
     CKF(bs_setup());
@@ -585,8 +591,9 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
         case 3: launch_confirm(d, s->confirm_grid, st); break;
         case 4: launch_group(d, s->nsm, st); break;
         case kStageBs:
-            // the two lockstep kernels on parallel branches (one stream when profiling)
-            launch_bs(d, s->nsm, st, g_prof ? st : s->side2, s->fork2_ev, s->join2_ev);
+            // the lockstep kernels on parallel branches (one stream when profiling)
+            launch_bs_packed(d, s->nsm, st);
+            launch_bs_lockstep(d, s->nsm, st, g_prof ? st : s->side2, s->fork2_ev, s->join2_ev, false);
             break;
         case kStageKick:
             launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
@@ -647,14 +654,17 @@ opal_status capture_graph(opal_sim* s) {
         const int k = order[q];
         if (s->d.overlap && k == kStageKick) continue;
         if (s->d.overlap && k == kStageBs) {
-            // fork: the kick on the side stream, the encounter integrator here; join before the fix
+            // fork: the kick on the side stream, the encounter integrator here; join before the fix.
+            // The packed kernel (many groups; at once done otherwise) runs before the fork: its
+            // blocks do not fit beside the kick's, and the lockstep kernels wait for it.
+            launch_bs_packed(s->d, s->nsm, s->stream);
             CK(cudaEventRecord(s->fork_ev, s->stream));
             CK(cudaStreamWaitEvent(s->side, s->fork_ev, 0));
             if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[0], s->side, cudaEventRecordExternal);
             launch_stage(s, kStageKick, s->side);
             if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[1], s->side, cudaEventRecordExternal);
             CK(cudaEventRecord(s->join_ev, s->side));
-            launch_stage(s, kStageBs, s->stream);
+            launch_bs_lockstep(s->d, s->nsm, s->stream, s->side3, s->fork2_ev, s->join2_ev, true);
             CK(cudaStreamWaitEvent(s->stream, s->join_ev, 0));
             continue;
         }
@@ -928,6 +938,7 @@ void opal_destroy(opal_sim* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->side) cudaStreamSynchronize(s->side);
     if (s->side2) cudaStreamSynchronize(s->side2);
+    if (s->side3) cudaStreamSynchronize(s->side3);
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->graph) cudaGraphDestroy(s->graph);
     for (auto e : s->kick_ev)
@@ -938,6 +949,7 @@ void opal_destroy(opal_sim* s) {
     if (s->fork_ev) cudaEventDestroy(s->fork_ev);
     if (s->join_ev) cudaEventDestroy(s->join_ev);
     if (s->side2) cudaStreamDestroy(s->side2);
+    if (s->side3) cudaStreamDestroy(s->side3);
     if (s->fork2_ev) cudaEventDestroy(s->fork2_ev);
     if (s->join2_ev) cudaEventDestroy(s->join2_ev);
     delete s;
@@ -1113,7 +1125,8 @@ opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0,
     CK(cudaMemcpy(d.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
     CK(cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), s->stream));
     CK(cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), s->stream));
-    launch_bs(d, s->nsm, s->stream, s->stream, nullptr, nullptr);
+    launch_bs_packed(d, s->nsm, s->stream);
+    launch_bs_lockstep(d, s->nsm, s->stream, s->stream, nullptr, nullptr, false);
     launch_bs_apply(d, s->nsm, s->stream);   // puts the result into the state
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));

@@ -536,7 +536,9 @@ void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, 
 void launch_confirm(const Dev& d, int grid, cudaStream_t s);
 void launch_group(const Dev& d, int nsm, cudaStream_t s);
 cudaError_t bs_setup();   // dynamic shared memory of the BS kernels
-void launch_bs(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
+void launch_bs_packed(const Dev& d, int nsm, cudaStream_t s);
+void launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join,
+                        bool small_first);
 void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int variant,
                  cudaStream_t s);
 // after the BS: apply its results; fix the kick's rows when it ran beside the BS
