@@ -107,24 +107,33 @@ __device__ void bs_merge(SH& S, const Params& p, double M0, int b, int q, double
 // the member with the larger rc (rc_bo = max(rc_b, rc_o)): rc, rc^2, 0.1 rc and
 // 1 / (0.9 rc), so K needs no division by rc.  Callers pass big members only:
 // a small body pulls nothing (Sec. 2.1: only big bodies are gravity sources).
+// Comparisons of doubles as their bit patterns: for values >= +0 the IEEE
+// patterns order as the values, and a value is <= 0 exactly when its pattern,
+// read as a signed integer, is.  The integer units take these tests, which
+// leaves the FP64 pipe (one warp instruction per many cycles) to the
+// arithmetic on the encounter integrator's critical chain.
+__device__ __forceinline__ bool ge_nonneg(double a, double b) {   // a >= b, both >= +0
+    return __double_as_longlong(a) >= __double_as_longlong(b);
+}
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {   // a > b, both >= +0
+    return __double_as_longlong(a) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool le_zero(double a) { return __double_as_longlong(a) <= 0; }
+
 __device__ __forceinline__ void bs_pair(const Params& p, double xb, double yb, double zb, double xo, double yo,
                                         double zo, double mo, double rc, double rc2, double c01, double inv,
                                         double& ax, double& ay, double& az) {
     const double dx = xo - xb, dy = yo - yb, dz = zo - zb;
     const double dr2 = dx * dx + dy * dy + dz * dz;
-    if (dr2 >= rc2) return;   // 1 - K = 0 at or beyond rc
+    if (ge_nonneg(dr2, rc2)) return;   // 1 - K = 0 at or beyond rc
     const double dri = rsqrt(dr2), dr = dr2 * dri;
+    if (ge_nonneg(dr, rc)) return;
     double K;
-    if (dr >= rc) {
-        K = 1.0;
-    } else {
-        const double y = (dr - c01) * inv;
-        if (y <= 0.0) K = 0.0;
-        else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
-        else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
-    }
+    const double y = (dr - c01) * inv;
+    if (le_zero(y)) K = 0.0;
+    else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
+    else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
     const double wgt = 1.0 - K;
-    if (wgt == 0.0) return;
     const double t = p.G * mo * wgt * (dri * dri * dri);
     ax += t * dx;
     ay += t * dy;
@@ -151,7 +160,7 @@ __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, 
     for (int j = si; j < nm - 1; j += sp) {
         const int o = j + (j >= b ? 1 : 0);
         if (!S.alive[o] || !S.big[o]) continue;   // (integer tests: no FP64 work)
-        const int w = S.rc[b] > S.rc[o] ? b : o;   // rc_bo = max(rc_b, rc_o)
+        const int w = gt_nonneg(S.rc[b], S.rc[o]) ? b : o;   // rc_bo = max(rc_b, rc_o)
         bs_pair(p, xb, yb, zb, S.pos[a][k][0][o], S.pos[a][k][1][o], S.pos[a][k][2][o], S.m[o], S.rc[w],
                 S.prc2[w], S.pc01[w], S.pinv[w], ax, ay, az);
     }
@@ -610,7 +619,7 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
                 for (int j = 0; j < Wc - 1; j++) {   // the j-th other lane of the segment, ascending
                     const int o = base + j + (j >= sl ? 1 : 0);
                     if (!W.alive[o] || !W.big[o]) continue;
-                    const int w = W.rc[lane] > W.rc[o] ? lane : o;
+                    const int w = gt_nonneg(W.rc[lane], W.rc[o]) ? lane : o;
                     bs_pair(p, P0, P1, P2, W.px[o], W.py[o], W.pz[o], W.m[o], W.rc[w], W.prc2[w], W.pc01[w],
                             W.pinv[w], ax, ay, az);
                 }
@@ -985,7 +994,7 @@ __global__ void __launch_bounds__(kWsThreads, 8) k_bs_ws(Dev d) {
                         for (int j = 0; j < nm - 1; j++) {   // the other members, ascending
                             const int o = j + (j >= b ? 1 : 0);
                             if (!S.alive[o] || !S.big[o]) continue;
-                            const int w = S.rc[b] > S.rc[o] ? b : o;
+                            const int w = gt_nonneg(S.rc[b], S.rc[o]) ? b : o;
                             bs_pair(p, px, py, pz, S.pos[par][k][0][o], S.pos[par][k][1][o], S.pos[par][k][2][o],
                                     S.m[o], S.rc[w], S.prc2[w], S.pc01[w], S.pinv[w], ax, ay, az);
                         }
