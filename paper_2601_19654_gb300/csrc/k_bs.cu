@@ -107,18 +107,6 @@ __device__ void bs_merge(SH& S, const Params& p, double M0, int b, int q, double
 // the member with the larger rc (rc_bo = max(rc_b, rc_o)): rc, rc^2, 0.1 rc and
 // 1 / (0.9 rc), so K needs no division by rc.  Callers pass big members only:
 // a small body pulls nothing (Sec. 2.1: only big bodies are gravity sources).
-// Comparisons of doubles as their bit patterns: for values >= +0 the IEEE
-// patterns order as the values, and a value is <= 0 exactly when its pattern,
-// read as a signed integer, is.  The integer units take these tests, which
-// leaves the FP64 pipe (one warp instruction per many cycles) to the
-// arithmetic on the encounter integrator's critical chain.
-__device__ __forceinline__ bool ge_nonneg(double a, double b) {   // a >= b, both >= +0
-    return __double_as_longlong(a) >= __double_as_longlong(b);
-}
-__device__ __forceinline__ bool gt_nonneg(double a, double b) {   // a > b, both >= +0
-    return __double_as_longlong(a) > __double_as_longlong(b);
-}
-__device__ __forceinline__ bool le_zero(double a) { return __double_as_longlong(a) <= 0; }
 
 __device__ __forceinline__ void bs_pair(const Params& p, double xb, double yb, double zb, double xo, double yo,
                                         double zo, double mo, double rc, double rc2, double c01, double inv,
@@ -768,23 +756,29 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
 // instructions on the warp that waits):
 //   warp 0 keeps each (sequence, member) state and takes the midpoint steps,
 //          then the extrapolation, acceptance test and decision;
-//   warps 1 and 2 evaluate the accelerations (stellar and (1 - K) mutual
-//          terms) of the even and of the odd evaluation points.
+//   warps 1 and 2 evaluate the (1 - K) mutual terms at the even and at the
+//          odd evaluation points;
+//   warp 3 evaluates the stellar term at every point, in order.
 // In the midpoint sequence x_{m+1} = x_{m-1} + 2h v_m, v_{m+1} = v_{m-1} +
 // 2h a(x_m), the position x_{m+2} needs a(x_m) but not a(x_{m+1}), so the
 // accelerations at two successive points are computed at once: as soon as
 // a(x_m) arrives, warp 0 forms v_{m+1} and x_{m+2} and hands x_{m+2} to the
 // warp of its parity while the other warp is still on a(x_{m+1}).  The
-// arithmetic, and so every result, is that of the sequential scheme.  Four
-// named barriers hand over positions and accelerations, one pair per
-// evaluating warp; buffers are doubled by parity.  Lanes: k * nm + b
+// arithmetic is that of the sequential scheme, except that a point's
+// acceleration is the stellar term plus the sum of the mutual terms (the
+// two parts come from different warps).  Four named barriers hand over
+// positions and accelerations, one pair per parity, each met by warp 0, the
+// mutual warp of its parity and the stellar warp; buffers are doubled by
+// parity.  The four warps sit on the SM's four schedulers, each with its
+// own FP64 unit.  Lanes: k * nm + b
 // (sequence k, member b).  Attempt 0 announces its acceptance to the other
 // blocks through distributed shared memory.
 struct WsSh {
     static constexpr int M = 4;
     double y[6][M];                      // current state, component-major
     double pos[2][kBsRows][3][M];        // evaluation points, by parity of the round
-    double acc[2][kBsRows][3][M];        // accelerations there
+    double acc[2][kBsRows][3][M];        // mutual terms there
+    double sacc[2][kBsRows][3][M];       // stellar terms there
     double row[kBsRows][6][M];           // the last extrapolated row of each member
     double diag[kBsRows][6][M];          // T[k][k] of every finished row
     double raw[6][M];                    // midpoint result of the sequence finishing this round
@@ -799,14 +793,15 @@ struct WsSh {
     double El;
 };
 
-constexpr int kWsThreads = 96;
-constexpr int kBarPos0 = 1, kBarPos1 = 2;   // named barriers: evaluation points written (warp 0 -> 1, 2)
-constexpr int kBarAcc0 = 3, kBarAcc1 = 4;   // accelerations written (warp 1, 2 -> 0)
+constexpr int kWsThreads = 128;
+constexpr int kBarPos0 = 1, kBarPos1 = 2;   // named barriers: evaluation points written (warp 0 -> 1 or 2, and 3)
+constexpr int kBarAcc0 = 3, kBarAcc1 = 4;   // accelerations written (warp 1 or 2, and 3 -> 0)
 
-__device__ __forceinline__ void ws_bar_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
-__device__ __forceinline__ void ws_bar_arrive(int id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); }
+// every named barrier is met by three warps
+__device__ __forceinline__ void ws_bar_sync(int id) { asm volatile("bar.sync %0, 96;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void ws_bar_arrive(int id) { asm volatile("bar.arrive %0, 96;" ::"r"(id) : "memory"); }
 
-__global__ void __launch_bounds__(kWsThreads, 8) k_bs_ws(Dev d) {
+__global__ void __launch_bounds__(kWsThreads, 6) k_bs_ws(Dev d) {
     __shared__ WsSh S;
     __shared__ int s_gi;
     constexpr int CA = 4, M = WsSh::M;
@@ -899,7 +894,7 @@ __global__ void __launch_bounds__(kWsThreads, 8) k_bs_ws(Dev d) {
                     if (act && m <= n) {
                         double a[3] = {0.0, 0.0, 0.0};
                         if (S.alive[b])
-                            for (int c = 0; c < 3; c++) a[c] = S.acc[par][k][c][b];
+                            for (int c = 0; c < 3; c++) a[c] = S.sacc[par][k][c][b] + S.acc[par][k][c][b];
                         if (m < n) {
                             double vn[3];
                             for (int c = 0; c < 3; c++) vn[c] = m == 0 ? V0[c] + h * a[c] : Vm[c] + 2.0 * h * a[c];
@@ -980,17 +975,36 @@ __global__ void __launch_bounds__(kWsThreads, 8) k_bs_ws(Dev d) {
                         break;
                     }
                 }
+            } else if (warp == 3) {
+                // ---- warp 3: the stellar term at every point, in order.  At the
+                // stop, warp 0 releases both position barriers: this warp meets
+                // the second one too, which the other parity's warp waits at.
+                for (int m = 0;; m++) {
+                    const int par = m & 1;
+                    ws_bar_sync(par ? kBarPos1 : kBarPos0);
+                    if (*reinterpret_cast<volatile int*>(&S.stop)) {
+                        ws_bar_sync(par ? kBarPos0 : kBarPos1);
+                        break;
+                    }
+                    if (act && m <= n && S.alive[b]) {
+                        const double px = S.pos[par][k][0][b], py = S.pos[par][k][1][b], pz = S.pos[par][k][2][b];
+                        const double r2 = px * px + py * py + pz * pz, ri = rsqrt(r2);
+                        const double sk = -GM0 * (ri * ri * ri);
+                        S.sacc[par][k][0][b] = sk * px;
+                        S.sacc[par][k][1][b] = sk * py;
+                        S.sacc[par][k][2][b] = sk * pz;
+                    }
+                    ws_bar_arrive(par ? kBarAcc1 : kBarAcc0);
+                }
             } else {
-                // ---- warps 1 and 2: accelerations at the points of their parity
+                // ---- warps 1 and 2: mutual terms at the points of their parity
                 const int par = warp - 1;
                 for (int m = par;; m += 2) {
                     ws_bar_sync(par ? kBarPos1 : kBarPos0);
                     if (*reinterpret_cast<volatile int*>(&S.stop)) break;
                     if (act && m <= n && S.alive[b]) {
                         const double px = S.pos[par][k][0][b], py = S.pos[par][k][1][b], pz = S.pos[par][k][2][b];
-                        const double r2 = px * px + py * py + pz * pz, ri = rsqrt(r2);
-                        const double sk = -GM0 * (ri * ri * ri);
-                        double ax = sk * px, ay = sk * py, az = sk * pz;
+                        double ax = 0.0, ay = 0.0, az = 0.0;
                         for (int j = 0; j < nm - 1; j++) {   // the other members, ascending
                             const int o = j + (j >= b ? 1 : 0);
                             if (!S.alive[o] || !S.big[o]) continue;

@@ -63,24 +63,21 @@ __device__ bool huge_sync(HugeCtl* hc) {
 __device__ __forceinline__ void huge_pair(const Dev& d, const Params& p, int b, int o, double xb, double yb,
                                           double zb, double& ax, double& ay, double& az) {
     const HugeBuf& H = d.hb;
-    const int w = H.rc[b] > H.rc[o] ? b : o;
+    if (le_zero(H.m[o])) return;   // a small body (m = 0): no source
+    const int w = gt_nonneg(H.rc[b], H.rc[o]) ? b : o;
     const double rc = H.rc[w];
     const int64_t c = H.cap;
     const double dx = H.pos[o] - xb, dy = H.pos[c + o] - yb, dz = H.pos[2 * c + o] - zb;
     const double dr2 = dx * dx + dy * dy + dz * dz;
-    if (dr2 >= rc * rc || H.m[o] == 0.0) return;   // beyond rc, or a small body (no source)
+    if (ge_nonneg(dr2, rc * rc)) return;   // 1 - K = 0 at or beyond rc
     const double dri = rsqrt(dr2), dr = dr2 * dri;
+    if (ge_nonneg(dr, rc)) return;
     double K;
-    if (dr >= rc) {
-        K = 1.0;
-    } else {
-        const double y = (dr - 0.1 * rc) * H.pinv[w];
-        if (y <= 0.0) K = 0.0;
-        else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
-        else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
-    }
+    const double y = (dr - 0.1 * rc) * H.pinv[w];
+    if (le_zero(y)) K = 0.0;
+    else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
+    else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
     const double wgt = 1.0 - K;
-    if (wgt == 0.0) return;
     const double t = p.G * H.m[o] * wgt * (dri * dri * dri);
     ax += t * dx;
     ay += t * dy;

@@ -296,6 +296,19 @@ __device__ __forceinline__ void system_total(const Dev& d, const double* part, c
     if (threadIdx.x == 0) counter[s] = 0;
 }
 
+// Comparisons of doubles as their bit patterns: for values >= +0 the IEEE
+// patterns order as the values, and a value is <= 0 exactly when its pattern,
+// read as a signed integer, is.  The integer units take these tests, which
+// leaves the FP64 pipe (one warp instruction per many cycles) to the
+// arithmetic on the encounter integrator's critical chain.
+__device__ __forceinline__ bool ge_nonneg(double a, double b) {   // a >= b, both >= +0
+    return __double_as_longlong(a) >= __double_as_longlong(b);
+}
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {   // a > b, both >= +0
+    return __double_as_longlong(a) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool le_zero(double a) { return __double_as_longlong(a) <= 0; }
+
 // Changeover weight K(r; rc): the rational form y^2/(2y^2-2y+1) or the
 // quintic 10y^3-15y^4+6y^5, y = (r - 0.1 rc)/(0.9 rc); 1 beyond rc, 0 below 0.1 rc.
 __device__ __forceinline__ double changeover(double r, double rc, int form) {
