@@ -684,12 +684,15 @@ opal_status capture_graph(opal_sim* s) {
 // Overlap (kick beside the encounter integrator, then patched) or in order.
 // The patch costs about 2 x bodies x big members involved pair terms against
 // the kick's bodies x big bodies, so the share that decides is that of the
-// big bodies (sources) in encounters.
+// big bodies (sources) in encounters.  The FP64 form always runs in order:
+// its kick is bound by the FP64 pipes the encounter integrator needs, and
+// beside it both slow down by more than the encounter integrator takes alone.
 opal_status choose_mode(opal_sim* s) {
     const double share = s->n_big > 0 ? (double)s->last_inv_big / (double)s->n_big : 0.0;
     int want = s->d.overlap;
     if (share < 0.03) want = 1;
     else if (share > 0.08) want = 0;
+    if (s->d.p.precision == 0) want = 0;
     if (want == s->d.overlap && s->exec) return OPAL_OK;
     s->d.overlap = want;
     return capture_graph(s);
