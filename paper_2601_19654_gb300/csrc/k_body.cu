@@ -344,35 +344,42 @@ __global__ void k_finish(Dev d) {
     }
 }
 
-// get_state: heliocentric velocities v = V + P / M0, one block per system
-__global__ void k_export(Dev d, double* vh) {
-    const SysInfo si = d.sys[blockIdx.x];
-    __shared__ double red[3][256];
-    double sx = 0, sy = 0, sz = 0;
-    for (int64_t k = threadIdx.x; k < si.cap; k += blockDim.x) {
-        int64_t b = si.off + k;
-        if (!d.alive[b]) continue;
-        sx += d.m[b] * d.vx[b];
-        sy += d.m[b] * d.vy[b];
-        sz += d.m[b] * d.vz[b];
+// get_state of system s, first pass: its momentum sum m V over the live
+// bodies, by fixed-order segments (the step's closing-jump partials are free
+// between steps), the total written by the system's last block.
+__global__ void __launch_bounds__(kBodyThreads) k_export_sum(Dev d, int s, double* P, int* counter) {
+    const SysInfo si = d.sys[s];
+    const int64_t first = si.off + (int64_t)blockIdx.x * kBodyThreads;
+    const int64_t b = first + threadIdx.x;
+    double px = 0.0, py = 0.0, pz = 0.0;
+    if (d.alive[b]) {
+        const double m = d.m[b];
+        px = m * d.vx[b];
+        py = m * d.vy[b];
+        pz = m * d.vz[b];
     }
-    red[0][threadIdx.x] = sx;
-    red[1][threadIdx.x] = sy;
-    red[2][threadIdx.x] = sz;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w >= 1; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int c = 0; c < 3; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
-        __syncthreads();
-    }
-    const double M0 = d.M0s[blockIdx.x];
-    double cx = red[0][0] / M0, cy = red[1][0] / M0, cz = red[2][0] / M0;
-    for (int64_t k = threadIdx.x; k < si.cap; k += blockDim.x) {
-        int64_t b = si.off + k;
-        vh[3 * b] = d.vx[b] + cx;
-        vh[3 * b + 1] = d.vy[b] + cy;
-        vh[3 * b + 2] = d.vz[b] + cz;
-    }
+    segment_sums(d, first, px, py, pz, d.pP_close);
+    system_total(d, d.pP_close, si, s, counter, P);
+}
+
+// second pass: one record a body for the host, (x, y, z, heliocentric v =
+// V + P / M0, m, R), and its live flag
+__global__ void __launch_bounds__(kBodyThreads) k_export_write(Dev d, int s, const double* P, double* rec,
+                                                               int* alive) {
+    const SysInfo si = d.sys[s];
+    const int64_t k = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
+    const int64_t b = si.off + k;
+    const double M0 = d.M0s[s];
+    double* r = rec + 8 * k;
+    r[0] = d.x[b];
+    r[1] = d.y[b];
+    r[2] = d.z[b];
+    r[3] = d.vx[b] + P[0] / M0;
+    r[4] = d.vy[b] + P[1] / M0;
+    r[5] = d.vz[b] + P[2] / M0;
+    r[6] = d.m[b];
+    r[7] = d.R[b];
+    alive[k] = d.alive[b];
 }
 
 // ---------------------------------------------------------------------------
@@ -589,6 +596,11 @@ void launch_finish(const Dev& d, cudaStream_t s) {
     k_finish<<<152, 256, 0, s>>>(d);
     prof_mark("finish");
 }
-void launch_export(const Dev& d, double* v_helio, cudaStream_t s) { k_export<<<d.nsys, 256, 0, s>>>(d, v_helio); }
+void launch_export(const Dev& d, int sys, int64_t cap, double* P, int* counter, double* rec, int* alive,
+                   cudaStream_t s) {
+    const unsigned nb = (unsigned)(cap / kBodyThreads);
+    k_export_sum<<<nb, kBodyThreads, 0, s>>>(d, sys, P, counter);
+    k_export_write<<<nb, kBodyThreads, 0, s>>>(d, sys, P, rec, alive);
+}
 
 }  // namespace opal

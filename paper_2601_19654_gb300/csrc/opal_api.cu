@@ -92,7 +92,12 @@ struct opal_sim {
     int64_t last_inv_big = 0;                // of them big bodies (sources of force)
     int64_t n_big = 0;                       // big bodies of all systems
     cudaEvent_t kick_ev[2] = {nullptr, nullptr};
-    double* d_vh = nullptr;        // heliocentric velocities for get_state
+    double* d_rec = nullptr;       // get_state: one record of 8 doubles a body, the largest system
+    int* d_ralive = nullptr;       // get_state: live flags
+    double* d_exP = nullptr;       // get_state: the system's momentum
+    int* d_excnt = nullptr;        // get_state: blocks done with their segments, a system
+    double* h_rec = nullptr;       // pinned host copies of the two (allocated at the first get_state)
+    int* h_ralive = nullptr;
     double* d_en_body = nullptr;
     double* d_en_pair = nullptr;
     double* d_en_out = nullptr;
@@ -445,7 +450,14 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &s->d_items, max_items));
     TRYF(dalloc(s, &s->d_tiles, s->tiles.size()));
     TRYF(dalloc(s, &s->d_tile_off, s->tile_off.size()));
-    TRYF(dalloc(s, &s->d_vh, 3 * N));
+    {
+        int64_t maxcap = 0;
+        for (auto& si : s->sys) maxcap = std::max(maxcap, si.cap);
+        TRYF(dalloc(s, &s->d_rec, 8 * maxcap));
+        TRYF(dalloc(s, &s->d_ralive, maxcap));
+        TRYF(dalloc(s, &s->d_exP, 3));
+        TRYF(dalloc(s, &s->d_excnt, nsys));
+    }
     TRYF(dalloc(s, &s->d_en_body, 7 * (N / 128)));
     TRYF(dalloc(s, &s->d_en_pair, s->tiles.size()));
     TRYF(dalloc(s, &s->d_en_out, 8 * nsys));
@@ -783,26 +795,27 @@ opal_status opal_get_state(const opal_sim* cs, int32_t sys, int64_t* n_alive, in
     if (sys < 0 || sys >= s->d.nsys) return set_err(s->err, "no system %d", sys), OPAL_EINVAL;
     const SysInfo si = s->sys[sys];
     const int64_t n = si.n;
-    launch_export(s->d, s->d_vh, s->stream);
+    if (!s->h_rec) {   // pinned staging for the largest system, kept until destroy
+        int64_t maxcap = 0;
+        for (auto& q : s->sys) maxcap = std::max(maxcap, q.cap);
+        CK(cudaHostAlloc(reinterpret_cast<void**>(&s->h_rec), std::max<int64_t>(1, 8 * maxcap) * 8, 0));
+        CK(cudaHostAlloc(reinterpret_cast<void**>(&s->h_ralive), std::max<int64_t>(1, maxcap) * 4, 0));
+    }
+    CK(cudaMemsetAsync(s->d_excnt, 0, s->d.nsys * sizeof(int), s->stream));
+    launch_export(s->d, sys, si.cap, s->d_exP, s->d_excnt, s->d_rec, s->d_ralive, s->stream);
     CK(cudaGetLastError());
-    std::vector<double> hx(n), hy(n), hz(n), hm(n), hR(n), hv(3 * n);
-    std::vector<int32_t> ha(n);
-    auto dn = [&](void* dst, const void* src, size_t bytes) {
-        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream);
-    };
-    CK(dn(hx.data(), s->d.x + si.off, n * 8)); CK(dn(hy.data(), s->d.y + si.off, n * 8));
-    CK(dn(hz.data(), s->d.z + si.off, n * 8)); CK(dn(hm.data(), s->d.m + si.off, n * 8));
-    CK(dn(hR.data(), s->d.R + si.off, n * 8)); CK(dn(ha.data(), s->d.alive + si.off, n * 4));
-    CK(dn(hv.data(), s->d_vh + 3 * si.off, 3 * n * 8));
+    CK(cudaMemcpyAsync(s->h_rec, s->d_rec, n * 8 * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(s->h_ralive, s->d_ralive, n * 4, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     int64_t k = 0;
     for (int64_t i = 0; i < n; i++) {
-        if (!ha[i]) continue;
+        if (!s->h_ralive[i]) continue;
+        const double* r = s->h_rec + 8 * i;
         if (ids) ids[k] = i;
-        if (m) m[k] = hm[i];
-        if (radius) radius[k] = hR[i];
-        if (x) { x[3 * k] = hx[i]; x[3 * k + 1] = hy[i]; x[3 * k + 2] = hz[i]; }
-        if (v) { v[3 * k] = hv[3 * i]; v[3 * k + 1] = hv[3 * i + 1]; v[3 * k + 2] = hv[3 * i + 2]; }
+        if (m) m[k] = r[6];
+        if (radius) radius[k] = r[7];
+        if (x) { x[3 * k] = r[0]; x[3 * k + 1] = r[1]; x[3 * k + 2] = r[2]; }
+        if (v) { v[3 * k] = r[3]; v[3 * k + 1] = r[4]; v[3 * k + 2] = r[5]; }
         k++;
     }
     if (n_alive) *n_alive = k;
@@ -947,6 +960,8 @@ void opal_destroy(opal_sim* s) {
     for (auto e : s->kick_ev)
         if (e) cudaEventDestroy(e);
     for (void* p : s->allocs) cudaFree(p);
+    if (s->h_rec) cudaFreeHost(s->h_rec);
+    if (s->h_ralive) cudaFreeHost(s->h_ralive);
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->side) cudaStreamDestroy(s->side);
     if (s->fork_ev) cudaEventDestroy(s->fork_ev);

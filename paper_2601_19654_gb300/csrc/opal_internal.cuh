@@ -572,7 +572,11 @@ void set_thread_error(const char* fmt, ...);
 
 void launch_energy(const Dev& d, const PairTile* tiles, int64_t ntiles, const int64_t* tile_off,
                    double* pair_part, double* body_part, double* out, int grid, cudaStream_t s);
-void launch_export(const Dev& d, double* v_helio, cudaStream_t s);
+// get_state of system sys (cap bodies): records (x, y, z, heliocentric v, m, R)
+// and live flags, one a body, into rec and alive; P: 3 doubles of scratch
+// (counter: nsys ints, zero on entry)
+void launch_export(const Dev& d, int sys, int64_t cap, double* P, int* counter, double* rec, int* alive,
+                   cudaStream_t s);
 void launch_debug_drift(int n, double mu, double dt, int max_iter, double* x, double* v, int* iters, cudaStream_t s);
 void launch_debug_scan_prep(const Dev& d, cudaStream_t s);
 
