@@ -370,7 +370,15 @@ def run_ours(args, rank, world, local):
     sim64.close()
     ms64 = max_over_ranks(float(np.mean(s64)), world)
 
+    # measured ALU peaks of this device (FP32 and FP64 FMA chains, MUFU rsqrt),
+    # beside the nominal FP32 peak
+    try:
+        alu = opal.probe_alu_peaks()
+    except opal.OpalError:
+        alu = None
+
     kick_avg = float(np.mean(kick_ms))
+    kick64_avg = float(np.mean(k64))
     flops = FLOPS_PER_INTERACTION * pairs
     peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / (kick_avg * 1e-3) / 1e12
@@ -386,8 +394,10 @@ def run_ours(args, rank, world, local):
         "dE_over_E": {"mixed": dE_mixed, "fp64": dE_fp64,
                       "over_steps": {"mixed": args.warmup + args.steps, "fp64": 3 + args.fp64_steps}},
         "fp64": {"value": world * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
-                 "interactions_per_s": world * 1e3 / ms64 * pairs, "kick_ms": float(np.mean(k64)),
-                 "steps": args.fp64_steps},
+                 "interactions_per_s": world * 1e3 / ms64 * pairs, "kick_ms": kick64_avg,
+                 "steps": args.fp64_steps, "kick_fp64_tflops": flops / (kick64_avg * 1e-3) / 1e12,
+                 "kick_frac_of_measured_fp64": (flops / (kick64_avg * 1e-3) / 1e12 / alu["fp64_tflops"]
+                                                if alu else None)},
         "mixed_over_fp64": ms64 / ms_per_step,
         "encounters_last_step": last,
         "roofline": {"bound": "alu", "kernel": "kick (mixed)", "achieved": achieved, "peak": peak,
@@ -397,7 +407,9 @@ def run_ours(args, rank, world, local):
                              "peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (of nominal max clock); the "
                              "kick is timed inside the step graph, where it runs beside the encounter "
                              "integrator and shares the SMs with it",
-                     "kick_ms": kick_avg, "kick_share_of_step": kick_avg / float(np.mean(step_ms))},
+                     "kick_ms": kick_avg, "kick_share_of_step": kick_avg / float(np.mean(step_ms)),
+                     "measured_alu_peaks": alu,
+                     "frac_of_measured_fp32": achieved / alu["fp32_tflops"] if alu else None},
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clocks,
     }

@@ -53,6 +53,14 @@ opal_status opal_debug_bs_group(opal_sim* sim, const double* x0, const double* V
                                 double* V, double* m, double* radius, int32_t* alive, double* E_lost,
                                 int64_t* substeps);
 
+/* Measured ALU peaks of the current device, for rooflines: out[0] FP32 FMA
+ * TFLOP/s (an FMA counts 2), out[1] FP64 FMA TFLOP/s, out[2] MUFU reciprocal
+ * square roots, Tops/s.  Independent FMA (or rsqrt) chains on every SM, a few
+ * milliseconds each, timed with CUDA events on the default stream after one
+ * warm-up launch.  Needs no simulation; allocates 64 bytes of device memory
+ * for the call.  OPAL_EINVAL for a NULL out, OPAL_ECUDA if a launch fails. */
+opal_status opal_probe_alu_peaks(double out[3]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libopal_gb300.so")
-SOURCES = ["k_body.cu", "k_kick.cu", "k_scan.cu", "k_bs.cu", "k_bs_huge.cu", "k_energy.cu", "opal_api.cu"]
+SOURCES = ["k_body.cu", "k_kick.cu", "k_scan.cu", "k_bs.cu", "k_bs_huge.cu", "k_energy.cu", "k_peaks.cu", "opal_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-diag-suppress", "1444"]
 

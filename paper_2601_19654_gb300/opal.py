@@ -81,7 +81,8 @@ def _declare(L):
     L.opal_debug_bs_group.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, _I32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]
     L.opal_energy_momentum_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, _P, _P, _P, _P, _P]
-    for name in ("opal_create", "opal_ensemble_create", "opal_step", "opal_step_async", "opal_wait", "opal_get_state", "opal_energy_momentum",
+    L.opal_probe_alu_peaks.argtypes = [_D]
+    for name in ("opal_probe_alu_peaks", "opal_create", "opal_ensemble_create", "opal_step", "opal_step_async", "opal_wait", "opal_get_state", "opal_energy_momentum",
                  "opal_last_step_stats", "opal_profile_steps", "opal_debug_accel", "opal_debug_drift",
                  "opal_debug_scan", "opal_debug_bs_group", "opal_energy_momentum_noalloc", "opal_central_mass"):
         getattr(L, name).restype = C.c_int
@@ -114,6 +115,14 @@ def energy_momentum_noalloc(n: int, G: float, M0: float, m_ptr: int, x_ptr: int,
     of one system into out_ptr[7], enqueued on stream; nothing is allocated."""
     _check(lib().opal_energy_momentum_noalloc(int(n), float(G), float(M0), m_ptr, x_ptr, v_ptr, out_ptr,
                                               stream or None))
+
+
+def probe_alu_peaks() -> dict:
+    """opal_probe_alu_peaks: measured FP32 and FP64 FMA TFLOP/s and MUFU rsqrt
+    Tops/s of the current device."""
+    out = np.zeros(3)
+    _check(lib().opal_probe_alu_peaks(out))
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "mufu_rsqrt_tops": float(out[2])}
 
 
 def default_params(**kw) -> Params:
