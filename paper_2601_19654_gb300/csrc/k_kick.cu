@@ -729,6 +729,7 @@ int kick_block_regs(int precision, int v) {
     return k.threads * ((k.regs() + 7) / 8 * 8);
 }
 int kick_occupancy(int precision, int v) { return precision == 1 ? kMixed[v].occupancy() : kFp64[v].occupancy(); }
+int kick_threads(int precision, int v) { return precision == 1 ? kMixed[v].threads : kFp64[v].threads; }
 void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int v,
                  cudaStream_t s) {
     if (precision == 1) kMixed[v].launch(d, items, nitems, grid, s);

@@ -562,6 +562,7 @@ int kick_num_variants(int precision);
 const char* kick_variant_name(int precision, int variant);
 int kick_occupancy(int precision, int variant);
 int kick_block_regs(int precision, int variant);   // registers one block of variant v holds
+int kick_threads(int precision, int variant);      // threads a block of variant v
 int bs_block_regs();
 int kick_itile(int precision, int variant);   // i-bodies per work item (a divisor of kPad)
 void launch_close(const Dev& d, cudaStream_t s);
