@@ -325,6 +325,32 @@ def test_ensemble_matches_each_system(opal):
             assert relpos(st["x"], osim.x[osim.alive > 0]) <= 1e-12
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_ensemble_on_a_sample_of_systems(opal, precision):
+    """The benchmark's 256-system ensemble (N log-uniform in 64-4096, about
+    32000 encounter groups a step), stepped as one simulation in its
+    benchmark launch configuration; the smallest, the largest and four
+    seeded-random systems against the oracle after two steps."""
+    systems = ic.ensemble(0, 256)
+    ns = np.array([s.n for s in systems])
+    pick = [int(np.argmin(ns)), int(np.argmax(ns))] + [int(k) for k in
+                                                        np.random.default_rng(1).choice(256, 4, replace=False)]
+    # FP64: 1e-9, as for the other many-group cases (an accept decision of the
+    # packed path can sit within rounding of the tolerance); mixed: 1e-6
+    tol = 1e-9 if precision == 0 else 1e-6
+    with opal.Simulation.ensemble(systems, precision=precision) as sim:
+        sim.step(2)
+        assert sim.stats()["n_groups"] > 608            # the packed path takes part
+        for k in pick:
+            osim = oracle.Sim.from_system(systems[k], dt=systems[0].dt)
+            assert osim.step(2) == oracle.OK
+            st = sim.state(k)
+            alive = np.nonzero(osim.alive)[0]
+            assert st["ids"].tolist() == alive.tolist(), k
+            assert relpos(st["x"], osim.x[alive]) <= tol, (k, relpos(st["x"], osim.x[alive]))
+            assert np.allclose(st["m"], osim.m[alive], rtol=1e-15, atol=0), k
+
+
 @pytest.mark.parametrize("inflate", [1.0, 30.0])
 def test_many_groups_take_the_packed_path_and_match_the_oracle(opal, inflate):
     """More encounter groups in a step than the lockstep kernels take (608):
