@@ -123,6 +123,43 @@ def test_accel_mixed_matches_oracle(opal, name):
     assert np.median(err) <= 1e-6 and err.max() <= 1e-4, (np.median(err), err.max())
 
 
+def _accel_rows(s, rc, rows, form=0):
+    """The oracle's kick sum for the given bodies only: G sum_j m_j K(r_ij;
+    max(rc_i, rc_j)) (x_j - x_i) / r_ij^3, K from the oracle's changeover
+    (1 beyond rc_ij, so only the few pairs inside it call it)."""
+    out = np.empty((len(rows), 3))
+    for q, i in enumerate(rows):
+        d = s.x - s.x[i]
+        r = np.linalg.norm(d, axis=1)
+        r[i] = np.inf
+        rcij = np.maximum(rc, rc[i])
+        K = np.ones(s.n)
+        for j in np.nonzero(r < rcij)[0]:
+            K[j] = oracle.changeover(r[j], rcij[j], form)
+        w = s.m * K / r ** 3
+        out[q] = s.G * (w[:, None] * d).sum(axis=0)
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_encounter_heavy_accelerations_on_a_sample(opal, precision):
+    """The 131072-body encounter-heavy workload with Jupiter and Saturn: the
+    kick's accelerations (every work item, chunk and partial row of the full
+    launch) for 256 seeded-random bodies and the two giants."""
+    s = ic.encounter_heavy(0)
+    rc = oracle.hill_rcrit(s.M0, 3.0, s.m, s.x)
+    with opal.Simulation.from_system(s, precision=precision) as sim:
+        a = sim.debug_accel(rc)
+    rows = sorted(set(np.random.default_rng(7).choice(s.n, 256, replace=False).tolist()) |
+                  {int(np.argmax(s.m)), int(np.argsort(s.m)[-2])})
+    ao = _accel_rows(s, rc, rows)
+    err = _accel_err(a[rows], ao)
+    if precision == 0:
+        assert err.max() <= 1e-12, err.max()
+    else:
+        assert np.median(err) <= 1e-6 and err.max() <= 1e-4, (np.median(err), err.max())
+
+
 # ---------------------------------------------------------------- scan
 def _scan_compare(opal, s, dt, f_hill):
     x0, V0, x1, V1 = drifted(s, dt)
