@@ -63,6 +63,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-small", action="store_true", help="skip the small-body (planetesimal) workload")
     ap.add_argument("--small-steps", type=int, default=50)
     ap.add_argument("--no-removals", action="store_true", help="skip the star-collision / ejection run")
+    ap.add_argument("--no-heavy", action="store_true", help="skip the encounter-heavy 131072-body run")
+    ap.add_argument("--heavy-steps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args(argv)
 
@@ -285,6 +287,28 @@ def small_body_rates(seed: int, steps: int, warmup: int, flush):
             "timing": "CUDA events on the simulation's stream, L2 flushed before every step"}
 
 
+def heavy_rates(seed: int, steps: int, warmup: int, flush):
+    """The encounter-heavy stress workload: 131072 bodies of 1e-4 Earth
+    masses between 2 and 10 au with Jupiter and Saturn, radii inflated
+    tenfold, dt = 0.05 yr; mixed form, device-timed like the headline.  Its
+    steps are bound by the Bulirsch-Stoer of the giants' encounter groups
+    (hundreds to thousands of members, the whole-GPU kernel)."""
+    from paper_2601_19654_gb300 import opal
+    system = ic.encounter_heavy(seed)
+    n = system.n
+    sim = opal.Simulation.from_system(system, precision=1)
+    E0 = sim.energy()[0]
+    step_ms, kick_ms = time_steps(sim, steps, warmup, flush)
+    dE = abs(sim.energy()[0] - E0) / abs(E0)
+    st = sim.stats()
+    sim.close()
+    ms = float(np.mean(step_ms))
+    return {"workload": system.name, "bodies": n, "steps": steps, "warmup": warmup, "steps_per_s": 1e3 / ms,
+            "ms_per_step": ms, "interactions_per_s": n * (n - 1) * 1e3 / ms, "kick_ms": float(np.mean(kick_ms)),
+            "dE_over_E": dE, "encounters_last_step": st,
+            "timing": "CUDA events on the simulation's stream, L2 flushed before every step"}
+
+
 def oracle_rate(system, seconds: float, max_steps: int | None = None):
     import oracle
     oracle.build()
@@ -419,6 +443,8 @@ def run_ours(args, rank, world, local):
             line["ensemble"] = ensemble_rates(args.seed, args.ensemble_steps, 3)
         if not args.no_small:
             line["small_bodies"] = small_body_rates(args.seed, args.small_steps, 5, flush)
+        if not args.no_heavy:
+            line["encounter_heavy"] = heavy_rates(args.seed, args.heavy_steps, 1, flush)
         if not args.no_removals:
             line["removals"] = removal_rates(system, min(args.steps, 100), 5, flush, ms_per_step)
         if not args.no_cpu_baseline:
