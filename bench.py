@@ -10,8 +10,10 @@ Bulirsch-Stoer of the flagged groups, jump, kick.
 Prints one JSON line.  `value` is the mixed form's steps/s summed over
 ranks (each rank advances its own replica: independent systems, no
 collective on the data path); the FP64 form, interactions/s, |dE/E|, the
-kick's roofline, the end-to-end rate through the C ABI with host buffers,
-clocks and the oracle's CPU rate are reported beside it.
+kick's roofline (against the nominal FP32 peak and the device's measured
+ALU peaks), the end-to-end rate through the C ABI with host buffers, the
+256-system ensemble, the small-body, removal and encounter-heavy
+workloads, clocks and the oracle's CPU rate are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
