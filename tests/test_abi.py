@@ -87,6 +87,28 @@ def test_empty_system_is_rejected(lib):
     assert e.value.status == lib.EINVAL
 
 
+@pytest.mark.parametrize("nps,needle", [
+    ([2, -1], "n ="),
+    ([], "at least one system"),
+])
+def test_bad_ensemble_layouts_are_rejected(lib, nps, needle):
+    m, x, v, R = _bodies(2)
+    with pytest.raises(lib.OpalError) as e:
+        lib.Simulation(m, x, v, R, n_per_sys=nps)
+    assert e.value.status == lib.EINVAL
+    assert needle in str(e.value)
+
+
+def test_small_before_big_in_a_later_system_is_rejected(lib):
+    """The big-first order holds within each system: the second system may
+    not put a big body after its own small one."""
+    m, x, v, R = _bodies(4)
+    m[:] = [1e-6, 0.0, 0.0, 1e-6]                 # system 1 = bodies 2, 3: small then big
+    with pytest.raises(lib.OpalError) as e:
+        lib.Simulation(m, x, v, R, n_per_sys=[2, 2])
+    assert e.value.status == lib.EINVAL and "follows a small" in str(e.value)
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     """With no built library there is no fallback: loading raises."""
     import importlib
