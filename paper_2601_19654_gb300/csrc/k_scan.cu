@@ -381,40 +381,78 @@ __device__ __forceinline__ double dot3p(const double* a, const double* b) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+// The same path in FP32 for the root search: relative position and its
+// first and second s-derivatives (T u folded into the tangents).
+__device__ __forceinline__ void hermite_rel_f(float s, const float* d0, const float* tu0, const float* d1,
+                                              const float* tu1, float* dd, float* dp, float* d2) {
+    const float s2 = s * s, s3 = s2 * s;
+    const float h00 = 2.0f * s3 - 3.0f * s2 + 1.0f, h10 = s3 - 2.0f * s2 + s;
+    const float h01 = -2.0f * s3 + 3.0f * s2, h11 = s3 - s2;
+    const float p00 = 6.0f * s2 - 6.0f * s, p10 = 3.0f * s2 - 4.0f * s + 1.0f;
+    const float p01 = -6.0f * s2 + 6.0f * s, p11 = 3.0f * s2 - 2.0f * s;
+    const float q00 = 12.0f * s - 6.0f, q10 = 6.0f * s - 4.0f, q01 = -12.0f * s + 6.0f, q11 = 6.0f * s - 2.0f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        dd[k] = h00 * d0[k] + h10 * tu0[k] + h01 * d1[k] + h11 * tu1[k];
+        dp[k] = p00 * d0[k] + p10 * tu0[k] + p01 * d1[k] + p11 * tu1[k];
+        d2[k] = q00 * d0[k] + q10 * tu0[k] + q01 * d1[k] + q11 * tu1[k];
+    }
+}
+
 // Stage 3, 16 lanes per candidate pair: lane k looks at interval k of the
-// 16, evaluating d.d' at its two ends exactly as the sequential scan does,
-// and refines its bracket when the sign changes from - to +; the minimum over
-// the ends and the lanes' interior minima is the sequential result (a
-// minimum does not depend on the order its terms are visited in).  Newton
-// starts from the secant point rather than the middle of the interval: the
-// iteration reaches the same root of g (to its 1e-12 stopping step), where
-// |d|^2 is flat, so the minimum agrees to rounding.
+// 16, and where g = d.d' changes sign from - to + on it, finds the root of g
+// (the minimum of |d|^2) by Newton from the secant point, kept inside the
+// bracket by bisection.  The bracket tests and the root search run in FP32
+// (one warp's FP64 instruction takes the FP64 unit for many cycles, and the
+// search is a long dependent chain).  At the root found, the path and its
+// derivatives are taken in FP64 with the oracle's arithmetic, and the minimum
+// is that of the local quadratic, |d|^2 - g^2 / g': a root off by ds leaves
+// an error of order ds^3, and an FP32 root is off by about 1e-7 (the minimum
+// then agrees with the oracle's to about 1e-13 relative, 1e-11 for near
+// head-on passes).  A sign of g that FP32 gets wrong at an interval's end
+// moves the bracket to the neighbouring interval, whose root is then that end.  The minimum over the lanes and the path's two ends is
+// the sequential result (a minimum does not depend on the order its terms
+// are visited in).
 __device__ double interval_min2(double T, int k, const double* d0, const double* u0, const double* d1,
                                 const double* u1) {
-    double dd[3], dp[3], d2[3];
-    hermite_rel(k / 16.0, T, d0, u0, d1, u1, dd, dp, d2);
-    const double ga = dot3p(dd, dp);
-    hermite_rel((k + 1) / 16.0, T, d0, u0, d1, u1, dd, dp, d2);
-    const double gb = dot3p(dd, dp);
-    if (!(ga < 0.0 && gb >= 0.0)) return HUGE_VAL;
-    // start at the secant root of g on the interval (close to the root, so
-    // Newton needs few steps); the minimum found is the same one
-    double lo = k / 16.0, hi = (k + 1) / 16.0;
-    double s = lo + (hi - lo) * (ga / (ga - gb));
-    if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
-    for (int it = 0; it < 60; it++) {
-        hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
-        double g = dot3p(dd, dp), gp = dot3p(dp, dp) + dot3p(dd, d2);
-        if (g < 0.0) lo = s;
-        else hi = s;
-        double sn = s - g / gp;
-        if (!(gp > 0.0 && sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
-        double step = sn - s;
-        s = sn;
-        if (fabs(step) <= 1e-12) break;
+    float f0[3], f1[3], tu0[3], tu1[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        f0[c] = (float)d0[c];
+        f1[c] = (float)d1[c];
+        tu0[c] = (float)(T * u0[c]);
+        tu1[c] = (float)(T * u1[c]);
     }
-    hermite_rel(s, T, d0, u0, d1, u1, dd, dp, d2);
-    return dot3p(dd, dd);
+    float dd[3], dp[3], d2[3];
+    const float lo0 = k / 16.0f, hi0 = (k + 1) / 16.0f;
+    hermite_rel_f(lo0, f0, tu0, f1, tu1, dd, dp, d2);
+    const float ga = dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2];
+    hermite_rel_f(hi0, f0, tu0, f1, tu1, dd, dp, d2);
+    const float gb = dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2];
+    if (!(ga < 0.0f && gb >= 0.0f)) return HUGE_VAL;
+    float lo = lo0, hi = hi0;
+    float s = lo + (hi - lo) * (ga / (ga - gb));
+    if (!(s > lo && s < hi)) s = 0.5f * (lo + hi);
+    for (int it = 0; it < 60; it++) {
+        hermite_rel_f(s, f0, tu0, f1, tu1, dd, dp, d2);
+        const float g = dd[0] * dp[0] + dd[1] * dp[1] + dd[2] * dp[2];
+        const float gp = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2] + dd[0] * d2[0] + dd[1] * d2[1] + dd[2] * d2[2];
+        if (g < 0.0f) lo = s;
+        else hi = s;
+        float sn = s - g / gp;
+        if (!(gp > 0.0f && sn > lo && sn < hi)) sn = 0.5f * (lo + hi);
+        const float step = sn - s;
+        s = sn;
+        if (fabsf(step) <= 1e-7f || hi - lo <= 2e-7f) break;
+    }
+    // FP64 at the root found: |d|^2 less g^2 / g', the minimum of the local
+    // quadratic (one Newton step's worth)
+    double ddd[3], dpd[3], d2d[3];
+    hermite_rel((double)s, T, d0, u0, d1, u1, ddd, dpd, d2d);
+    const double g = dot3p(ddd, dpd), gp = dot3p(dpd, dpd) + dot3p(ddd, d2d);
+    double D = dot3p(ddd, ddd);
+    if (gp > 0.0) D -= g * g / gp;
+    return fmax(D, 0.0);
 }
 
 __global__ void __launch_bounds__(256) k_confirm(Dev d) {
