@@ -425,8 +425,6 @@ __global__ void __launch_bounds__(256) k_kick_apply(Dev d) {
         d.undo[3 * k] = d.m[g];
         d.undo[3 * k + 1] = d.R[g];
         d.undo[3 * k + 2] = (double)d.alive[g];
-        d.okh[k] = d.kh[g];
-        d.okl[k] = d.kl[g];
         d.okx[k] = D4{d.x[g], d.y[g], d.z[g], d.m[g]};
         const double* o = d.bsout + (int64_t)kBsOut * k;
         if (o[8] < 0.0) {   // no encounter kernel wrote this member's result
@@ -448,7 +446,7 @@ __global__ void __launch_bounds__(256) k_kick_apply(Dev d) {
 constexpr int kFixThreads = kBodyThreads;
 
 __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_blocks) {
-    __shared__ float4 snh[kFixThreads], snl[kFixThreads], soh[kFixThreads], sol[kFixThreads];
+    __shared__ float4 snh[kFixThreads], snl[kFixThreads];
     __shared__ float snr[kFixThreads];
     __shared__ D4 snx[kFixThreads], sox[kFixThreads];
     __shared__ double snrd[kFixThreads];
@@ -484,8 +482,9 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
         const double xi = d.x[b], yi = d.y[b], zi = d.z[b], rcid = d.rc[b];
         const double td = 2.0 * (rcid + (double)rcm);
         const double thrd = fmax(td * td, 1e-300);
-        // mixed: the new-minus-old terms summed in float and folded into hi/lo
-        // pairs (FP64 arithmetic costs far more on this chip); FP64: in doubles
+        // mixed: the members' new terms (the kick left them out as sources)
+        // summed in float and folded into hi/lo pairs (FP64 arithmetic costs
+        // far more on this chip); FP64: new minus old terms, in doubles
         double cx = 0.0, cy = 0.0, cz = 0.0;
         float hx = 0.0f, hy = 0.0f, hz = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
         for (int kb = k0; kb < k1; kb += kFixThreads) {
@@ -510,8 +509,6 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
                     snh[slot] = d.kh[g];
                     snl[slot] = d.kl[g];
                     snr[slot] = d.rcf[g];
-                    soh[slot] = d.okh[k];
-                    sol[slot] = d.okl[k];
                 } else {
                     snx[slot] = D4{d.x[g], d.y[g], d.z[g], d.m[g]};
                     sox[slot] = d.okx[k];
@@ -521,13 +518,13 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
             __syncthreads();
             if (!want || n == 0) continue;
             if (mixed) {
+                // the kick left the members out as sources: their new terms only
                 float tx = 0.0f, ty = 0.0f, tz = 0.0f;
                 for (int q = 0; q < n; q++) {
                     const float3 tn = term_f(hi, li, rci, thrf, snh[q], snl[q], snr[q], form);
-                    const float3 to = term_f(hi, li, rci, thrf, soh[q], sol[q], snr[q], form);
-                    tx += tn.x - to.x;
-                    ty += tn.y - to.y;
-                    tz += tn.z - to.z;
+                    tx += tn.x;
+                    ty += tn.y;
+                    tz += tn.z;
                 }
                 fold(hx, lx, tx);
                 fold(hy, ly, ty);

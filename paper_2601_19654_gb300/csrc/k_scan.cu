@@ -647,6 +647,10 @@ __global__ void __launch_bounds__(kBodyThreads) k_group_place(Dev d) {
         // the count goes back to zero as the range fills, ready for the next step
         const int pos = d.gofs[r] + atomicSub(&d.gcount[r], 1) - 1;
         d.members[pos] = (int)b;
+        // the mixed kick beside the encounter integrator leaves the members
+        // out as sources (mass 0 in its float copy; k_kick_apply writes the
+        // new copy with the mass), so the fix-up adds their new terms only
+        if (d.overlap && d.p.precision == 1) d.kh[b].w = 0.0f;
     }
     // big members counted (the cost of patching the kick after the encounters)
     const SysInfo& si = d.sys[d.body_sys[(int64_t)blockIdx.x * kBodyThreads]];

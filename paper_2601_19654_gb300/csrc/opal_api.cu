@@ -421,8 +421,6 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     {
         const int64_t mcap = std::min<int64_t>(2 * d.flag_cap + 2, N + 2);   // members are distinct bodies
         TRYF(dalloc(s, &d.bsout, kBsOut * mcap));
-        TRYF(dalloc(s, &d.okh, mcap));
-        TRYF(dalloc(s, &d.okl, mcap));
         TRYF(dalloc(s, &d.okx, mcap));
     }
     TRYF(dalloc(s, &d.gcount, N));

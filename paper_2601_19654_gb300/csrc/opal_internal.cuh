@@ -208,8 +208,6 @@ struct Dev {
     double* glost;                      // per group energy lost to mergers
     double* undo;                       // per member slot: m, R, alive (3 doubles)
     double* bsout;                      // per member slot: the BS result (kBsOut doubles)
-    float4* okh;                        // per member slot: kh before the BS result was applied
-    float4* okl;                        // per member slot: kl before it
     D4* okx;                            // per member slot: x, y, z, m before it
     int* mlo;                           // [nsys] first member slot of the system (or a large value)
     int* mhi;                           // [nsys] one past its last member slot (or 0)
