@@ -42,7 +42,7 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("M0", C.c_double), ("dt", C.c_double),
                 ("rcrit_hill", C.c_double), ("bs_tol", C.c_double),
                 ("changeover", C.c_int32), ("kepler_max_iter", C.c_int32),
-                ("bs_max_substeps", C.c_int32), ("pad", C.c_int32),
+                ("bs_max_substeps", C.c_int32), ("scan_prune", C.c_int32),
                 ("r_star", C.c_double), ("r_eject", C.c_double), ("eject_every", C.c_int64),
                 ("steps_done", C.c_int64)]
 
@@ -77,7 +77,7 @@ def lib():
             L.orc_drift_min_r.restype = C.c_double
             L.orc_min_sep2.argtypes = [C.c_double, _D, _D, _D, _D]
             L.orc_min_sep2.restype = C.c_double
-            L.orc_scan.argtypes = [_i64, C.c_double, _D, _D, _D, _D, _D, _I, C.c_void_p, _i64, _I, _I,
+            L.orc_scan.argtypes = [_i64, C.c_double, _D, _D, _D, _D, _D, _I, C.c_void_p, C.c_int32, _i64, _I, _I,
                                    C.POINTER(C.c_int64)]
             L.orc_scan.restype = C.c_int64
             L.orc_groups.argtypes = [_i64, _i64, _I, _I, _I]
@@ -106,8 +106,12 @@ def _alive(n, alive=None):
 
 
 def make_params(G=1.0, M0=1.0, dt=0.01 * 2 * np.pi, rcrit_hill=3.0, bs_tol=1e-12, changeover=0,
-                kepler_max_iter=0, bs_max_substeps=0, r_star=0.0, r_eject=0.0, eject_every=0) -> Params:
-    return Params(G, M0, dt, rcrit_hill, bs_tol, changeover, kepler_max_iter, bs_max_substeps, 0,
+                kepler_max_iter=0, bs_max_substeps=0, r_star=0.0, r_eject=0.0, eject_every=0,
+                scan_prune=0) -> Params:
+    """scan_prune=0: the encounter scan runs the exact test on every pair (the
+    plain definition); 1: it first skips the pairs the end-point bound rules
+    out (same flagged set, for systems too large for the all-pairs test)."""
+    return Params(G, M0, dt, rcrit_hill, bs_tol, changeover, kepler_max_iter, bs_max_substeps, int(scan_prune),
                   r_star, r_eject, eject_every, 0)
 
 
@@ -167,9 +171,10 @@ def min_sep2(dt, d0, u0, d1, u1):
     return lib().orc_min_sep2(dt, _d(d0), _d(u0), _d(d1), _d(u1))
 
 
-def scan(dt, x0, V0, x1, V1, rc, alive=None, m=None):
+def scan(dt, x0, V0, x1, V1, rc, alive=None, m=None, prune=0):
     """Flagged pairs; m (optional) marks the small bodies (m == 0), no two of
-    which are ever a pair.  Without m every body counts as big."""
+    which are ever a pair.  Without m every body counts as big.  prune=0 tests
+    every pair exactly; prune=1 skips the pairs the end-point bound rules out."""
     n = np.asarray(rc).size
     cap = max(16, 4 * n)
     mm = None if m is None else _d(m)
@@ -179,7 +184,8 @@ def scan(dt, x0, V0, x1, V1, rc, alive=None, m=None):
         nc = C.c_int64(0)
         cnt = lib().orc_scan(n, dt, _d(x0, (n, 3)), _d(V0, (n, 3)), _d(x1, (n, 3)), _d(V1, (n, 3)),
                              _d(rc), _alive(n, alive),
-                             None if mm is None else mm.ctypes.data_as(C.c_void_p), cap, pi, pj, C.byref(nc))
+                             None if mm is None else mm.ctypes.data_as(C.c_void_p), int(prune), cap, pi, pj,
+                             C.byref(nc))
         if cnt <= cap:
             return pi[:cnt].copy(), pj[:cnt].copy(), nc.value
         cap = int(cnt)
@@ -217,9 +223,9 @@ class Sim:
 
     def __init__(self, m, x, v_helio, R, G=1.0, M0=1.0, dt=0.01 * 2 * np.pi, rcrit_hill=3.0,
                  bs_tol=1e-12, changeover=0, kepler_max_iter=0, bs_max_substeps=0, r_star=0.0,
-                 r_eject=0.0, eject_every=0):
+                 r_eject=0.0, eject_every=0, scan_prune=0):
         self.p = make_params(G, M0, dt, rcrit_hill, bs_tol, changeover, kepler_max_iter,
-                             bs_max_substeps, r_star, r_eject, eject_every)
+                             bs_max_substeps, r_star, r_eject, eject_every, scan_prune)
         self.n = int(np.asarray(m).size)
         self.m = _d(m).copy()
         self.R = _d(R).copy()

@@ -143,10 +143,9 @@ void orc_accel(int64_t n, double G, int32_t form, const double* m, const double*
 /* Stumpff functions c_0..c_3 of the universal-variable Kepler solution used
  * by the drift (Sec. 3.1, third block; WHFast lineage).  c_k(z) is the series
  * sum_j (-z)^j / (k + 2j)!.  Arguments with |z| > 0.1 are first divided by 4
- * until small; c2 and c3 are summed there as ten nested terms (each term
- * multiplies by the reciprocal of (k+2j-1)(k+2j), an exact rational rounded
- * once), c0 = 1 - z c2 and c1 = 1 - z c3 follow from the series, and the
- * quartering is undone with the double-angle relations
+ * until small; each c_k is summed there as the series itself, ten terms
+ * nested from the innermost, c_k = (1 - z/((k+1)(k+2)) (1 - z/((k+3)(k+4)) (...))) / k!,
+ * and the quartering is undone with the double-angle relations
  *   c0(4z) = 2 c0^2 - 1,  c1(4z) = c0 c1,  c2(4z) = c1^2 / 2,
  *   c3(4z) = (c2 + c0 c3) / 4. */
 void orc_stumpff(double z, double c[4]) {
@@ -155,15 +154,12 @@ void orc_stumpff(double z, double c[4]) {
         z *= 0.25;
         nq++;
     }
-    double s2 = 1.0, s3 = 1.0;
-    for (int j = 10; j >= 1; j--) {
-        s2 = 1.0 - z * s2 * (1.0 / (double)((2 * j + 1) * (2 * j + 2)));
-        s3 = 1.0 - z * s3 * (1.0 / (double)((2 * j + 2) * (2 * j + 3)));
+    static const double fact[4] = {1.0, 1.0, 2.0, 6.0};
+    for (int k = 0; k < 4; k++) {
+        double s = 1.0;
+        for (int j = 10; j >= 1; j--) s = 1.0 - z * s / (double)((k + 2 * j - 1) * (k + 2 * j));
+        c[k] = s / fact[k];
     }
-    c[2] = s2 * 0.5;
-    c[3] = s3 * (1.0 / 6.0);
-    c[0] = 1.0 - z * c[2];
-    c[1] = 1.0 - z * c[3];
     for (; nq > 0; nq--) {
         c[3] = (c[2] + c[0] * c[3]) * 0.25;
         c[2] = c[1] * c[1] * 0.5;
@@ -310,57 +306,54 @@ double orc_drift_min_r(double mu, double dt, const double x0[3], const double V0
  * Reading: the relative path over the step is the cubic Hermite interpolant
  * of the relative position d and velocity u at its two ends,
  *   d(s) = h00 d0 + h10 T u0 + h01 d1 + h11 T u1,  s in [0, 1], T = dt,
- * and the result is min over s of |d(s)|^2: the two ends, and every local
- * minimum inside, found where g(s) = d(s).d'(s) changes sign from - to + on a
- * grid of 16 equal intervals and refined by Newton's method on g
- * (g' = |d'|^2 + d.d''), kept inside the sign-change bracket by bisection,
- * until a step is below 1e-12 (at most 60 iterations). */
-static void hermite_rel(double s, double T, const double* d0, const double* u0, const double* d1,
-                        const double* u1, double* d, double* dd, double* d2) {
-    double s2 = s * s, s3 = s2 * s;
-    double h00 = 2.0 * s3 - 3.0 * s2 + 1.0, h10 = s3 - 2.0 * s2 + s;
-    double h01 = -2.0 * s3 + 3.0 * s2, h11 = s3 - s2;
-    double p00 = 6.0 * s2 - 6.0 * s, p10 = 3.0 * s2 - 4.0 * s + 1.0;
-    double p01 = -6.0 * s2 + 6.0 * s, p11 = 3.0 * s2 - 2.0 * s;
-    double q00 = 12.0 * s - 6.0, q10 = 6.0 * s - 4.0, q01 = -12.0 * s + 6.0, q11 = 6.0 * s - 2.0;
-    for (int k = 0; k < 3; k++) {
-        d[k] = h00 * d0[k] + h10 * T * u0[k] + h01 * d1[k] + h11 * T * u1[k];
-        dd[k] = p00 * d0[k] + p10 * T * u0[k] + p01 * d1[k] + p11 * T * u1[k];
-        d2[k] = q00 * d0[k] + q10 * T * u0[k] + q01 * d1[k] + q11 * T * u1[k];
-    }
+ * written here in powers of s (collecting the basis polynomials
+ * h00 = 2s^3 - 3s^2 + 1, h10 = s^3 - 2s^2 + s, h01 = -2s^3 + 3s^2, h11 = s^3 - s^2):
+ *   d(s) = A + B s + C s^2 + D s^3,  A = d0,  B = T u0,
+ *   C = 3 (d1 - d0) - T (2 u0 + u1),  D = 2 (d0 - d1) + T (u0 + u1).
+ * The result is min over s of |d(s)|^2: the two ends, and every local minimum
+ * inside.  Those lie where g(s) = d.d' = (1/2) d|d|^2/ds, the quintic
+ *   g = A.B + (2 A.C + B.B) s + 3 (A.D + B.C) s^2 + (4 B.D + 2 C.C) s^3
+ *       + 5 C.D s^4 + 3 D.D s^5,
+ * changes sign from - to + ; the sign is read on a grid of 16 equal intervals
+ * and each such interval is halved 48 times (bisection: the root is then
+ * known to 2^-52 of the step). */
+static double poly_g(const double g[6], double s) {
+    return g[0] + s * (g[1] + s * (g[2] + s * (g[3] + s * (g[4] + s * g[5]))));
 }
 
 double orc_min_sep2(double T, const double d0[3], const double u0[3], const double d1[3],
                     const double u1[3]) {
-    double D = dot3(d0, d0), D1 = dot3(d1, d1);
-    if (D1 < D) D = D1;
-    double d[3], dd[3], d2[3];
-    hermite_rel(0.0, T, d0, u0, d1, u1, d, dd, d2);
-    double ga = dot3(d, dd);
+    double A[3], B[3], Cc[3], D[3];
+    for (int k = 0; k < 3; k++) {
+        A[k] = d0[k];
+        B[k] = T * u0[k];
+        Cc[k] = 3.0 * (d1[k] - d0[k]) - T * (2.0 * u0[k] + u1[k]);
+        D[k] = 2.0 * (d0[k] - d1[k]) + T * (u0[k] + u1[k]);
+    }
+    const double g[6] = {dot3(A, B), 2.0 * dot3(A, Cc) + dot3(B, B), 3.0 * (dot3(A, D) + dot3(B, Cc)),
+                         4.0 * dot3(B, D) + 2.0 * dot3(Cc, Cc), 5.0 * dot3(Cc, D), 3.0 * dot3(D, D)};
+    double Dmin = dot3(d0, d0), D1 = dot3(d1, d1);
+    if (D1 < Dmin) Dmin = D1;
+    double ga = poly_g(g, 0.0);
     for (int k = 0; k < 16; k++) {
-        double sa = k / 16.0, sb = (k + 1) / 16.0;
-        hermite_rel(sb, T, d0, u0, d1, u1, d, dd, d2);
-        double gb = dot3(d, dd);
+        const double sa = k / 16.0, sb = (k + 1) / 16.0;
+        const double gb = poly_g(g, sb);
         if (ga < 0.0 && gb >= 0.0) {
-            double lo = sa, hi = sb, s = 0.5 * (sa + sb);
-            for (int it = 0; it < 60; it++) {
-                hermite_rel(s, T, d0, u0, d1, u1, d, dd, d2);
-                double g = dot3(d, dd), gp = dot3(dd, dd) + dot3(d, d2);
-                if (g < 0.0) lo = s;
-                else hi = s;
-                double sn = s - g / gp;
-                if (!(gp > 0.0 && sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
-                double step = sn - s;
-                s = sn;
-                if (fabs(step) <= 1e-12) break;
+            double lo = sa, hi = sb;
+            for (int it = 0; it < 48; it++) {
+                const double mid = 0.5 * (lo + hi);
+                if (poly_g(g, mid) < 0.0) lo = mid;
+                else hi = mid;
             }
-            hermite_rel(s, T, d0, u0, d1, u1, d, dd, d2);
-            double Dm = dot3(d, d);
-            if (Dm < D) D = Dm;
+            const double s = 0.5 * (lo + hi);
+            double d[3];
+            for (int q = 0; q < 3; q++) d[q] = A[q] + s * (B[q] + s * (Cc[q] + s * D[q]));
+            const double Dm = dot3(d, d);
+            if (Dm < Dmin) Dmin = Dm;
         }
         ga = gb;
     }
-    return D;
+    return Dmin;
 }
 
 /* Close-encounter scan (Sec. 3.1, mce_snif LOOPs 1-3): for every pair i < j
@@ -371,35 +364,25 @@ double orc_min_sep2(double T, const double d0[3], const double u0[3], const doub
  * Two small bodies (m = 0 both; m may be NULL: no small bodies) are never a
  * pair: they do not interact (Sec. 2.1).
  *
- * Two exact bounds skip pairs that cannot be flagged (they only save time;
- * the flagged set is the one of the exact test):
- *  (1) each body's Hermite path p(s) stays within
- *      rho = |x1 - x0|/2 + (sqrt 3/18)|x0 - x1 + T V1| + (4/27 + 1/8)|T||V0 - V1|
- *      of its midpoint c = p(1/2) = (x0 + x1)/2 + T (V0 - V1)/8: p(s) minus the
- *      chord (1-s) x0 + s x1 is psi(s)(x0 - x1 + T V1) + h10(s) T (V0 - V1)
- *      with psi = s(2s-1)(s-1), |psi| <= sqrt 3/18, 0 <= h10 <= 4/27, the chord
- *      is within |x1 - x0|/2 of (x0 + x1)/2, and that is |T(V0 - V1)|/8 from c;
- *      so |d(s)| >= |c_j - c_i| - rho_i - rho_j;
- *  (2) d(s) - [(1 - s) d0 + s d1] = s(2s - 1)(s - 1)(d0 - d1) + h10 T u0 +
- *      h11 T u1, whose size is at most (sqrt 3 / 18)|d1 - d0| +
- *      (4/27)|T|(|u0| + |u1|) =: E; so |d(s)| >= dist(0, chord) - E.
- * Returns the number of flagged pairs (the first min(count, cap) are written). */
+ * prune = 0 runs the exact test on every pair.  prune = 1 first skips the
+ * pairs that one bound rules out; it only saves time, the flagged set is the
+ * exact test's (the tests check the two modes give the same set):
+ * during the drift dx/dt = V, and the interpolant of body i's own path
+ * p(s) = h00 x0 + h10 T V0 + h01 x1 + h11 T V1 satisfies
+ * p(s) - x1 = h00 (x0 - x1) + h10 T V0 + h11 T V1 (h00 + h01 = 1), with
+ * |h00| <= 1 and |h10|, |h11| <= 4/27 on [0, 1]; so p stays within
+ * rho = |x0 - x1| + (4/27)|T|(|V0| + |V1|) of x1, and
+ * |d(s)| >= |x1_j - x1_i| - rho_i - rho_j.
+ * Returns the number of flagged pairs (the first min(count, cap) are written);
+ * n_candidates gets the number of pairs given the exact test. */
 int64_t orc_scan(int64_t n, double T, const double* x0, const double* V0, const double* x1,
-                 const double* V1, const double* rc, const int32_t* alive, const double* m, int64_t cap,
-                 int32_t* pi, int32_t* pj, int64_t* n_candidates) {
+                 const double* V1, const double* rc, const int32_t* alive, const double* m, int32_t prune,
+                 int64_t cap, int32_t* pi, int32_t* pj, int64_t* n_candidates) {
     double* rho = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    double* cen = (double*)malloc(sizeof(double) * (size_t)(3 * n > 0 ? 3 * n : 1));
     for (int64_t i = 0; i < n; i++) {
-        double w[3], e[3], dv[3];
-        for (int k = 0; k < 3; k++) {
-            w[k] = x1[3 * i + k] - x0[3 * i + k];
-            e[k] = x0[3 * i + k] - x1[3 * i + k] + T * V1[3 * i + k];
-            dv[k] = V0[3 * i + k] - V1[3 * i + k];
-            cen[3 * i + k] = 0.5 * (x0[3 * i + k] + x1[3 * i + k]) + 0.125 * T * dv[k];
-        }
-        rho[i] = 0.5 * norm3(w) + (sqrt(3.0) / 18.0) * norm3(e) + (4.0 / 27.0 + 0.125) * fabs(T) * norm3(dv);
+        double w[3] = {x0[3 * i] - x1[3 * i], x0[3 * i + 1] - x1[3 * i + 1], x0[3 * i + 2] - x1[3 * i + 2]};
+        rho[i] = norm3(w) + (4.0 / 27.0) * fabs(T) * (norm3(V0 + 3 * i) + norm3(V1 + 3 * i));
     }
-    const double e_chord = sqrt(3.0) / 18.0;
     int64_t count = 0, ncand = 0;
     for (int64_t i = 0; i < n; i++) {
         if (!alive[i]) continue;
@@ -407,29 +390,17 @@ int64_t orc_scan(int64_t n, double T, const double* x0, const double* V0, const 
             if (!alive[j]) continue;
             if (m && m[i] == 0.0 && m[j] == 0.0) continue; /* two small bodies */
             double rcij = rc[i] > rc[j] ? rc[i] : rc[j];
-            double d1[3], d0[3], u0[3], u1[3], dc[3];
-            for (int k = 0; k < 3; k++) {
-                d1[k] = x1[3 * j + k] - x1[3 * i + k];
-                dc[k] = cen[3 * j + k] - cen[3 * i + k];
-            }
-            double r1 = norm3(d1), rcen = norm3(dc);
-            if (rcen - rho[i] - rho[j] > rcij + 1e-12 * (rcen + rho[i] + rho[j])) continue; /* bound (1) */
+            double d0[3], u0[3], d1[3], u1[3];
             for (int k = 0; k < 3; k++) {
                 d0[k] = x0[3 * j + k] - x0[3 * i + k];
                 u0[k] = V0[3 * j + k] - V0[3 * i + k];
+                d1[k] = x1[3 * j + k] - x1[3 * i + k];
                 u1[k] = V1[3 * j + k] - V1[3 * i + k];
             }
-            double w[3] = {d1[0] - d0[0], d1[1] - d0[1], d1[2] - d0[2]};
-            double ww = dot3(w, w);
-            double t = 0.0;
-            if (ww > 0.0) {
-                t = -dot3(d0, w) / ww;
-                t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+            if (prune) {
+                double r1 = norm3(d1);
+                if (r1 - rho[i] - rho[j] > rcij + 1e-12 * (r1 + rho[i] + rho[j])) continue;
             }
-            double c[3] = {d0[0] + t * w[0], d0[1] + t * w[1], d0[2] + t * w[2]};
-            double E = e_chord * sqrt(ww) + (4.0 / 27.0) * fabs(T) * (norm3(u0) + norm3(u1));
-            double cd = norm3(c);
-            if (cd - E > rcij + 1e-12 * (norm3(d0) + r1 + E)) continue; /* bound (2) */
             ncand++;
             double D = orc_min_sep2(T, d0, u0, d1, u1);
             if (D <= rcij * rcij) {
@@ -442,7 +413,6 @@ int64_t orc_scan(int64_t n, double T, const double* x0, const double* V0, const 
         }
     }
     free(rho);
-    free(cen);
     if (n_candidates) *n_candidates = ncand;
     return count;
 }
@@ -642,10 +612,10 @@ int32_t orc_bs_group(const orc_params* p, int64_t nm, const int32_t* members, do
                 double* Tkj = Tb + (int64_t)(k * KMAX + j) * q;
                 double* Tkj1 = Tb + (int64_t)(k * KMAX + j - 1) * q;
                 double* Tpj1 = Tb + (int64_t)((k - 1) * KMAX + j - 1) * q;
-                /* 1 / ((n_k / n_{k-j})^2 - 1) as one rounding of an exact rational */
-                double inv = (double)((k - j + 1) * (k - j + 1)) /
-                             (double)((k + 1) * (k + 1) - (k - j + 1) * (k - j + 1));
-                for (int64_t i = 0; i < q; i++) Tkj[i] = Tkj1[i] + (Tkj1[i] - Tpj1[i]) * inv;
+                /* Neville's recurrence in h^2: T_kj = T_k,j-1 + (T_k,j-1 - T_k-1,j-1) / ((n_k / n_k-j)^2 - 1) */
+                double ratio = (double)(k + 1) / (double)(k - j + 1);
+                double den = ratio * ratio - 1.0;
+                for (int64_t i = 0; i < q; i++) Tkj[i] = Tkj1[i] + (Tkj1[i] - Tpj1[i]) / den;
             }
             if (k >= 1) {
                 double* Tkk = Tb + (int64_t)(k * KMAX + k) * q;
@@ -842,12 +812,12 @@ int32_t orc_step(orc_params* p, int64_t n, double* m, double* R, double* x, doub
         }
         if (status == ORC_OK) {
             orc_hill_rcrit(n, M0, p->rcrit_hill, m, x, alive, rc);
-            int64_t np = orc_scan(n, dt, x0, V0, x, V, rc, alive, m, cap, pi, pj, &s.n_candidates);
+            int64_t np = orc_scan(n, dt, x0, V0, x, V, rc, alive, m, p->scan_prune, cap, pi, pj, &s.n_candidates);
             if (np > cap) {
                 cap = np;
                 pi = realloc(pi, sizeof(int32_t) * (size_t)cap);
                 pj = realloc(pj, sizeof(int32_t) * (size_t)cap);
-                np = orc_scan(n, dt, x0, V0, x, V, rc, alive, m, cap, pi, pj, &s.n_candidates);
+                np = orc_scan(n, dt, x0, V0, x, V, rc, alive, m, p->scan_prune, cap, pi, pj, &s.n_candidates);
             }
             s.n_pairs = np;
             if (np > 0) {

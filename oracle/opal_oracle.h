@@ -31,7 +31,7 @@ typedef struct {
     int32_t changeover;     /* 0: rational y^2/(2y^2-2y+1); 1: quintic 10y^3-15y^4+6y^5 */
     int32_t kepler_max_iter;/* cap on universal-variable iterations (0: default 50) */
     int32_t bs_max_substeps;/* cap on BS substeps per group per step (0: default 1<<20) */
-    int32_t pad;
+    int32_t scan_prune;     /* 0: the exact test on every pair; 1: skip pairs a bound rules out first */
     double r_star;          /* radius of the star: a drift passing within it is accreted (0: off) */
     double r_eject;         /* ejection distance from the star (0: off) */
     int64_t eject_every;    /* steps between ejection checks (Sec. 2.1.2: every 200 yr) */
@@ -69,7 +69,7 @@ double orc_min_sep2(double dt, const double d0[3], const double u0[3], const dou
                     const double u1[3]);
 int64_t orc_scan(int64_t n, double dt, const double* x0, const double* V0, const double* x1,
                  const double* V1, const double* rc, const int32_t* alive, const double* m,
-                 int64_t cap, int32_t* pi, int32_t* pj, int64_t* n_candidates);
+                 int32_t prune, int64_t cap, int32_t* pi, int32_t* pj, int64_t* n_candidates);
 int64_t orc_groups(int64_t n, int64_t npairs, const int32_t* pi, const int32_t* pj,
                    int32_t* label);
 

@@ -12,8 +12,12 @@
 //   2. FP32, on the list of pairs that pass, one thread per pair: distance
 //      from the origin to the chord d0 -> d1 minus a bound on the path's
 //      deviation from the chord;
-//   3. FP64 exact minimum on the survivors, in the same arithmetic as the
-//      oracle (16 intervals, sign change of d.d', bracketed Newton).
+//   3. the minimum on the survivors: the sign of g = d.d' on 16 equal
+//      intervals and a bracketed Newton search for each - to + change, both
+//      in FP32, then the path, d' and d'' at the root found taken in FP64
+//      and the minimum there as the local quadratic's, |d|^2 - g^2 / g'
+//      (an FP32 root is off by ~1e-7 of the step, which leaves errors of
+//      order its square: the minimum agrees with an FP64 search to ~1e-13).
 // Stages 1-2 carry margins far above FP32 rounding, so they never drop a
 // pair stage 3 would flag; the flagged set is that of stage 3 alone.
 #include "opal_internal.cuh"

@@ -1,8 +1,8 @@
 """The closest-approach search of the encounter confirmation, restated in
 numpy in the precisions the kernel uses (bracket tests and Newton search in
 FP32, the path and its derivatives at the root in FP64, the minimum taken as
-the local quadratic's |d|^2 - g^2 / g'), against the oracle's FP64 Newton
-minimum: the two must agree far inside the 1e-9 relative band the GPU's and
+the local quadratic's |d|^2 - g^2 / g'), against the oracle's FP64
+minimum (bisection of g on the same 16 intervals): the two must agree far inside the 1e-9 relative band the GPU's and
 the oracle's flagged sets are compared at, also for near head-on passes
 whose minimum is tiny.  The GPU parity tests check the kernel itself; this
 pins the accuracy of the method it uses.

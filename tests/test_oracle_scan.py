@@ -112,6 +112,117 @@ def test_scan_flags_fast_flyby_caught_only_mid_step():
     assert len(pi) == 0
 
 
+def _drifted_system(s, dt):
+    V0 = oracle.helio_to_dh(s.M0, s.m, s.v)
+    x0 = s.x.copy()
+    x1, V1 = x0.copy(), V0.copy()
+    for i in range(s.n):
+        st, x1[i], V1[i], _ = oracle.kepler_drift(s.G * s.M0, dt, x0[i], V0[i])
+        assert st == oracle.OK
+    return x0, V0, x1, V1
+
+
+@pytest.mark.parametrize("kind,n,f_hill,dt_mult", [
+    ("planetesimals", 300, 3.0, 1.0), ("planetesimals", 1000, 3.0, 1.0), ("planetesimals", 2000, 3.0, 1.0),
+    ("planetesimals", 1000, 30.0, 4.0), ("disk", 2000, 3.0, 1.0), ("disk", 2000, 10.0, 1.0),
+    ("disk", 2000, 30.0, 3.0), ("disk", 1000, 60.0, -2.0)])
+def test_pruned_scan_equals_the_all_pairs_scan(kind, n, f_hill, dt_mult):
+    """The skip bound only saves time: on systems built like the 1000-
+    planetesimal and the equal-mass disk workloads (the disk at its own
+    surface density, in an annulus; drifted by the oracle's
+    own Kepler solver), with Hill factors and steps up to 30x and 4x the
+    workloads' (forward and backward), the pruned scan flags exactly the
+    pairs the exact test flags on every pair, while the bound removes almost
+    all of them."""
+    if kind == "planetesimals":
+        s = ic.planetesimals_jupiter(7, n=n)
+    else:
+        # a 0.3 au wide annulus of the 16384-body disk: its bodies at the
+        # workload's own surface density (about n of them)
+        s = ic.equal_mass_disk(7)
+        r = np.linalg.norm(s.x, axis=1)
+        keep = np.nonzero((r > 1.0) & (r < 1.3))[0][:n]
+        s = ic.System(s.name, s.m[keep], s.x[keep], s.v[keep], s.R[keep], dt=s.dt, nsteps=1)
+    dt = s.dt * dt_mult
+    x0, V0, x1, V1 = _drifted_system(s, dt)
+    rc = oracle.hill_rcrit(s.M0, f_hill, s.m, x1)
+    alive = np.ones(s.n, np.int32)
+    alive[::97] = 0
+    pi0, pj0, nc0 = oracle.scan(dt, x0, V0, x1, V1, rc, alive, prune=0)
+    pi1, pj1, nc1 = oracle.scan(dt, x0, V0, x1, V1, rc, alive, prune=1)
+    nlive = int(alive.sum())
+    assert nc0 == nlive * (nlive - 1) // 2                  # every live pair got the exact test
+    assert pi1.tolist() == pi0.tolist() and pj1.tolist() == pj0.tolist()
+    assert len(pi0) > 0
+    # the bound removes almost every pair at the workloads' parameters, and
+    # most of them in the stress cases
+    assert nc1 < (0.05 if (f_hill == 3.0 and dt_mult == 1.0) else 0.25) * nc0
+
+
+def test_pruned_scan_keeps_pairs_just_inside_the_bound():
+    """Pairs placed so that the minimum separation over the step sits just
+    inside and just outside the critical distance, around many random
+    directions and speeds: the pruned and the exact scans agree on each."""
+    rng = np.random.default_rng(5)
+    T = 0.0628
+    for _ in range(40):
+        n = 40
+        x0 = rng.normal(size=(n, 3)) * 0.05 + [1.0, 0.0, 0.0]
+        V0 = rng.normal(size=(n, 3)) * 0.3 + [0.0, 1.0, 0.0]
+        x1, V1 = x0.copy(), V0.copy()
+        for i in range(n):
+            st, x1[i], V1[i], _ = oracle.kepler_drift(1.0, T, x0[i], V0[i])
+            assert st == oracle.OK
+        rc = np.full(n, 0.0)
+        # each pair's critical distance set at its own minimum, scaled by 1 -/+ 1e-7:
+        # use one radius per body equal to the median minimum of its pairs
+        D = np.array([[oracle.min_sep2(T, x0[j] - x0[i], V0[j] - V0[i], x1[j] - x1[i], V1[j] - V1[i])
+                       if j != i else np.inf for j in range(n)] for i in range(n)])
+        rc = np.sqrt(np.median(np.where(np.isfinite(D), D, np.nan), axis=1, keepdims=False)) * rng.uniform(0.2, 0.6)
+        pi0, pj0, _ = oracle.scan(T, x0, V0, x1, V1, rc, prune=0)
+        pi1, pj1, _ = oracle.scan(T, x0, V0, x1, V1, rc, prune=1)
+        assert pi1.tolist() == pi0.tolist() and pj1.tolist() == pj0.tolist()
+
+
+def test_pruned_scan_on_paths_that_bulge_to_the_bound():
+    """The end-point bound is tight for paths that leave and come back within
+    the step.  With x1 = x0 and V1 = 0, body i's interpolated path is
+    x0 + T h10(s) V0, whose largest excursion is (4/27) T |V0| at s = 1/3, the
+    bound's own coefficient; with V1 = -V0 it is T |V0| / 4 at s = 1/2.  A
+    partner at rest just inside (or outside) the critical distance of that
+    apex, where the two end points are far apart, must be flagged (or not)
+    alike by the pruned and the exact scans, and the exact minimum is checked
+    against the apex distance."""
+    rng = np.random.default_rng(17)
+    T = 0.0628
+    for kind in ("third", "half"):
+        n = 80
+        x0 = np.zeros((n, 3))
+        V0 = np.zeros((n, 3))
+        V1 = np.zeros((n, 3))
+        rc = np.zeros(n)
+        expect = {}
+        for b in range(n // 2):
+            i, j = 2 * b, 2 * b + 1
+            x0[i] = rng.normal(size=3) * 3.0 + [20.0 * b, 0.0, 0.0]
+            u = rng.normal(size=3)
+            u /= np.linalg.norm(u)
+            speed = rng.uniform(0.5, 5.0)
+            V0[i] = speed * u
+            V1[i] = 0.0 if kind == "third" else -V0[i]
+            apex = (4.0 / 27.0 if kind == "third" else 0.25) * T * speed
+            rc[i] = rc[j] = rng.uniform(0.02, 0.2) * apex
+            inside = b % 2 == 0
+            x0[j] = x0[i] + u * (apex + rc[i] * (0.999 if inside else 1.001))
+            expect[(i, j)] = inside
+        x1 = x0.copy()
+        pi0, pj0, _ = oracle.scan(T, x0, V0, x1, V1, rc, prune=0)
+        pi1, pj1, _ = oracle.scan(T, x0, V0, x1, V1, rc, prune=1)
+        got = set(zip(pi0.tolist(), pj0.tolist()))
+        assert got == {p for p, f in expect.items() if f}, kind
+        assert pi1.tolist() == pi0.tolist() and pj1.tolist() == pj0.tolist(), kind
+
+
 def test_groups_are_connected_components():
     pi = np.array([0, 2, 5, 3, 7], np.int32)
     pj = np.array([4, 5, 9, 9, 8], np.int32)
