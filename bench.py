@@ -44,11 +44,13 @@ SM_MAX_MHZ = 2070.0
 # algorithmic FP32 flops of one pair interaction of the kick (FMA = 2):
 # 3 subtractions, r^2 (1 mul + 2 fma = 5), rsqrt (1), m r^-3 (3 mul), 3 fma (6)
 FLOPS_PER_INTERACTION = 18
-# DRAM bytes (read + written) of one launch of the kick variants the autotuner
-# picks on this workload, from ncu captures of the current kernel (the
-# summaries are committed beside the profiles); another variant reports none
-KICK_TRAFFIC = {"mixed t128 i1 r": 1.559552e6 + 0.71936e6, "mixed t128 i1": 3.064064e6 + 2.145792e6,
-               "mixed t128 i1 5": 1.570048e6 + 0.690944e6}
+# DRAM bytes (read + written) of one launch of the mixed kick, from the ncu
+# capture summarised in profiles/kick_mixed_disk16384.md (launch shape
+# "mixed t128 i1"); the other one-i-body shapes run the same code with
+# another register cap, so they move the same bytes.  Other shapes report none.
+_KICK_I1_TRAFFIC = 0.794624e6 + 0.0
+KICK_TRAFFIC = {"mixed t128 i1": _KICK_I1_TRAFFIC, "mixed t128 i1 6": _KICK_I1_TRAFFIC,
+                "mixed t128 i1 8": _KICK_I1_TRAFFIC}
 
 
 def parse_args(argv=None):
@@ -187,23 +189,27 @@ def time_steps(sim, steps: int, warmup: int, flush):
 
 def e2e_rate(system, steps: int, precision: int):
     """Steps/s through the public API with host buffers: create from host
-    arrays (host->device), then every step opal_step and opal_get_state
-    (device->host of ids, masses, positions, velocities, radii)."""
+    arrays (host->device, with the kick autotuning and the step graph's
+    capture), then every step opal_step and opal_get_state (device->host of
+    ids, masses, positions, velocities, radii).  The value covers create and
+    the steps; create's time and the per-step rate are reported beside it."""
     from paper_2601_19654_gb300 import opal
     n = system.n
     t0 = time.perf_counter()
     sim = opal.Simulation.from_system(system, precision=precision)
+    t1 = time.perf_counter()
     for _ in range(steps):
         sim.step(1)
         st = sim.state()
-    t1 = time.perf_counter()
+    t2 = time.perf_counter()
     sim.close()
     assert st["x"].shape[0] > 0
     h2d = n * 8 * (1 + 3 + 3 + 1)
     d2h = n * (8 + 8 + 24 + 24 + 8)
-    return {"value": steps / (t1 - t0), "unit": UNIT, "steps": steps, "h2d_bytes_per_step": h2d / steps,
-            "d2h_bytes_per_step": d2h, "note": "create (H2D, autotune, graph capture) inside the timed region, "
-                                              "amortised over the steps; state read back every step"}
+    return {"value": steps / (t2 - t0), "unit": UNIT, "steps": steps, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h, "create_ms": (t1 - t0) * 1e3, "steps_per_s_after_create": steps / (t2 - t1),
+            "note": "host clock; create (H2D of the state, kick autotuning, graph capture) and the steps, each "
+                    "step followed by the state read back to host"}
 
 
 def ensemble_rates(seed: int, steps: int, warmup: int):
@@ -312,9 +318,12 @@ def heavy_rates(seed: int, steps: int, warmup: int, flush):
 
 
 def oracle_rate(system, seconds: float, max_steps: int | None = None):
+    """Steps/s of the oracle on this host's cores for about `seconds`; its
+    scan skips the pairs its end-point bound rules out (the same flagged set
+    as its all-pairs test).  Also returns its state, to compare against."""
     import oracle
     oracle.build()
-    sim = oracle.Sim.from_system(system)
+    sim = oracle.Sim.from_system(system, scan_prune=1)
     E0 = sim.energy()[0]
     t0 = time.perf_counter()
     done = 0
@@ -326,7 +335,29 @@ def oracle_rate(system, seconds: float, max_steps: int | None = None):
             break
     dE = abs(sim.energy()[0] - E0) / abs(E0)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return done / el, done, el, threads, dE
+    return done / el, done, el, threads, dE, sim
+
+
+def relpos(a, b):
+    """Largest relative position error of a against b (rows are bodies)."""
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
+
+
+def gpu_vs_oracle(system, steps: int, osim):
+    """Both GPU forms over the oracle's `steps` steps from the same inputs:
+    relative position error against the oracle's state and |dE/E|."""
+    from paper_2601_19654_gb300 import opal
+    alive = np.nonzero(osim.alive)[0]
+    out = {"steps": steps}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        with opal.Simulation.from_system(system, precision=prec) as sim:
+            E0 = sim.energy()[0]
+            sim.step(steps)
+            st = sim.state()
+            out[f"dE_over_E_{name}"] = abs(sim.energy()[0] - E0) / abs(E0)
+            out[f"pos_err_{name}"] = (relpos(st["x"], osim.x[alive]) if st["ids"].tolist() == alive.tolist()
+                                      else None)
+    return out
 
 
 # ---------------------------------------------------------------- main
@@ -336,7 +367,7 @@ def run_reference(args, rank, world):
     system = ic.equal_mass_disk(args.seed)
     import oracle
     oracle.build()
-    sim = oracle.Sim.from_system(system)
+    sim = oracle.Sim.from_system(system, scan_prune=1)
     warm = min(args.warmup, 3)   # each oracle step of this system takes about a second
     for _ in range(warm):
         sim.step(1)
@@ -354,7 +385,8 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": system.name, "bodies": system.n, "form": "FP64 serial oracle (C, OpenMP kick)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{done} full steps of the 16384-body system ({el:.1f} s)"},
+                             "sample": f"{done} full steps of the 16384-body system ({el:.1f} s; the scan "
+                                       "skips pairs by its end-point bound)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "interactions_per_s": v * system.n * (system.n - 1)}
     print(json.dumps(line), flush=True)
@@ -385,8 +417,19 @@ def run_ours(args, rank, world, local):
     value, total_ms = job_rate(float(np.sum(step_ms)), args.steps, world)
     dE_mixed = abs(sim.energy()[0] - E0) / abs(E0)
     last = sim.stats()
+    mixed_state = sim.state()
+    # the same kick kernel launched alone on the state the timed run left
+    kick_alone = sim.kick_alone_ms(20)
+    step_order = "overlap" if os.environ.get("OPAL_STEP_ORDER", "") != "inorder" else "inorder"
     sim.close()
     ms_per_step = total_ms / args.steps
+    # the FP64 form over the same steps from the same inputs: the mixed
+    # form's position error against it
+    with opal.Simulation.from_system(system, precision=0) as ref64:
+        ref64.step(args.warmup + args.steps)
+        ref_state = ref64.state()
+    pos_err_vs_fp64 = (relpos(mixed_state["x"], ref_state["x"])
+                       if mixed_state["ids"].tolist() == ref_state["ids"].tolist() else None)
 
     # FP64 form, same workload
     sim64 = opal.Simulation.from_system(system, precision=0)
@@ -407,7 +450,8 @@ def run_ours(args, rank, world, local):
     kick64_avg = float(np.mean(k64))
     flops = FLOPS_PER_INTERACTION * pairs
     peak = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flops / (kick_avg * 1e-3) / 1e12
+    achieved = flops / (kick_alone * 1e-3) / 1e12
+    achieved_graph = flops / (kick_avg * 1e-3) / 1e12
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -419,6 +463,9 @@ def run_ours(args, rank, world, local):
         "interactions_per_s": value * pairs,
         "dE_over_E": {"mixed": dE_mixed, "fp64": dE_fp64,
                       "over_steps": {"mixed": args.warmup + args.steps, "fp64": 3 + args.fp64_steps}},
+        "pos_err_vs_fp64": {"value": pos_err_vs_fp64, "steps": args.warmup + args.steps,
+                            "note": "max relative position error of the mixed run against the FP64 GPU form "
+                                    "after the same steps from the same inputs"},
         "fp64": {"value": world * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
                  "interactions_per_s": world * 1e3 / ms64 * pairs, "kick_ms": kick64_avg,
                  "steps": args.fp64_steps, "kick_fp64_tflops": flops / (kick64_avg * 1e-3) / 1e12,
@@ -430,17 +477,22 @@ def run_ours(args, rank, world, local):
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": KICK_TRAFFIC.get(kick_cfg.split(",")[0]),
                      "note": f"{FLOPS_PER_INTERACTION} FP32 flops per pair x N(N-1) pairs per launch; "
-                             "peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (of nominal max clock); the "
-                             "kick is timed inside the step graph, where it runs beside the encounter "
-                             "integrator and shares the SMs with it",
-                     "kick_ms": kick_avg, "kick_share_of_step": kick_avg / float(np.mean(step_ms)),
-                     "measured_alu_peaks": alu,
-                     "frac_of_measured_fp32": achieved / alu["fp32_tflops"] if alu else None},
+                             "peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (of nominal max clock); "
+                             "achieved: the step's kick kernel launched alone 20 times on the state the "
+                             "timed run left (CUDA events on the simulation's stream); in_graph: the same "
+                             "kernel timed inside the step graph over the timed steps, where it runs "
+                             "beside the encounter integrator",
+                     "kick_ms": kick_alone, "measured_alu_peaks": alu,
+                     "frac_of_measured_fp32": achieved / alu["fp32_tflops"] if alu else None,
+                     "in_graph": {"kick_ms": kick_avg, "achieved": achieved_graph, "frac": achieved_graph / peak,
+                                  "frac_of_measured_fp32": achieved_graph / alu["fp32_tflops"] if alu else None,
+                                  "kick_share_of_step": kick_avg / float(np.mean(step_ms)),
+                                  "step_order": step_order}},
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clocks,
     }
     if rank == 0:
-        line["e2e"] = e2e_rate(system, max(5, args.steps), precision=1)
+        line["e2e"] = e2e_rate(system, max(300, args.steps), precision=1)
         if not args.no_ensemble:
             line["ensemble"] = ensemble_rates(args.seed, args.ensemble_steps, 3)
         if not args.no_small:
@@ -450,10 +502,15 @@ def run_ours(args, rank, world, local):
         if not args.no_removals:
             line["removals"] = removal_rates(system, min(args.steps, 100), 5, flush, ms_per_step)
         if not args.no_cpu_baseline:
-            v, done, el, threads, dE = oracle_rate(system, args.cpu_seconds)
+            v, done, el, threads, dE, osim = oracle_rate(system, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                    "sample": f"{done} full steps of the {n}-body system ({el:.1f} s)",
+                                    "sample": f"{done} full steps of the {n}-body system ({el:.1f} s; the scan "
+                                              "skips pairs by its end-point bound)",
                                     "dE_over_E": dE}
+            # the FP64 oracle over those steps against both GPU forms
+            cmp = gpu_vs_oracle(system, done, osim)
+            cmp["dE_over_E_oracle"] = dE
+            line["vs_oracle"] = cmp
         print(json.dumps(line), flush=True)
 
 

@@ -113,7 +113,12 @@ opal_status opal_ensemble_create(const opal_params* p, int32_t nsys, const int64
 
 /* Advance every system by nsteps steps (synchronous).  Stops at the first
  * step that fails; that step is undone and its status returned
- * (OPAL_EKEPLER, OPAL_EBS, OPAL_EOVERFLOW, OPAL_ENONFINITE or OPAL_ECUDA). */
+ * (OPAL_EKEPLER, OPAL_EBS, OPAL_EOVERFLOW, OPAL_ENONFINITE or OPAL_ECUDA).
+ * In the mixed form the kick runs beside the encounter integrator, on the
+ * state after the drift, and is corrected for the encounter members
+ * afterwards, while under 3% of the big bodies were in encounters in the
+ * previous call (in order, after the encounters, above 8%); the environment
+ * variable OPAL_STEP_ORDER=overlap or inorder forces one. */
 opal_status opal_step(opal_sim* sim, int64_t nsteps);
 
 /* Enqueue nsteps steps on the simulation's stream and return at once;
@@ -169,7 +174,9 @@ opal_status opal_energy_momentum(const opal_sim* sim, int32_t sys, double* E, do
  * scratch row the call reads are written by the same call.
  * The first call on each device looks up the scratch's device address
  * (cudaGetSymbolAddress, with that device current): make that first call
- * before any stream capture begins.  All calls on a device share the one
+ * before any stream capture begins.  The address is kept per device and
+ * context: after a device reset (a new primary context) the next call looks
+ * it up again, so make that call outside any capture as well.  All calls on a device share the one
  * scratch array, so two calls in flight at once (other streams or other
  * host threads) race and may return wrong values: serialize them.
  * Errors: OPAL_EINVAL (n out of range, G or M0 invalid, a NULL, misaligned
@@ -206,6 +213,16 @@ const char* opal_kick_config(const opal_sim* sim);
  * the most recent step (waiting for it), or -1 when timing is off. */
 opal_status opal_time_kick(opal_sim* sim, int32_t enable);
 double opal_last_kick_ms(const opal_sim* sim);
+
+/* The kick kernel alone: reps launches (reps >= 1, after one untimed
+ * launch) of the step's kick kernel on the simulation's stream, on the
+ * sorted copies the last step left (the same item list and launch shape as
+ * in the step graph, without the encounter integrator beside it), timed with
+ * CUDA events on that stream; *ms gets the mean device time of one launch.
+ * It rewrites only the kick's partial rows, which every step computes
+ * afresh, so the simulation's state and later steps are unchanged.
+ * Errors: OPAL_EINVAL (NULL argument, reps < 1), OPAL_ECUDA. */
+opal_status opal_time_kick_alone(opal_sim* sim, int32_t reps, double* ms);
 
 /* Number of kernel launches in one step (kernel nodes of the step graph). */
 int32_t opal_graph_kernels(const opal_sim* sim);

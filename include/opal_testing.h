@@ -53,6 +53,19 @@ opal_status opal_debug_bs_group(opal_sim* sim, const double* x0, const double* V
                                 double* V, double* m, double* radius, int32_t* alive, double* E_lost,
                                 int64_t* substeps);
 
+/* Grid barriers of the whole-GPU encounter kernel (groups of more than 64
+ * members, whose blocks meet at grid-wide barriers between the phases of
+ * every derivative).  Each barrier wait is bounded by the global timer:
+ * after wait_ns (wait_ns = 0 restores the default, 4 s) the waiting block
+ * sets an abort flag that every block leaves through, and the step fails
+ * with OPAL_EBS and is undone from its saved start.  hold = 1 makes the
+ * last block to arrive wait as well instead of releasing the others, as if
+ * a block never arrived, so the first barrier's waits run out; hold = 0
+ * restores normal barriers.  The setting holds for the simulation's later
+ * steps; the step graph is captured again.  Errors: OPAL_EINVAL for
+ * wait_ns < 0 or hold not 0 or 1; OPAL_ECUDA if the capture fails. */
+opal_status opal_debug_barrier(opal_sim* sim, int64_t wait_ns, int32_t hold);
+
 /* Measured ALU peaks of the current device, for rooflines: out[0] FP32 FMA
  * TFLOP/s (an FMA counts 2), out[1] FP64 FMA TFLOP/s, out[2] MUFU reciprocal
  * square roots, Tops/s.  Independent FMA (or rsqrt) chains on every SM, a few

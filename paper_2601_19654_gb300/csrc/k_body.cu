@@ -204,9 +204,10 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     const SysInfo si = d.sys[s];
     const double* P = d.Ptot + 3 * (d.nsys + s);   // momentum for the closing jump
     const double half = 0.5 * d.p.dt, G = d.p.G;
-    const int64_t local = b - si.off;
     // the kick's partial rows, summed in row order; eight rows' loads are
-    // issued together so their latencies overlap
+    // issued together so their latencies overlap.  The mixed kick writes a
+    // body's partials at its sorted position, the FP64 kick at its index.
+    const int64_t local = (d.p.precision == 1 ? (int64_t)d.cpos[b] : b) - si.off;
     double ax = 0, ay = 0, az = 0;
     int c = 0;
     for (; c + 8 <= si.nchunk; c += 8) {
@@ -232,8 +233,10 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
         az += d.pacc_z[slot];
     }
     // after encounters, when the kick ran beside the BS: a member's row was
-    // recomputed at its new place, every other body's row gets the members'
-    // old terms swapped for new ones
+    // recomputed at its new place; every other body's row gets the members'
+    // terms at their new places added (the mixed kick left the members out
+    // as sources: mass 0 in its float copy), or in the FP64 form, which never
+    // runs beside the BS, their old terms swapped for new ones
     if (!first && d.ctl->ninvolved > 0) {
         const bool member = d.label[b] >= 0;
         if (member) d.label[b] = -1;   // in both orders: next step's groups start from no labels
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(kRemThreads) k_remove(Dev d) {
     }
 }
 
-// Start of a step: the counters, bounds and scratch the step's kernels// Start of a step: the counters, bounds and scratch the step's kernels
+// Start of a step: the counters, bounds and scratch the step's kernels
 // accumulate into, zeroed or preset in one launch (rather than ten memsets).
 __global__ void __launch_bounds__(256) k_step_reset(Dev d) {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;

@@ -1141,8 +1141,9 @@ void launch_bs_packed(const Dev& d, int nsm, cudaStream_t s) {
 // blocks fit (a larger-group block takes half an SM's registers or more).
 // Otherwise the larger-group kernels go first, on a branch of the same
 // priority, and the small-group blocks fill the room they leave.
-void launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join,
-                        bool small_first) {
+cudaError_t launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork,
+                               cudaEvent_t join, bool small_first) {
+    cudaError_t err = cudaSuccess;   // the first failed launch, if any (the cluster and cooperative ones)
     if (s2 != s) {
         cudaEventRecord(fork, s);
         cudaStreamWaitEvent(s2, fork, 0);
@@ -1152,7 +1153,8 @@ void launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, 
         if (s2 == s) prof_mark("bs: groups of 5-32");
         k_bs<kBsLargerThreads, 1, 1><<<nsm, kBsLargerThreads, sizeof(BsSh<kBsLargerThreads, 1>), s2>>>(d, 2);
         if (s2 == s) prof_mark("bs: groups of 33-64");
-        launch_bs_huge(d, nsm, s2);
+        const cudaError_t e = launch_bs_huge(d, nsm, s2);
+        if (err == cudaSuccess) err = e;
     };
     if (!small_first) larger();
     {
@@ -1169,7 +1171,8 @@ void launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, 
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, k_bs_ws, d);
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_bs_ws, d);
+        if (err == cudaSuccess) err = e;
     }
     prof_mark("bs: groups <= 4");
     if (small_first) larger();
@@ -1177,6 +1180,7 @@ void launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, 
         cudaEventRecord(join, s2);
         cudaStreamWaitEvent(s, join, 0);
     }
+    return err;
 }
 
 }  // namespace opal

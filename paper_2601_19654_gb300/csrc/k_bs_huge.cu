@@ -16,8 +16,8 @@
 //            the tableau and the error, folded into a grid-wide maximum).
 // Every thread takes the same decisions from the same values in global
 // memory, so the control flow is identical in all blocks.  A barrier that
-// waits longer than four seconds sets an abort flag: every block leaves and
-// the step reports OPAL_EBS.
+// waits longer than its limit (four seconds; a test hook sets it shorter)
+// sets an abort flag: every block leaves and the step reports OPAL_EBS.
 #include "opal_internal.cuh"
 
 namespace opal {
@@ -31,14 +31,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// grid-wide barrier (all blocks of the launch are resident); false once aborted
-__device__ bool huge_sync(HugeCtl* hc) {
+// grid-wide barrier (all blocks of the launch are resident); false once aborted.
+// Each wait is bounded by wait_ns of the global timer.  hold (a test hook):
+// the last block to arrive does not release the others but waits too, so
+// every wait runs out, as if a block never arrived.
+__device__ bool huge_sync(HugeCtl* hc, unsigned long long wait_ns, int hold) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned int* gen = &hc->bar_gen;
         const unsigned int g = *gen;
         __threadfence();
-        if (atomicAdd(&hc->bar_count, 1u) == gridDim.x - 1) {
+        if (atomicAdd(&hc->bar_count, 1u) == gridDim.x - 1 && !hold) {
             hc->bar_count = 0;   // nobody adds again before the generation moves
             __threadfence();
             atomicAdd(&hc->bar_gen, 1u);
@@ -46,7 +49,7 @@ __device__ bool huge_sync(HugeCtl* hc) {
             const unsigned long long t0 = global_ns();
             while (*gen == g) {
                 if (*(volatile int*)&hc->abort) break;
-                if (global_ns() - t0 > 4000000000ull) {
+                if (global_ns() - t0 > wait_ns) {
                     atomicExch(&hc->abort, 1);
                     break;
                 }
@@ -191,9 +194,16 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
     HugeCtl* hc = d.hctl;
     const int nh = d.ctl->nhuge;
     if (nh == 0) return;   // fixed before the launch: the same in every block
+    const unsigned long long wait_ns = (unsigned long long)d.huge_wait_ns;
+    const int hold = d.huge_hold;
+    auto huge_sync = [&](HugeCtl* h) { return opal::huge_sync(h, wait_ns, hold); };
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     // status set before this kernel: block 0 looks, everyone follows
-    if (blockIdx.x == 0 && threadIdx.x == 0) hc->skip = d.ctl->status;
-    if (!huge_sync(hc)) return;
+    if (lead) hc->skip = d.ctl->status;
+    if (!huge_sync(hc)) {
+        if (lead) set_status(d.ctl, kEbs, kHugeAbortDetail);   // no group started: a barrier wait ran out
+        return;
+    }
     if (*(volatile int*)&hc->skip) return;
     const Params p = d.p;
     const HugeBuf& H = d.hb;
@@ -201,7 +211,6 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
     const double dt = p.dt, tol2 = p.bs_tol * p.bs_tol;
     const int cap = p.bs_max_substeps;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
-    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     for (int hi = 0; hi < nh; hi++) {
         const int g = d.ghuge[hi];
         const int m0 = d.goff[g], M = d.goff[g + 1] - m0;
@@ -412,7 +421,7 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
             }
         }
         if (!ok) {
-            if (lead) set_status(d.ctl, kEbs, 3000000 + g);
+            if (lead) set_status(d.ctl, kEbs, kHugeAbortDetail + 1 + g);
             return;
         }
         for (int64_t b = gt; b < M; b += nt) {
@@ -432,7 +441,7 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
     }
 }
 
-void launch_bs_huge(const Dev& d, int nsm, cudaStream_t s) {
+cudaError_t launch_bs_huge(const Dev& d, int nsm, cudaStream_t s) {
     // all blocks must be resident at once for the barriers: a cooperative launch
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nsm);
@@ -444,8 +453,9 @@ void launch_bs_huge(const Dev& d, int nsm, cudaStream_t s) {
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_bs_huge, d);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_bs_huge, d);
     prof_mark("bs: groups of more than 64");
+    return e;
 }
 
 }  // namespace opal

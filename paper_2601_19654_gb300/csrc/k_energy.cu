@@ -4,6 +4,7 @@
 //   E = sum 1/2 m |V|^2 - sum G M0 m / |x| + |P|^2 / (2 M0) - sum_{i<j} G m_i m_j / r_ij,
 //   P = sum m V,  L = sum m x x V.
 // FP64 throughout; every partial is summed in a fixed order.
+#include <cuda.h>   // driver types only: cuCtxGetCurrent / cuCtxGetId are reached through the runtime
 #include <cmath>
 #include <mutex>
 
@@ -230,9 +231,49 @@ __global__ void __launch_bounds__(256) k_energy_na_final(int nb, double G, doubl
 namespace {
 
 std::mutex g_na_mu;
-double* g_na_ptr[kNaMaxDevices] = {};
+// per device: the scratch's device address and the context it belongs to
+struct NaScratch {
+    unsigned long long ctx_id;
+    double* ptr;
+};
+NaScratch g_na[kNaMaxDevices] = {};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
 
-// the device address of g_na_part on the current device, looked up once per device
+// unique id of the current context (0 if none is current yet); caller holds g_na_mu
+opal_status na_context_id(unsigned long long* id) {
+    if (!g_ctx_current || !g_ctx_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            cudaGetLastError();
+            set_thread_error("the driver's context queries (cuCtxGetCurrent, cuCtxGetId) are unavailable");
+            return OPAL_ECUDA;
+        }
+        g_ctx_current = (CtxGetCurrentFn)f1;
+        g_ctx_id = (CtxGetIdFn)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS) {
+        set_thread_error("cuCtxGetCurrent failed");
+        return OPAL_ECUDA;
+    }
+    *id = 0;
+    if (ctx && g_ctx_id(ctx, id) != CUDA_SUCCESS) {
+        set_thread_error("cuCtxGetId failed");
+        return OPAL_ECUDA;
+    }
+    return OPAL_OK;
+}
+
+// the device address of g_na_part in the current device's context, looked up
+// once per device and context (a device reset or a new primary context makes
+// the module load again at another address, so the lookup is redone)
 opal_status na_scratch(double** out) {
     int dev = -1;
     cudaError_t rc = cudaGetDevice(&dev);
@@ -245,7 +286,10 @@ opal_status na_scratch(double** out) {
         return OPAL_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    unsigned long long id = 0;
+    opal_status st = na_context_id(&id);
+    if (st != OPAL_OK) return st;
+    if (!g_na[dev].ptr || id == 0 || g_na[dev].ctx_id != id) {
         void* p = nullptr;
         rc = cudaGetSymbolAddress(&p, g_na_part);
         if (rc != cudaSuccess || !p) {
@@ -253,9 +297,12 @@ opal_status na_scratch(double** out) {
                              cudaGetErrorString(rc));
             return OPAL_ECUDA;
         }
-        g_na_ptr[dev] = (double*)p;
+        st = na_context_id(&id);   // the lookup made the primary context current if none was
+        if (st != OPAL_OK) return st;
+        g_na[dev].ctx_id = id;
+        g_na[dev].ptr = (double*)p;
     }
-    *out = g_na_ptr[dev];
+    *out = g_na[dev].ptr;
     return OPAL_OK;
 }
 

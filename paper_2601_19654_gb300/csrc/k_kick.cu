@@ -39,8 +39,8 @@ __device__ __forceinline__ void fold(float& hi, float& lo, float t) {
 // Slow path of the mixed kick: the lo parts refine the separation, then the
 // changeover weight; returns (s, dx, dy, dz) with the weighted 1/r^3 in s.
 // li, lj: lo parts of i and j; rcj: rc of j (all already on chip).
-__device__ __forceinline__ float4 slow_pair_f(float4 li, float4 lj, float dx, float dy, float dz, float mj,
-                                              float rci, float rcj, int form) {
+__device__ __noinline__ float4 slow_pair_f(float4 li, float4 lj, float dx, float dy, float dz, float mj,
+                                           float rci, float rcj, int form) {
     dx += lj.x - li.x;
     dy += lj.y - li.y;
     dz += lj.z - li.z;
@@ -76,237 +76,350 @@ __device__ __forceinline__ void queue_done(const Dev& d) {
     }
 }
 
-// One staged j-tile against the thread's NI i-bodies.  NEAR: some pair may be
-// closer than the i-body's threshold, so every pair is tested and the close
-// ones take the slow path; otherwise every pair is a plain Newtonian term.
-template <int NI, bool NEAR, int NJ>
-__device__ __forceinline__ void kick_tile(const float4* sj, const float4* sl, const float* src, int nj,
-                                          const float (&xi)[NI], const float (&yi)[NI], const float (&zi)[NI],
-                                          const float (&thr)[NI], const float (&rci)[NI], const float4 (&li)[NI],
-                                          int form, float (&tx)[NI], float (&ty)[NI], float (&tz)[NI]) {
-    // NJ > 0: a full tile, the trip count known at compile time.  Near tiles
-    // are few: a rolled loop keeps their registers down.
-    const int n = NJ > 0 ? NJ : nj;
-#pragma unroll(NEAR ? 2 : 8)
-    for (int jj = 0; jj < n; jj++) {
-        const float4 pj = sj[jj];
-#pragma unroll
-        for (int q = 0; q < NI; q++) {
-            float dx = pj.x - xi[q], dy = pj.y - yi[q], dz = pj.z - zi[q];
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            float s;
-            if (NEAR && r2 < thr[q]) {
-                float4 r = slow_pair_f(li[q], sl[jj], dx, dy, dz, pj.w, rci[q], src[jj], form);
-                s = r.x;
-                dx = r.y;
-                dy = r.z;
-                dz = r.w;
-            } else {
-                float ri = rsqrt_approx(r2);
-                s = (pj.w * ri) * (ri * ri);
-            }
-            tx[q] = fmaf(s, dx, tx[q]);
-            ty[q] = fmaf(s, dy, ty[q]);
-            tz[q] = fmaf(s, dz, tz[q]);
-        }
-    }
-}
-
-// Box of the points the block's threads hold (each thread: its own box bl, bh,
-// empty when have is false), reduced over the block through red; every
-// thread gets the result.  An empty box comes out with lo > hi.  The caller
-// makes sure no thread still reads red from an earlier use.
-template <int T>
-__device__ __forceinline__ void block_box(bool have, const float (&bl)[3], const float (&bh)[3],
-                                          int (*red)[T / 32], float (&lo)[3], float (&hi)[3]) {
+// ---------------------------------------------------------------------------
+// Staging, before each mixed kick: the float copies of the kick's bodies in
+// the scan's spatial order (position p holds body csorted[p]) as separate
+// arrays, so that a j-tile is a contiguous run of records, and for every
+// 128-position tile the box of its live positions and its largest near
+// threshold (2 (rc + rc_max))^2, so that the kick reads a tile's box instead
+// of reducing it (also for every 256 positions, the j-tiles and the larger
+// i-tiles).  Parked bodies (dead or padding, at kFar) stay out of the boxes;
+// an empty tile gets lo > hi.
+__global__ void __launch_bounds__(2 * kKickBox) k_kick_stage(Dev d) {
+    if (d.gated && !d.ctl->reprime) return;   // the re-evaluation after a removal, with none
+    if (d.ctl->status) return;
+    constexpr int W = 2 * kKickBox / 32;      // warps of the block (8)
+    __shared__ int red[7][W];
+    const int64_t p = (int64_t)blockIdx.x * 2 * kKickBox + threadIdx.x;   // grid: ntot / 256 blocks
+    const int b = d.csorted[p];
+    const float4 h = d.kh[b];
+    const float rc = d.rcf[b];
+    d.ks_x[p] = h.x;
+    d.ks_y[p] = h.y;
+    d.ks_z[p] = h.z;
+    d.ks_m[p] = h.w;
+    d.ks_lo[p] = d.kl[b];
+    d.ks_rc[p] = rc;
+    const bool live = h.x < 0.5f * kFar;
+    const float t = 2.0f * (rc + d.rcmax[d.body_sys[b]]);
+    const float thr = fmaxf(t * t, 1e-30f);
+    const float c[3] = {h.x, h.y, h.z};
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        const int a = __reduce_min_sync(0xffffffffu, have ? ford(bl[k]) : 0x7fffffff);
-        const int b = __reduce_max_sync(0xffffffffu, have ? ford(bh[k]) : (int)0x80000000);
-        if ((threadIdx.x & 31) == 0) {
-            red[k][threadIdx.x >> 5] = a;
-            red[k + 3][threadIdx.x >> 5] = b;
+        const int lo = __reduce_min_sync(0xffffffffu, live ? ford(c[k]) : 0x7fffffff);
+        const int hi = __reduce_max_sync(0xffffffffu, live ? ford(c[k]) : (int)0x80000000);
+        if (lane == 0) {
+            red[k][wq] = lo;
+            red[3 + k][wq] = hi;
         }
     }
+    // thresholds are >= 0: their bits order as their values
+    const int tm = __reduce_max_sync(0xffffffffu, live ? __float_as_int(thr) : 0);
+    if (lane == 0) red[6][wq] = tm;
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        int a = red[k][0], b = red[k + 3][0];
-#pragma unroll
-        for (int wq = 1; wq < T / 32; wq++) {
-            a = min(a, red[k][wq]);
-            b = max(b, red[k + 3][wq]);
+    // thread 0: the first 128 positions, thread 1: the second, thread 2: all 256
+    if (threadIdx.x < 3) {
+        const int w0 = threadIdx.x == 1 ? W / 2 : 0, w1 = threadIdx.x == 0 ? W / 2 : W;
+        int v[7];
+        for (int k = 0; k < 7; k++) {
+            v[k] = red[k][w0];
+            for (int w = w0 + 1; w < w1; w++) v[k] = (k < 3) ? min(v[k], red[k][w]) : max(v[k], red[k][w]);
         }
-        lo[k] = fordinv(a);
-        hi[k] = fordinv(b);
+        const float4 lo = make_float4(fordinv(v[0]), fordinv(v[1]), fordinv(v[2]), __int_as_float(v[6]));
+        const float4 hi = make_float4(fordinv(v[3]), fordinv(v[4]), fordinv(v[5]), 0.0f);
+        float4* o = threadIdx.x < 2 ? d.kbox + 2 * (2 * (int64_t)blockIdx.x + threadIdx.x)
+                                    : d.kbox2 + 2 * (int64_t)blockIdx.x;
+        o[0] = lo;
+        o[1] = hi;
     }
 }
 
-__device__ __forceinline__ void box_add(const float4& p, bool& have, float (&bl)[3], float (&bh)[3]) {
-    if (p.x < 0.5f * kFar) {   // parked (dead or padding) bodies stay out
-        bl[0] = fminf(bl[0], p.x); bl[1] = fminf(bl[1], p.y); bl[2] = fminf(bl[2], p.z);
-        bh[0] = fmaxf(bh[0], p.x); bh[1] = fmaxf(bh[1], p.y); bh[2] = fmaxf(bh[2], p.z);
-        have = true;
+// Far j-tile (no pair can be near): plain Newtonian terms in packed FP32
+// pairs.  Each 16-byte shared load brings four j records' x (or y, z, m);
+// each packed instruction takes two j at once against one i, the two lanes
+// of the packed accumulators holding the even and the odd j.  The arithmetic
+// of each lane is the scalar fast path's: x_j + (-x_i) is x_j - x_i exactly.
+template <int NI>
+__device__ __forceinline__ void far_tile(const float* sx, const float* sy, const float* sz, const float* sm,
+                                         const float2 (&nx)[NI], const float2 (&ny)[NI], const float2 (&nz)[NI],
+                                         float2 (&ax)[NI], float2 (&ay)[NI], float2 (&az)[NI]) {
+    const float4* px = reinterpret_cast<const float4*>(sx);
+    const float4* py = reinterpret_cast<const float4*>(sy);
+    const float4* pz = reinterpret_cast<const float4*>(sz);
+    const float4* pm = reinterpret_cast<const float4*>(sm);
+#pragma unroll 2
+    for (int jq = 0; jq < kJTile / 4; jq++) {
+        const float4 x4 = px[jq], y4 = py[jq], z4 = pz[jq], m4 = pm[jq];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const float2 xj = h ? make_float2(x4.z, x4.w) : make_float2(x4.x, x4.y);
+            const float2 yj = h ? make_float2(y4.z, y4.w) : make_float2(y4.x, y4.y);
+            const float2 zj = h ? make_float2(z4.z, z4.w) : make_float2(z4.x, z4.y);
+            const float2 mj = h ? make_float2(m4.z, m4.w) : make_float2(m4.x, m4.y);
+#pragma unroll
+            for (int q = 0; q < NI; q++) {
+                const float2 dx = __fadd2_rn(xj, nx[q]), dy = __fadd2_rn(yj, ny[q]), dz = __fadd2_rn(zj, nz[q]);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                const float2 sv = __fmul2_rn(__fmul2_rn(mj, ri), __fmul2_rn(ri, ri));
+                ax[q] = __ffma2_rn(sv, dx, ax[q]);
+                ay[q] = __ffma2_rn(sv, dy, ay[q]);
+                az[q] = __ffma2_rn(sv, dz, az[q]);
+            }
+        }
     }
+}
+
+// Near j-tile: the packed loop, with every pair closer than the i-body's
+// threshold left out (its term set to zero) and its j noted in the lane's
+// own list in shared memory; then the lanes take the slow path (lo parts,
+// changeover) for their listed pairs side by side, each adding its own in
+// j order, so the warp runs as many slow-path rounds as its longest list
+// holds rather than one for every j where any lane has a near pair.  A list
+// that could overflow is worked off first (a warp-uniform test).  The
+// i-body's lo parts, rc and threshold are read here (near tiles are few).
+constexpr int kNearList = 32;   // listed near pairs per lane and i-body before a flush
+
+template <int T, int NI>
+__device__ __forceinline__ void near_flush(const float* sx, const float* sy, const float* sz, const float* sm,
+                                           const float4* sl, const float* src, const unsigned char* lst,
+                                           const int (&cnt)[NI], const float2 (&nx)[NI], const float2 (&ny)[NI],
+                                           const float2 (&nz)[NI], const float4 (&li)[NI], const float (&rci)[NI],
+                                           int form, float2 (&ax)[NI], float2 (&ay)[NI], float2 (&az)[NI]) {
+#pragma unroll
+    for (int q = 0; q < NI; q++) {
+        int most = cnt[q];
+        for (int o = 16; o >= 1; o >>= 1) most = max(most, __shfl_xor_sync(0xffffffffu, most, o));
+        for (int k = 0; k < most; k++) {
+            if (k < cnt[q]) {
+                const int jj = lst[(k * NI + q) * T + threadIdx.x];
+                const float4 r = slow_pair_f(li[q], sl[jj], sx[jj] + nx[q].x, sy[jj] + ny[q].x, sz[jj] + nz[q].x,
+                                             sm[jj], rci[q], src[jj], form);
+                ax[q].x = fmaf(r.x, r.y, ax[q].x);
+                ay[q].x = fmaf(r.x, r.z, ay[q].x);
+                az[q].x = fmaf(r.x, r.w, az[q].x);
+            }
+        }
+    }
+}
+
+template <int T, int NI>
+__device__ __forceinline__ void near_tile(const Dev& d, int64_t i0, float rcm, const float* sx, const float* sy,
+                                          const float* sz, const float* sm, const float4* sl, const float* src,
+                                          unsigned char* lst, const float2 (&nx)[NI], const float2 (&ny)[NI],
+                                          const float2 (&nz)[NI], int form, float2 (&ax)[NI], float2 (&ay)[NI],
+                                          float2 (&az)[NI]) {
+    float4 li[NI];
+    float rci[NI], thr[NI];
+    int cnt[NI];
+#pragma unroll
+    for (int q = 0; q < NI; q++) {
+        const int64_t p = i0 + q * T + threadIdx.x;
+        li[q] = d.ks_lo[p];
+        rci[q] = d.ks_rc[p];
+        const float t = 2.0f * (rci[q] + rcm);
+        thr[q] = fmaxf(t * t, 1e-30f);
+        cnt[q] = 0;
+    }
+    const float4* px = reinterpret_cast<const float4*>(sx);
+    const float4* py = reinterpret_cast<const float4*>(sy);
+    const float4* pz = reinterpret_cast<const float4*>(sz);
+    const float4* pm = reinterpret_cast<const float4*>(sm);
+#pragma unroll 1
+    for (int jq = 0; jq < kJTile / 4; jq++) {
+        // room for the four pairs of this quad in every lane's list, or work it off
+        bool full = false;
+#pragma unroll
+        for (int q = 0; q < NI; q++) full |= cnt[q] > kNearList - 4;
+        if (__any_sync(0xffffffffu, full)) {
+            near_flush<T, NI>(sx, sy, sz, sm, sl, src, lst, cnt, nx, ny, nz, li, rci, form, ax, ay, az);
+#pragma unroll
+            for (int q = 0; q < NI; q++) cnt[q] = 0;
+        }
+        const float4 x4 = px[jq], y4 = py[jq], z4 = pz[jq], m4 = pm[jq];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const float2 xj = h ? make_float2(x4.z, x4.w) : make_float2(x4.x, x4.y);
+            const float2 yj = h ? make_float2(y4.z, y4.w) : make_float2(y4.x, y4.y);
+            const float2 zj = h ? make_float2(z4.z, z4.w) : make_float2(z4.x, z4.y);
+            const float2 mj = h ? make_float2(m4.z, m4.w) : make_float2(m4.x, m4.y);
+#pragma unroll
+            for (int q = 0; q < NI; q++) {
+                const float2 dx = __fadd2_rn(xj, nx[q]), dy = __fadd2_rn(yj, ny[q]), dz = __fadd2_rn(zj, nz[q]);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                float2 sv = __fmul2_rn(__fmul2_rn(mj, ri), __fmul2_rn(ri, ri));
+                const int j = 4 * jq + 2 * h;
+                if (r2.x < thr[q]) {
+                    sv.x = 0.0f;
+                    lst[(cnt[q]++ * NI + q) * T + threadIdx.x] = (unsigned char)j;
+                }
+                if (r2.y < thr[q]) {
+                    sv.y = 0.0f;
+                    lst[(cnt[q]++ * NI + q) * T + threadIdx.x] = (unsigned char)(j + 1);
+                }
+                ax[q] = __ffma2_rn(sv, dx, ax[q]);
+                ay[q] = __ffma2_rn(sv, dy, ay[q]);
+                az[q] = __ffma2_rn(sv, dz, az[q]);
+            }
+        }
+    }
+    near_flush<T, NI>(sx, sy, sz, sm, sl, src, lst, cnt, nx, ny, nz, li, rci, form, ax, ay, az);
 }
 
 // Items index the system's bodies in the order the encounter scan sorted
-// them (cells of the path midpoints, so a 128-body tile is compact).  Each
-// staged j-tile gets its box; when that box is farther from the i-tile's box
-// than the largest i threshold allows, no pair of the tile can need the slow
-// path and the tile runs without the per-pair test.
+// them (cells of the path midpoints, so a 128-body tile is compact); the
+// staging kernel has copied them there.  An item is one j-tile of 256
+// sources, staged in shared memory once, against a run of i-tiles of
+// T x NI bodies (every istep-th position: a run's tiles are spread over the
+// system, so that the few near ones fall into different items); each thread
+// takes NI i-bodies of each i-tile, and the next i-tile's positions and box
+// are loaded while the current one runs.  An
+// i-tile whose box is farther from the j-tile's box than the i-tile's
+// largest threshold allows cannot hold a near pair and runs the packed loop
+// with no per-pair test.  Records past the item's j-range are parked (kFar,
+// zero mass): they add exact zeros.  Each (i-tile, j-tile) sum goes to the
+// j-tile's partial row, at the i-body's sorted position; k_close adds the
+// rows in order.
 template <int T, int NI, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_kick_mixed(Dev d, const KickItem* __restrict__ items, int64_t nitems) {
     if (d.gated && !d.ctl->reprime) return;   // the re-evaluation after a removal, with none
-    constexpr int JPT = kJTile / T;   // j records each thread stages
-    __shared__ float4 sj[kJTile];
-    __shared__ int sid[kJTile];
-    __shared__ float4 sl[kJTile];     // lo parts and rc of the j-tile, staged only when it is near
+    constexpr int JPT = kJTile / T;           // j records each thread stages (2 or 4)
+    constexpr int IT = T * NI;                // bodies of an i-tile: 128 or 256, one staged box
+    static_assert(JPT == 2 || JPT == 4, "the kick stages 2 or 4 records a thread");
+    static_assert(IT == kKickBox || IT == 2 * kKickBox, "an i-tile is one staged box");
+    const float4* ibox = IT == kKickBox ? d.kbox : d.kbox2;
+    __shared__ __align__(16) float sx[kJTile], sy[kJTile], sz[kJTile], sm[kJTile];
+    __shared__ float4 sl[kJTile];     // lo parts and 4 rc^2 of the j-tile (the near path's)
     __shared__ float src[kJTile];
-    __shared__ int red[6][T / 32];
-    __shared__ int red_t[T / 32];
-    __shared__ int s_item;
+    __shared__ KickItem s_w;          // the block's item
+    __shared__ float s_jbox[6];       // its j-tile's box (lo xyz, hi xyz)
+    __shared__ unsigned char s_near[kNearList * NI * T];   // near pairs' j, per lane and i-body
     if (d.ctl->status) return;
     const int form = d.p.changeover;
     for (;;) {
         // items are taken in list order (largest first) by whichever block is free
         __syncthreads();
-        if (threadIdx.x == 0) s_item = atomicAdd(&d.ctl->kick_next, 1);
+        if (threadIdx.x == 0) {
+            const int64_t it = atomicAdd(&d.ctl->kick_next, 1);
+            s_w.sys = -1;
+            if (it < nitems) s_w = items[it];
+        }
         __syncthreads();
-        const int64_t it = s_item;
-        if (it >= nitems) break;
-        const KickItem w = items[it];
-        const SysInfo si = d.sys[w.sys];
+        if (s_w.sys < 0) break;
+        const KickItem w = s_w;
+        const int nj = (int)(w.j1 - w.j0);
         const float rcm = d.rcmax[w.sys];
-        float xi[NI], yi[NI], zi[NI], thr[NI], rci[NI];
-        float4 li[NI];
-        int ii[NI];
-        float hx[NI], hy[NI], hz[NI], lx[NI], ly[NI], lz[NI];
-        float tmax = 0.0f;
-        bool ihave = false;
-        float ibl[3] = {3.0e38f, 3.0e38f, 3.0e38f}, ibh[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+        // stage the j-tile: contiguous records, past nj parked
+        {
+            const int k0 = threadIdx.x * JPT;
+            float vx[JPT], vy[JPT], vz[JPT], vm[JPT];
+            if (k0 + JPT <= nj) {
+                if (JPT == 2) {
+                    const float2 a = *reinterpret_cast<const float2*>(d.ks_x + w.j0 + k0);
+                    const float2 b = *reinterpret_cast<const float2*>(d.ks_y + w.j0 + k0);
+                    const float2 c = *reinterpret_cast<const float2*>(d.ks_z + w.j0 + k0);
+                    const float2 e = *reinterpret_cast<const float2*>(d.ks_m + w.j0 + k0);
+                    vx[0] = a.x; vx[1] = a.y; vy[0] = b.x; vy[1] = b.y;
+                    vz[0] = c.x; vz[1] = c.y; vm[0] = e.x; vm[1] = e.y;
+                } else {
+                    const float4 a = *reinterpret_cast<const float4*>(d.ks_x + w.j0 + k0);
+                    const float4 b = *reinterpret_cast<const float4*>(d.ks_y + w.j0 + k0);
+                    const float4 c = *reinterpret_cast<const float4*>(d.ks_z + w.j0 + k0);
+                    const float4 e = *reinterpret_cast<const float4*>(d.ks_m + w.j0 + k0);
+                    vx[0] = a.x; vx[1] = a.y; vx[JPT - 2] = a.z; vx[JPT - 1] = a.w;
+                    vy[0] = b.x; vy[1] = b.y; vy[JPT - 2] = b.z; vy[JPT - 1] = b.w;
+                    vz[0] = c.x; vz[1] = c.y; vz[JPT - 2] = c.z; vz[JPT - 1] = c.w;
+                    vm[0] = e.x; vm[1] = e.y; vm[JPT - 2] = e.z; vm[JPT - 1] = e.w;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < JPT; u++) {
+                    const bool in = k0 + u < nj;
+                    vx[u] = in ? d.ks_x[w.j0 + k0 + u] : kFar;
+                    vy[u] = in ? d.ks_y[w.j0 + k0 + u] : kFar;
+                    vz[u] = in ? d.ks_z[w.j0 + k0 + u] : kFar;
+                    vm[u] = in ? d.ks_m[w.j0 + k0 + u] : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < JPT; u++) {
+                sx[k0 + u] = vx[u];
+                sy[k0 + u] = vy[u];
+                sz[k0 + u] = vz[u];
+                sm[k0 + u] = vm[u];
+                sl[k0 + u] = k0 + u < nj ? d.ks_lo[w.j0 + k0 + u] : make_float4(0.0f, 0.0f, 0.0f, 1e-30f);
+                src[k0 + u] = k0 + u < nj ? d.ks_rc[w.j0 + k0 + u] : 0.0f;
+            }
+            if (threadIdx.x == 0) {
+                // the j-tile's box: its whole 256 positions (any records past nj
+                // are padding or small bodies, and a larger box only sends more
+                // i-tiles to the near path)
+                const float4 lo = d.kbox2[2 * (w.j0 / kJTile)], hi = d.kbox2[2 * (w.j0 / kJTile) + 1];
+                s_jbox[0] = lo.x; s_jbox[1] = lo.y; s_jbox[2] = lo.z;
+                s_jbox[3] = hi.x; s_jbox[4] = hi.y; s_jbox[5] = hi.z;
+            }
+        }
+        __syncthreads();
+        const SysInfo si = d.sys[w.sys];
+        const int64_t base = si.slot0 + (int64_t)w.chunk * si.cap - si.off;
+        // the first i-tile's positions and box
+        float px[NI], py[NI], pz[NI];
+        float4 pb[2];
 #pragma unroll
         for (int q = 0; q < NI; q++) {
-            ii[q] = d.csorted[w.i0 + q * T + threadIdx.x];
-            const float4 h = d.kh[ii[q]];
-            xi[q] = h.x; yi[q] = h.y; zi[q] = h.z;
-            rci[q] = d.rcf[ii[q]];
-            li[q] = d.kl[ii[q]];
-            float t = 2.0f * (rci[q] + rcm);
-            thr[q] = fmaxf(t * t, 1e-30f);
-            if (h.x < 0.5f * kFar) tmax = fmaxf(tmax, thr[q]);
-            box_add(h, ihave, ibl, ibh);
-            hx[q] = hy[q] = hz[q] = lx[q] = ly[q] = lz[q] = 0.0f;
+            const int64_t p = w.i0 + q * T + threadIdx.x;
+            px[q] = d.ks_x[p];
+            py[q] = d.ks_y[p];
+            pz[q] = d.ks_z[p];
         }
-        // box of the i-tile and its largest threshold (>= 0: its bits order as its values)
-        float ilo[3], ihi[3];
-        __syncthreads();
-        {
-            const int tm = __reduce_max_sync(0xffffffffu, __float_as_int(tmax));
-            if ((threadIdx.x & 31) == 0) red_t[threadIdx.x >> 5] = tm;
-        }
-        block_box<T>(ihave, ibl, ibh, red, ilo, ihi);
-        {
-            int t_all = red_t[0];
-#pragma unroll
-            for (int wq = 1; wq < T / 32; wq++) t_all = max(t_all, red_t[wq]);
-            tmax = __int_as_float(t_all) * 1.001f;
-        }
-        // j records: with few per thread, each tile's are fetched while the
-        // previous tile runs (PF); otherwise at the start of the tile
-        constexpr bool PF = JPT <= 2;
-        int pid[JPT];
-        float4 ph[JPT];
-        if (PF) {
-#pragma unroll
-            for (int u = 0; u < JPT; u++) {
-                const int64_t k = (int64_t)u * T + threadIdx.x;
-                pid[u] = w.j0 + k < w.j1 ? d.csorted[w.j0 + k] : -1;
-            }
-#pragma unroll
-            for (int u = 0; u < JPT; u++) ph[u] = pid[u] >= 0 ? d.kh[pid[u]] : make_float4(kFar, kFar, kFar, 0.0f);
-        }
-        for (int64_t jb = w.j0; jb < w.j1; jb += kJTile) {
-            const int nj = (int)min((int64_t)kJTile, w.j1 - jb);
-            __syncthreads();
-            if (!PF) {
-#pragma unroll
-                for (int u = 0; u < JPT; u++) {
-                    const int64_t k = jb + (int64_t)u * T + threadIdx.x;
-                    pid[u] = k < w.j1 ? d.csorted[k] : -1;
-                }
-#pragma unroll
-                for (int u = 0; u < JPT; u++)
-                    ph[u] = pid[u] >= 0 ? d.kh[pid[u]] : make_float4(kFar, kFar, kFar, 0.0f);
-            }
-            bool have = false;
-            float bl[3] = {3.0e38f, 3.0e38f, 3.0e38f}, bh[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-            int cid[JPT];
-#pragma unroll
-            for (int u = 0; u < JPT; u++) {
-                const int k = u * T + threadIdx.x;
-                cid[u] = pid[u];
-                if (k < nj) {
-                    sj[k] = ph[u];
-                    sid[k] = pid[u];
-                    box_add(ph[u], have, bl, bh);
-                }
-            }
-            if (PF) {   // the next tile's records; their latency hides behind this tile
-                const int64_t jn = jb + kJTile;
-#pragma unroll
-                for (int u = 0; u < JPT; u++) {
-                    const int64_t k = jn + (int64_t)u * T + threadIdx.x;
-                    pid[u] = k < w.j1 ? d.csorted[k] : -1;
-                }
-#pragma unroll
-                for (int u = 0; u < JPT; u++)
-                    ph[u] = pid[u] >= 0 ? d.kh[pid[u]] : make_float4(kFar, kFar, kFar, 0.0f);
-            }
-            float jlo[3], jhi[3];
-            block_box<T>(have, bl, bh, red, jlo, jhi);
-            // squared gap between the boxes (huge when either is empty)
-            float g2 = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const float g = fmaxf(0.0f, fmaxf(jlo[k] - ihi[k], ilo[k] - jhi[k]));
-                g2 = fmaf(g, g, g2);
-            }
-            float tx[NI], ty[NI], tz[NI];
-#pragma unroll
-            for (int q = 0; q < NI; q++) tx[q] = ty[q] = tz[q] = 0.0f;
-            if (g2 < tmax) {   // block-uniform: stage what the slow path needs
-#pragma unroll
-                for (int u = 0; u < JPT; u++) {
-                    const int k = u * T + threadIdx.x;
-                    if (k < nj) {
-                        sl[k] = d.kl[cid[u]];
-                        src[k] = d.rcf[cid[u]];
-                    }
-                }
-                __syncthreads();
-                if (nj == kJTile)
-                    kick_tile<NI, true, kJTile>(sj, sl, src, nj, xi, yi, zi, thr, rci, li, form, tx, ty, tz);
-                else
-                    kick_tile<NI, true, 0>(sj, sl, src, nj, xi, yi, zi, thr, rci, li, form, tx, ty, tz);
-            } else if (nj == kJTile) {
-                kick_tile<NI, false, kJTile>(sj, sl, src, nj, xi, yi, zi, thr, rci, li, form, tx, ty, tz);
-            } else {
-                kick_tile<NI, false, 0>(sj, sl, src, nj, xi, yi, zi, thr, rci, li, form, tx, ty, tz);
-            }
+        pb[0] = ibox[2 * (w.i0 / IT)];
+        pb[1] = ibox[2 * (w.i0 / IT) + 1];
+        for (int64_t ib = w.i0; ib < w.i1; ib += w.istep) {
+            float2 nx[NI], ny[NI], nz[NI];
 #pragma unroll
             for (int q = 0; q < NI; q++) {
-                fold(hx[q], lx[q], tx[q]);
-                fold(hy[q], ly[q], ty[q]);
-                fold(hz[q], lz[q], tz[q]);
+                nx[q] = make_float2(-px[q], -px[q]);
+                ny[q] = make_float2(-py[q], -py[q]);
+                nz[q] = make_float2(-pz[q], -pz[q]);
             }
-        }
+            // near test of this i-tile against the j-tile (block-uniform)
+            bool near;
+            {
+                const float lo[3] = {pb[0].x, pb[0].y, pb[0].z}, hi[3] = {pb[1].x, pb[1].y, pb[1].z};
+                float g2 = 0.0f;
 #pragma unroll
-        for (int q = 0; q < NI; q++) {
-            int64_t slot = si.slot0 + (int64_t)w.chunk * si.cap + (ii[q] - si.off);
-            d.pacc_x[slot] = (double)hx[q] + (double)lx[q];
-            d.pacc_y[slot] = (double)hy[q] + (double)ly[q];
-            d.pacc_z[slot] = (double)hz[q] + (double)lz[q];
+                for (int k = 0; k < 3; k++) {
+                    const float g = fmaxf(0.0f, fmaxf(s_jbox[k] - hi[k], lo[k] - s_jbox[3 + k]));
+                    g2 = fmaf(g, g, g2);
+                }
+                near = g2 < pb[0].w * 1.001f;
+            }
+            // the next i-tile's positions and box, in flight during this one
+            const int64_t nb0 = ib + w.istep < w.i1 ? ib + w.istep : ib;
+#pragma unroll
+            for (int q = 0; q < NI; q++) {
+                const int64_t p = nb0 + q * T + threadIdx.x;
+                px[q] = d.ks_x[p];
+                py[q] = d.ks_y[p];
+                pz[q] = d.ks_z[p];
+            }
+            pb[0] = ibox[2 * (nb0 / IT)];
+            pb[1] = ibox[2 * (nb0 / IT) + 1];
+            float2 ax[NI], ay[NI], az[NI];
+#pragma unroll
+            for (int q = 0; q < NI; q++) ax[q] = ay[q] = az[q] = make_float2(0.0f, 0.0f);
+            if (near) near_tile<T, NI>(d, ib, rcm, sx, sy, sz, sm, sl, src, s_near, nx, ny, nz, form, ax, ay, az);
+            else far_tile<NI>(sx, sy, sz, sm, nx, ny, nz, ax, ay, az);
+            // partial rows by sorted position (coalesced); k_close reads them through cpos
+#pragma unroll
+            for (int q = 0; q < NI; q++) {
+                const int64_t slot = base + ib + q * T + threadIdx.x;
+                d.pacc_x[slot] = (double)ax[q].x + (double)ax[q].y;
+                d.pacc_y[slot] = (double)ay[q].x + (double)ay[q].y;
+                d.pacc_z[slot] = (double)az[q].x + (double)az[q].y;
+            }
         }
     }
     queue_done(d);
@@ -328,7 +441,8 @@ __global__ void __launch_bounds__(T) k_kick_fp64(Dev d, const KickItem* __restri
         const KickItem w = items[it];
         const SysInfo si = d.sys[w.sys];
         const double rcm = (double)d.rcmax[w.sys];
-        const int64_t i = w.i0 + threadIdx.x;
+        for (int64_t ib = w.i0; ib < w.i1; ib += w.istep) {
+        const int64_t i = ib + threadIdx.x;
         const double xi = d.x[i], yi = d.y[i], zi = d.z[i], rci = d.rc[i];
         double t = 2.0 * (rci + rcm);
         const double thr = fmax(t * t, 1e-300);
@@ -362,6 +476,7 @@ __global__ void __launch_bounds__(T) k_kick_fp64(Dev d, const KickItem* __restri
         d.pacc_x[slot] = ax;
         d.pacc_y[slot] = ay;
         d.pacc_z[slot] = az;
+        }
     }
     queue_done(d);
 }
@@ -370,9 +485,11 @@ __global__ void __launch_bounds__(T) k_kick_fp64(Dev d, const KickItem* __restri
 // After the encounter integrator.  k_kick_apply puts each member's BS result
 // into the state, keeping the old float copies and position.  When the kick
 // ran beside the BS (overlap), on the state after the drift, its partial rows
-// hold every group member at its old place, and k_kick_fix then
+// leave the group members out as sources (k_group_place set their mass to 0
+// in the kick's float copy; overlap runs in the mixed form only), and
+// k_kick_fix then
 //   - recomputes the full row of each member at its new place,
-//   - for every other body swaps the members' old terms for their new ones,
+//   - adds the members' new terms to every other body's row,
 //   - sums m V per 64-body segment for the closing jump (after the mergers;
 //     this part runs in both orders).
 // A pair's term is computed exactly as the kick computes it: the slow path
@@ -657,11 +774,13 @@ void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s) {
 }
 
 // Kick variants the autotuner picks from: (threads, i-bodies per thread,
-// minimum resident blocks); every variant covers a 128-body i-tile.
+// minimum resident blocks); an item's i-tile is threads x i-bodies (128 or
+// 256 bodies, a divisor of the system padding).
 struct KickVariant {
     const char* name;
     int threads;
     int ni;           // i-bodies per thread: an item's i-tile is threads x ni bodies
+    bool jmajor;      // items: a j-tile against a run of i-tiles (else an i-tile against a j-chunk)
     void (*launch)(const Dev&, const KickItem*, int64_t, int, cudaStream_t);
     int (*occupancy)();
     int (*regs)();
@@ -701,20 +820,21 @@ int occ_fp64() {
 }
 
 static const KickVariant kMixed[] = {
-    {"mixed t128 i1", 128, 1, launch_mixed<128, 1, 6>, occ_mixed<128, 1, 6>, regs_mixed<128, 1, 6>},
-    {"mixed t64 i2", 64, 2, launch_mixed<64, 2, 12>, occ_mixed<64, 2, 12>, regs_mixed<64, 2, 12>},
-    {"mixed t128 i2", 128, 2, launch_mixed<128, 2, 4>, occ_mixed<128, 2, 4>, regs_mixed<128, 2, 4>},
-    {"mixed t128 i1 r", 128, 1, launch_mixed<128, 1, 4>, occ_mixed<128, 1, 4>, regs_mixed<128, 1, 4>},
-    {"mixed t128 i1 5", 128, 1, launch_mixed<128, 1, 5>, occ_mixed<128, 1, 5>, regs_mixed<128, 1, 5>},
+    {"mixed t128 i1", 128, 1, true, launch_mixed<128, 1, 7>, occ_mixed<128, 1, 7>, regs_mixed<128, 1, 7>},
+    {"mixed t128 i1 6", 128, 1, true, launch_mixed<128, 1, 6>, occ_mixed<128, 1, 6>, regs_mixed<128, 1, 6>},
+    {"mixed t128 i1 8", 128, 1, true, launch_mixed<128, 1, 8>, occ_mixed<128, 1, 8>, regs_mixed<128, 1, 8>},
+    {"mixed t64 i2", 64, 2, true, launch_mixed<64, 2, 8>, occ_mixed<64, 2, 8>, regs_mixed<64, 2, 8>},
+    {"mixed t128 i2", 128, 2, true, launch_mixed<128, 2, 5>, occ_mixed<128, 2, 5>, regs_mixed<128, 2, 5>},
 };
 static const KickVariant kFp64[] = {
-    {"fp64 t128", 128, 1, launch_fp64<128>, occ_fp64<128>, regs_fp64<128>},
+    {"fp64 t128", 128, 1, false, launch_fp64<128>, occ_fp64<128>, regs_fp64<128>},
 };
 
 int kick_num_variants(int precision) {
     return precision == 1 ? (int)(sizeof(kMixed) / sizeof(kMixed[0])) : (int)(sizeof(kFp64) / sizeof(kFp64[0]));
 }
 const char* kick_variant_name(int precision, int v) { return precision == 1 ? kMixed[v].name : kFp64[v].name; }
+bool kick_jmajor(int precision, int v) { return precision == 1 ? kMixed[v].jmajor : kFp64[v].jmajor; }
 int kick_itile(int precision, int v) {
     const KickVariant& k = precision == 1 ? kMixed[v] : kFp64[v];
     return k.threads * k.ni;
@@ -732,6 +852,12 @@ void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, 
     if (precision == 1) kMixed[v].launch(d, items, nitems, grid, s);
     else kFp64[v].launch(d, items, nitems, grid, s);
     prof_mark("kick");
+}
+
+void launch_kick_stage(const Dev& d, int precision, cudaStream_t s) {
+    if (precision != 1) return;   // the FP64 kick reads the state itself
+    k_kick_stage<<<(unsigned)(d.ntot / (2 * kKickBox)), 2 * kKickBox, 0, s>>>(d);
+    prof_mark("kick: sorted copies and tile boxes");
 }
 
 }  // namespace opal

@@ -88,6 +88,7 @@ struct opal_sim {
     int kick_variant = 0;
     char kick_desc[256] = {0};
     int time_kick = 0;                       // graph records events around the kick
+    cudaError_t launch_err = cudaSuccess;    // the first failed cluster or cooperative launch of a capture
     int64_t last_involved = 0;               // bodies in encounters in the last step
     int64_t last_inv_big = 0;                // of them big bodies (sources of force)
     int64_t n_big = 0;                       // big bodies of all systems
@@ -143,22 +144,73 @@ bool finite_all(const double* a, int64_t n) {
     return true;
 }
 
-// The kick's work list: i-tiles of itile bodies against j-chunks of the system's
-// first nb places (its big bodies), chunk edges on whole j-tiles.  The kick takes items from a
-// queue, largest first; about eight items per resident block keep the tail
-// short.  Chunks of one system are of equal length to within a tile.
-void build_kick_items(opal_sim* s, int slots, int itile) {
+// The kick's work list.  Only a system's first nb places (its big bodies)
+// are sources: j runs over them (small bodies follow them, in storage and in
+// the sorted order alike); i runs over all cap places.  Items are taken from
+// a queue, largest first.
+//  - i-major (jmajor false): an i-tile of itile bodies against a j-chunk,
+//    chunk edges on whole j-tiles, about eight items per resident block;
+//    the chunk's partial row.
+//  - j-major: one j-tile (staged once) against a run of i-tiles; the j-tile
+//    index is the partial row.  The (i-tile, j-tile) units are grouped into
+//    runs of 4 while more than three resident blocks' worth of units
+//    remain, then of 2 while more than one remains, then single units, so
+//    that the queue ends on the smallest items.
+void build_kick_items(opal_sim* s, int slots, int itile, bool jmajor) {
     double work = 0;
     for (auto& si : s->sys) work += (double)si.cap * (double)si.nb;
     const double target = std::max(1.0, work / (8.0 * std::max(1, slots)));
     s->items.clear();
-    int64_t slot = 0;
+    int64_t slot = 0, units = 0;
+    for (auto& si : s->sys) units += (si.cap / itile) * ((si.nb + kKickJTile - 1) / kKickJTile);
+    int64_t left = units;
     for (size_t k = 0; k < s->sys.size(); k++) {
         SysInfo& si = s->sys[k];
         const int64_t itiles = si.cap / itile;
-        // only the big bodies are sources: j runs over the first nb (small bodies
-        // follow them, in storage and in the sorted order alike)
         const int64_t jtiles = (si.nb + kKickJTile - 1) / kKickJTile;
+        if (jmajor) {
+            si.nchunk = (int32_t)std::max<int64_t>(1, jtiles);
+            si.slot0 = slot;
+            slot += (int64_t)si.nchunk * si.cap;
+            for (int64_t t = 0; t < jtiles; t++) {
+                const int64_t j0 = si.off + t * kKickJTile, j1 = si.off + std::min(si.nb, (t + 1) * kKickJTile);
+                for (int64_t a = 0; a < itiles;) {
+                    int64_t run = left > 3 * (int64_t)slots ? 4 : (left > slots ? 2 : 1);
+                    run = std::min(run, itiles - a);
+                    // the run's i-tiles a + u * S (u < run) for a block of run * S tiles,
+                    // S = the block's stride: spatial neighbours go to different items
+                    const int64_t span = std::min(itiles - a, (itiles - a) / run * run);
+                    const int64_t S = std::max<int64_t>(1, span / run);
+                    for (int64_t b = 0; b < S; b++) {
+                        KickItem it{};
+                        it.sys = (int32_t)k;
+                        it.chunk = (int32_t)t;
+                        it.i0 = si.off + (a + b) * itile;
+                        it.istep = S * itile;
+                        it.i1 = it.i0 + run * S * itile;
+                        it.j0 = j0;
+                        it.j1 = j1;
+                        s->items.push_back(it);
+                        left -= run;
+                    }
+                    a += run * S;
+                }
+            }
+            if (jtiles == 0) {
+                // no sources: one empty item per i-tile still writes the zero partial row
+                for (int64_t a = 0; a < itiles; a++) {
+                    KickItem it{};
+                    it.sys = (int32_t)k;
+                    it.chunk = 0;
+                    it.i0 = si.off + a * itile;
+                    it.i1 = it.i0 + itile;
+                    it.istep = itile;
+                    it.j0 = it.j1 = si.off;
+                    s->items.push_back(it);
+                }
+            }
+            continue;
+        }
         const double w_tile = (double)itile * (double)si.nb;
         int64_t nchunk = (int64_t)std::llround(w_tile / target);
         nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, jtiles));
@@ -173,14 +225,17 @@ void build_kick_items(opal_sim* s, int slots, int itile) {
                 it.sys = (int32_t)k;
                 it.chunk = (int32_t)c;
                 it.i0 = si.off + t * itile;
+                it.i1 = it.i0 + itile;
+                it.istep = itile;
                 it.j0 = j0;
                 it.j1 = j1;
                 s->items.push_back(it);
             }
         }
     }
-    std::stable_sort(s->items.begin(), s->items.end(),
-                     [](const KickItem& a, const KickItem& b) { return (a.j1 - a.j0) > (b.j1 - b.j0); });
+    std::stable_sort(s->items.begin(), s->items.end(), [](const KickItem& a, const KickItem& b) {
+        return (a.i1 - a.i0) * (a.j1 - a.j0) > (b.i1 - b.i0) * (b.j1 - b.j0);
+    });
 }
 
 void build_pair_tiles(opal_sim* s) {
@@ -330,6 +385,8 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     Dev& d = s->d;
     d.ntot = N;
     d.nsys = nsys;
+    d.huge_wait_ns = kHugeWaitNs;
+    d.huge_hold = 0;
     d.nseg_tot = N / kSeg;
     // kick variants: the work list of each, and the largest partial buffer any needs
     const int nvar = kick_num_variants(p->precision);
@@ -339,7 +396,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     int64_t max_slots = 0;
     for (int v = 0; v < nvar; v++) {
         int occ = std::max(1, kick_occupancy(p->precision, v));
-        build_kick_items(s, s->nsm * occ, kick_itile(p->precision, v));
+        build_kick_items(s, s->nsm * occ, kick_itile(p->precision, v), kick_jmajor(p->precision, v));
         var_items[v] = s->items;
         var_sys[v] = s->sys;
         var_grid[v] = (int)std::min<int64_t>((int64_t)s->items.size(), (int64_t)s->nsm * occ);
@@ -364,12 +421,18 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     float4** f4[] = {&d.kh, &d.kl, &d.cen, &d.sc0, &d.sc1, &d.sv0, &d.sv1};
     for (auto pp : f4) TRYF(dalloc(s, pp, N));
     TRYF(dalloc(s, &d.rcf, N));
+    float** ksf[] = {&d.ks_x, &d.ks_y, &d.ks_z, &d.ks_m, &d.ks_rc};
+    for (auto pp : ksf) TRYF(dalloc(s, pp, N));
+    TRYF(dalloc(s, &d.ks_lo, N));
+    TRYF(dalloc(s, &d.kbox, 2 * (N / kKickBox)));
+    TRYF(dalloc(s, &d.kbox2, 2 * (N / (2 * kKickBox))));
     d.ncell = (int)(N / kBucketDiv);
     TRYF(dalloc(s, &d.sbox, 6 * nsys));
     TRYF(dalloc(s, &d.ckey, N));
     TRYF(dalloc(s, &d.cstart, d.ncell));
     TRYF(dalloc(s, &d.ccursor, d.ncell));
     TRYF(dalloc(s, &d.csorted, N));
+    TRYF(dalloc(s, &d.cpos, N));
     TRYF(dalloc(s, &d.cscratch, N));
     TRYF(dalloc(s, &d.cen_sorted, N));
     TRYF(dalloc(s, &d.tbox, 6 * (N / kSeg)));
@@ -524,6 +587,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         if (force) {
             best = std::max(0, std::min(nvar - 1, atoi(force)));
         } else if (nvar > 1 && work >= 4.0e6) {
+            launch_kick_stage(d, P.precision, s->stream);
             cudaEvent_t e0, e1;
             CKF(cudaEventCreate(&e0));
             CKF(cudaEventCreate(&e1));
@@ -571,6 +635,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         CKF(up(d.sys, s->sys.data(), nsys * sizeof(SysInfo)));
         CKF(up(s->d_items, s->items.data(), s->items.size() * sizeof(KickItem)));
     }
+    launch_kick_stage(d, P.precision, s->stream);
     launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, P.precision, s->kick_variant, s->stream);
     launch_first_accel_finish(d, s->stream);
     CKF(cudaGetLastError());
@@ -605,6 +670,11 @@ constexpr int kNumKernels = 13;
 constexpr int kStageReprime = 11, kStageRemove = 12;
 constexpr int kStageBs = 5, kStageKick = 6, kStageApply = 7;
 
+// keep the first error of a cluster or cooperative launch, for the capture to report
+void note_launch(opal_sim* s, cudaError_t e) {
+    if (e != cudaSuccess && s->launch_err == cudaSuccess) s->launch_err = e;
+}
+
 // stage k of a step on stream st
 void launch_stage(opal_sim* s, int k, cudaStream_t st) {
     const Dev& d = s->d;
@@ -617,10 +687,15 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
         case kStageBs:
             // the lockstep kernels on parallel branches (one stream when profiling)
             launch_bs_packed(d, s->nsm, st);
-            launch_bs_lockstep(d, s->nsm, st, g_prof ? st : s->side2, s->fork2_ev, s->join2_ev, false);
+            note_launch(s, launch_bs_lockstep(d, s->nsm, st, g_prof ? st : s->side2, s->fork2_ev, s->join2_ev,
+                                              false));
             break;
         case kStageKick:
+            // the timing events (when on) bracket the kick kernel alone, not its staging
+            launch_kick_stage(d, d.p.precision, st);
+            if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[0], st, cudaEventRecordExternal);
             launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
+            if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[1], st, cudaEventRecordExternal);
             break;
         case kStageApply: launch_bs_apply(d, s->nsm, st); break;
         case 8: launch_kick_fix(d, s->nsm, st); break;
@@ -632,6 +707,7 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
             Dev g = d;
             g.gated = 1;
             launch_prime(g, st);
+            launch_kick_stage(g, d.p.precision, st);
             launch_kick(g, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
             launch_first_accel_finish(g, st);
             prof_mark("accelerations afresh after a removal");
@@ -673,6 +749,7 @@ opal_status capture_graph(opal_sim* s) {
     }
     int order[kNumKernels];
     const int ns = stage_order(s, order);
+    s->launch_err = cudaSuccess;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     for (int q = 0; q < ns; q++) {
         const int k = order[q];
@@ -684,19 +761,24 @@ opal_status capture_graph(opal_sim* s) {
             launch_bs_packed(s->d, s->nsm, s->stream);
             CK(cudaEventRecord(s->fork_ev, s->stream));
             CK(cudaStreamWaitEvent(s->side, s->fork_ev, 0));
-            if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[0], s->side, cudaEventRecordExternal);
             launch_stage(s, kStageKick, s->side);
-            if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[1], s->side, cudaEventRecordExternal);
             CK(cudaEventRecord(s->join_ev, s->side));
-            launch_bs_lockstep(s->d, s->nsm, s->stream, s->side3, s->fork2_ev, s->join2_ev, true);
+            note_launch(s, launch_bs_lockstep(s->d, s->nsm, s->stream, s->side3, s->fork2_ev, s->join2_ev, true));
             CK(cudaStreamWaitEvent(s->stream, s->join_ev, 0));
             continue;
         }
-        if (s->time_kick && k == kStageKick) cudaEventRecordWithFlags(s->kick_ev[0], s->stream, cudaEventRecordExternal);
         launch_stage(s, k);
-        if (s->time_kick && k == kStageKick) cudaEventRecordWithFlags(s->kick_ev[1], s->stream, cudaEventRecordExternal);
     }
     cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
+    if (s->launch_err != cudaSuccess) {
+        set_err(s->err, "launch of an encounter kernel (cluster of four blocks, or the cooperative whole-GPU "
+                        "kernel) refused: %s", cudaGetErrorString(s->launch_err));
+        if (s->graph) {
+            cudaGraphDestroy(s->graph);
+            s->graph = nullptr;
+        }
+        return OPAL_ECUDA;
+    }
     if (e != cudaSuccess) {
         set_err(s->err, "graph capture failed: %s", cudaGetErrorString(e));
         return OPAL_ECUDA;
@@ -717,6 +799,12 @@ opal_status choose_mode(opal_sim* s) {
     if (share < 0.03) want = 1;
     else if (share > 0.08) want = 0;
     if (s->d.p.precision == 0) want = 0;
+    // OPAL_STEP_ORDER=overlap or inorder forces one (the mixed form; the FP64 form is always in order)
+    const char* force = getenv("OPAL_STEP_ORDER");
+    if (force && s->d.p.precision == 1) {
+        if (!strcmp(force, "overlap")) want = 1;
+        else if (!strcmp(force, "inorder")) want = 0;
+    }
     if (want == s->d.overlap && s->exec) return OPAL_OK;
     s->d.overlap = want;
     return capture_graph(s);
@@ -730,8 +818,12 @@ opal_status finish_steps(opal_sim* s, int64_t before) {
     s->last_involved = c.ninvolved;
     s->last_inv_big = c.ninv_big;
     if (c.status) {
-        set_err(s->err, "step %lld: %s (detail %d)", (long long)(c.steps_done + 1), status_name(c.status),
-                c.detail);
+        if (c.status == kEbs && c.detail >= kHugeAbortDetail)
+            set_err(s->err, "step %lld: whole-GPU encounter kernel: a grid-barrier wait ran out (detail %d)",
+                    (long long)(c.steps_done + 1), c.detail);
+        else
+            set_err(s->err, "step %lld: %s (detail %d)", (long long)(c.steps_done + 1), status_name(c.status),
+                    c.detail);
         int zero[2] = {0, 0};
         CK(cudaMemcpy(s->d.ctl, zero, sizeof(zero), cudaMemcpyHostToDevice));
         return (opal_status)c.status;
@@ -961,6 +1053,30 @@ double opal_last_kick_ms(const opal_sim* cs) {
     return ms;
 }
 
+opal_status opal_time_kick_alone(opal_sim* s, int32_t reps, double* ms) {
+    if (!s || !ms) return set_err(g_err, "NULL argument"), OPAL_EINVAL;
+    if (reps < 1) return set_err(s->err, "reps < 1"), OPAL_EINVAL;
+    const Dev& d = s->d;
+    CK(cudaStreamSynchronize(s->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int64_t ni = (int64_t)s->items.size();
+    launch_kick(d, s->d_items, ni, s->kick_grid, d.p.precision, s->kick_variant, s->stream);
+    cudaEventRecord(e0, s->stream);
+    for (int32_t r = 0; r < reps; r++)
+        launch_kick(d, s->d_items, ni, s->kick_grid, d.p.precision, s->kick_variant, s->stream);
+    cudaEventRecord(e1, s->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return set_err(s->err, "kick timing failed: %s", cudaGetErrorString(e)), OPAL_ECUDA;
+    *ms = (double)t / reps;
+    return OPAL_OK;
+}
+
 void opal_destroy(opal_sim* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
@@ -1005,6 +1121,7 @@ opal_status opal_debug_accel(opal_sim* s, const double* rc, double* a) {
     reset_scan_order(s);
     launch_debug_scan_prep(d, s->stream);
     launch_sort_bodies(d, s->stream);
+    launch_kick_stage(d, d.p.precision, s->stream);
     launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, s->stream);
     launch_first_accel_finish(d, s->stream);
     CK(cudaGetLastError());
@@ -1117,6 +1234,15 @@ opal_status opal_debug_scan(opal_sim* s, const double* x0, const double* V0, con
     return OPAL_OK;
 }
 
+opal_status opal_debug_barrier(opal_sim* s, int64_t wait_ns, int32_t hold) {
+    if (!s) return set_err(g_err, "NULL simulation"), OPAL_EINVAL;
+    if (wait_ns < 0 || (hold != 0 && hold != 1))
+        return set_err(s->err, "wait_ns must be >= 0 and hold 0 or 1"), OPAL_EINVAL;
+    s->d.huge_wait_ns = wait_ns > 0 ? wait_ns : kHugeWaitNs;
+    s->d.huge_hold = hold;
+    return capture_graph(s);
+}
+
 opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0, const double* rc, double* x,
                                 double* V, double* m, double* radius, int32_t* alive, double* E_lost,
                                 int64_t* substeps) {
@@ -1156,7 +1282,7 @@ opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0,
     CK(cudaMemsetAsync(d.mlo, 0x7f, d.nsys * sizeof(int), s->stream));
     CK(cudaMemsetAsync(d.mhi, 0, d.nsys * sizeof(int), s->stream));
     launch_bs_packed(d, s->nsm, s->stream);
-    launch_bs_lockstep(d, s->nsm, s->stream, s->stream, nullptr, nullptr, false);
+    CK(launch_bs_lockstep(d, s->nsm, s->stream, s->stream, nullptr, nullptr, false));
     launch_bs_apply(d, s->nsm, s->stream);   // puts the result into the state
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));

@@ -17,7 +17,10 @@ constexpr int kPad = 256;        // body padding of every system (largest kick i
 constexpr int kSeg = 64;         // bodies per partial-sum segment
 constexpr int kBodyThreads = 128;
 constexpr int kBsMaxMembers = 64;   // bodies per encounter group of the lockstep kernels
-constexpr int kKickJTile = 256;     // j-bodies the kick stages in shared memory at a time
+constexpr int64_t kHugeWaitNs = 4000000000;   // the whole-GPU encounter kernel's barrier wait limit (4 s)
+constexpr int kHugeAbortDetail = 2999999;      // status detail of its barrier aborts: this, or this + 1 + group
+constexpr int kKickJTile = 256;
+constexpr int kKickBox = 128;      // positions per tile box of the kick's sorted copies     // j-bodies the kick stages in shared memory at a time
 constexpr int kBsManyGroups = 608;  // above this many groups a step integrates them packed, lane per member
 constexpr int kBucketDiv = 4;       // body slots per bucket of the spatial sort (cap / 4 buckets a system)
 constexpr int kBsOut = 9;           // doubles per member slot of the BS side buffer: x, V, m, R, alive
@@ -120,9 +123,10 @@ struct SysInfo {
 // One unit of kick work: an i-tile against a j-range of the same system.
 struct KickItem {
     int32_t sys;
-    int32_t chunk;    // index of the j-range within the system
-    int64_t i0;       // first body of the i-tile (global)
-    int64_t j0, j1;   // j-range (global, half-open)
+    int32_t chunk;    // index of the j-range within the system (the partial row it writes)
+    int64_t i0, i1;   // i-tiles at i0, i0 + istep, ... below i1 (global sorted positions)
+    int64_t istep;
+    int64_t j0, j1;   // j-range (global sorted positions, half-open)
 };
 
 // One unit of scan / energy work: an i-tile against a j-tile at or above it.
@@ -147,6 +151,8 @@ struct Dev {
     int nsys;
     int overlap;       // 1: the kick runs beside the BS and is fixed afterwards; 0: after it
     int gated;         // the launch belongs to the re-evaluation after a removal: run only if one happened
+    int huge_hold;     // test hook: the whole-GPU encounter kernel's barriers never release (waits run out)
+    int64_t huge_wait_ns;   // limit of one wait at that kernel's grid barriers (default 4 s)
     Params p;
     double* M0s;       // [nsys] the star's mass of each system (it grows by what it accretes)
     int* accf;         // [ntot] the body's drift passed within the star's radius this step
@@ -164,6 +170,16 @@ struct Dev {
     float4* kl;    // (x_lo, y_lo, z_lo, max(4 rc^2, tiny))
     float* rcf;    // rc as float (rounded up)
     float* rcmax;  // per system: largest rc of the step (rounded up)
+    // the kick's copies in the scan's spatial order (position p holds body
+    // csorted[p]), written before each kick: hi parts and mass as separate
+    // arrays, lo parts with 4 rc^2, rc; and per 128-position tile its box
+    // of live positions and largest near threshold (two float4: lo xyz +
+    // threshold, hi xyz)
+    float *ks_x, *ks_y, *ks_z, *ks_m;
+    float4* ks_lo;
+    float* ks_rc;
+    float4* kbox;    // per 128 positions
+    float4* kbox2;   // per 256 positions
     float4* cen;   // (c_hi, s): midpoint of the body's path over the step and the radius
                    // s bounding the path's distance from it (plus rc and margins)
     float4* sc0;   // (x0_hi, y0_hi, z0_hi, s)
@@ -185,6 +201,7 @@ struct Dev {
     int* ccursor;                       // [ncell] scatter cursors
     int2* cscratch;                     // (body, bucket or -1 if dead) after the scatter, any order in a bucket
     int* csorted;                       // bodies in sorted order, ascending ids within a cell
+    int* cpos;                          // its inverse: the sorted position of each body
     float4* cen_sorted;                 // their midpoint records, in sorted order
     float* tbox;                        // [ntot / 64][6] tile boxes of c +- s
     int ncell;                          // buckets: one per kBucketDiv body slots
@@ -548,12 +565,12 @@ void launch_confirm(const Dev& d, int grid, cudaStream_t s);
 void launch_group(const Dev& d, int nsm, cudaStream_t s);
 cudaError_t bs_setup();   // dynamic shared memory of the BS kernels
 void launch_bs_packed(const Dev& d, int nsm, cudaStream_t s);
-void launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join,
+cudaError_t launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join,
                         bool small_first);
 void launch_kick(const Dev& d, const KickItem* items, int64_t nitems, int grid, int precision, int variant,
                  cudaStream_t s);
 // after the BS: apply its results; fix the kick's rows when it ran beside the BS
-void launch_bs_huge(const Dev& d, int nsm, cudaStream_t s);
+cudaError_t launch_bs_huge(const Dev& d, int nsm, cudaStream_t s);
 void launch_bs_apply(const Dev& d, int nsm, cudaStream_t s);
 void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s);
 int kick_num_variants(int precision);
@@ -562,7 +579,9 @@ int kick_occupancy(int precision, int variant);
 int kick_block_regs(int precision, int variant);   // registers one block of variant v holds
 int kick_threads(int precision, int variant);      // threads a block of variant v
 int bs_block_regs();
-int kick_itile(int precision, int variant);   // i-bodies per work item (a divisor of kPad)
+int kick_itile(int precision, int variant);   // i-bodies per i-tile (a divisor of kPad)
+bool kick_jmajor(int precision, int variant); // items: one j-tile against a run of i-tiles (else an i-tile against j-tiles)
+void launch_kick_stage(const Dev& d, int precision, cudaStream_t s);   // the sorted copies the mixed kick reads
 void launch_close(const Dev& d, cudaStream_t s);
 void launch_first_accel_finish(const Dev& d, cudaStream_t s);
 void launch_finish(const Dev& d, cudaStream_t s);

@@ -66,6 +66,8 @@ def _declare(L):
     L.opal_time_kick.restype = C.c_int
     L.opal_last_kick_ms.argtypes = [_P]
     L.opal_last_kick_ms.restype = C.c_double
+    L.opal_time_kick_alone.argtypes = [_P, C.c_int32, C.POINTER(C.c_double)]
+    L.opal_time_kick_alone.restype = C.c_int
     L.opal_graph_kernels.argtypes = [_P]
     L.opal_graph_kernels.restype = C.c_int32
     L.opal_kick_config.argtypes = [_P]
@@ -80,11 +82,13 @@ def _declare(L):
                                   C.POINTER(C.c_int64)]
     L.opal_debug_bs_group.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, _I32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]
+    L.opal_debug_barrier.argtypes = [_P, C.c_int64, C.c_int32]
     L.opal_energy_momentum_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, _P, _P, _P, _P, _P]
     L.opal_probe_alu_peaks.argtypes = [_D]
     for name in ("opal_probe_alu_peaks", "opal_create", "opal_ensemble_create", "opal_step", "opal_step_async", "opal_wait", "opal_get_state", "opal_energy_momentum",
                  "opal_last_step_stats", "opal_profile_steps", "opal_debug_accel", "opal_debug_drift",
-                 "opal_debug_scan", "opal_debug_bs_group", "opal_energy_momentum_noalloc", "opal_central_mass"):
+                 "opal_debug_scan", "opal_debug_bs_group", "opal_debug_barrier", "opal_energy_momentum_noalloc",
+                 "opal_central_mass"):
         getattr(L, name).restype = C.c_int
 
 
@@ -251,6 +255,12 @@ class Simulation:
     def last_kick_ms(self) -> float:
         return lib().opal_last_kick_ms(self.ptr)
 
+    def kick_alone_ms(self, reps: int = 10) -> float:
+        """Mean device time of the step's kick kernel launched alone."""
+        ms = C.c_double(0.0)
+        _check(lib().opal_time_kick_alone(self.ptr, int(reps), C.byref(ms)), self.ptr)
+        return ms.value
+
     def profile(self, nsteps: int) -> dict:
         cap = 64
         nk = C.c_int32(0)
@@ -296,6 +306,11 @@ class Simulation:
         st = lib().opal_debug_bs_group(self.ptr, _d(x0, (n, 3)), _d(V0, (n, 3)), _d(rc), x, V, m, radius, alive,
                                        C.byref(El), C.byref(sub))
         return st, dict(x=x, V=V, m=m, R=radius, alive=alive, E_lost=El.value, substeps=sub.value)
+
+    def debug_barrier(self, wait_ns: int = 0, hold: int = 0):
+        """Limit of the whole-GPU encounter kernel's barrier waits (0: the
+        default); hold=1 makes the barriers never release (test hook)."""
+        _check(lib().opal_debug_barrier(self.ptr, int(wait_ns), int(hold)), self.ptr)
 
     def close(self):
         if getattr(self, "_ptr", None) is not None:

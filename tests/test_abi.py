@@ -118,3 +118,8 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     with pytest.raises(opal.OpalError):
         opal.lib()
     importlib.reload(opal)
+
+
+def test_barrier_hook_rejects_a_null_simulation(lib):
+    """The barrier test hook validates on the host: no simulation, no call."""
+    assert lib.lib().opal_debug_barrier(None, 1000, 1) == lib.EINVAL

@@ -2,8 +2,9 @@
 
 opal_energy_momentum_noalloc (device arrays in, nothing allocated, fixed
 scratch in device memory) must give the E, L and P that
-opal_energy_momentum gives for the same state, on two calls in a row.  Both
-go through the C ABI.  The file name sorts last so that the test also runs
+opal_energy_momentum gives for the same state, on two calls in a row, and
+the oracle's energy and momenta of one state.  Both library calls go
+through the C ABI.  The file name sorts last so that the test also runs
 after every other GPU test has used the device.
 
 Tolerances: the two sides sum the same FP64 terms in different orders (and
@@ -70,6 +71,22 @@ def test_noalloc_matches_energy_momentum(opal, name, make, steps):
     _check(second, E, L, P, st)
     # same inputs, same fixed-order sums: the second call repeats the first exactly
     assert np.array_equal(first, second)
+
+
+def test_noalloc_matches_the_oracle_energy(opal):
+    """Once against the oracle itself: the oracle's energy and momenta (its
+    own DH conversion and compensated sums) of the same 1001-body state."""
+    import oracle
+    oracle.build()
+    s = ic.planetesimals_jupiter(6, 1000)
+    with opal.Simulation.from_system(s, precision=0) as sim:
+        sim.step(10)
+        st = sim.state()
+    n = st["m"].size
+    out = _noalloc(opal, n, s.G, s.M0, _dev(st["m"]), _dev(st["x"]), _dev(st["v"]))
+    V = oracle.helio_to_dh(s.M0, st["m"], st["v"])
+    E, L, P = oracle.energy(s.G, s.M0, st["m"], st["x"], V)
+    _check(out, E, L, P, st)
 
 
 def test_noalloc_empty_and_rejections(opal):
