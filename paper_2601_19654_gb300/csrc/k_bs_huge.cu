@@ -53,7 +53,7 @@ __device__ bool huge_sync(HugeCtl* hc, unsigned long long wait_ns, int hold) {
                     atomicExch(&hc->abort, 1);
                     break;
                 }
-                __nanosleep(200);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -62,15 +62,16 @@ __device__ bool huge_sync(HugeCtl* hc, unsigned long long wait_ns, int hold) {
     return *(volatile int*)&hc->abort == 0;
 }
 
-// (1 - K) term of member b against o (as the small-group kernels compute it)
-__device__ __forceinline__ void huge_pair(const Dev& d, const Params& p, int b, int o, double xb, double yb,
-                                          double zb, double& ax, double& ay, double& az) {
+// (1 - K) term of member b against o (as the small-group kernels compute it),
+// at the positions pos ([3][cap]) of one sequence's evaluation point
+__device__ __forceinline__ void huge_pair(const Dev& d, const Params& p, const double* pos, int b, int o, double xb,
+                                          double yb, double zb, double& ax, double& ay, double& az) {
     const HugeBuf& H = d.hb;
     if (le_zero(H.m[o])) return;   // a small body (m = 0): no source
     const int w = gt_nonneg(H.rc[b], H.rc[o]) ? b : o;
     const double rc = H.rc[w];
     const int64_t c = H.cap;
-    const double dx = H.pos[o] - xb, dy = H.pos[c + o] - yb, dz = H.pos[2 * c + o] - zb;
+    const double dx = pos[o] - xb, dy = pos[c + o] - yb, dz = pos[2 * c + o] - zb;
     const double dr2 = dx * dx + dy * dy + dz * dz;
     if (ge_nonneg(dr2, rc * rc)) return;   // 1 - K = 0 at or beyond rc
     const double dri = rsqrt(dr2), dr = dr2 * dri;
@@ -87,27 +88,113 @@ __device__ __forceinline__ void huge_pair(const Dev& d, const Params& p, int b, 
     az += t * dz;
 }
 
-// pair phase: every (member, chunk) slot from the positions in H.pos / H.posf
-__device__ void huge_pairs(const Dev& d, const Params& p, int M, int nch) {
+// Chunk culling.  The pair phase tests a pair in FP32 against
+// lim = max(rc_b, rc_o) + slack_b; a chunk whose box of float positions
+// (with its largest rc) lies farther from member b than max(rc_b, rc_max) +
+// slack_b holds no pair that passes, since FP32 subtraction, squares and sums
+// round monotonically (the factor 1.001 covers a contraction into an FMA).
+// The pair phase skips such a (member, chunk) task and the member phase,
+// taking the same decision from the same values, skips its slot: culled
+// chunks would only add zeros.
+__device__ __forceinline__ bool chunk_culled(float4 pb, float4 blo, float4 bhi) {
+    const float slack = 1e-5f * (1.0f + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
+    const float lim = fmaxf(pb.w, blo.w) + slack;
+    const float gx = fmaxf(0.0f, fmaxf(blo.x - pb.x, pb.x - bhi.x));
+    const float gy = fmaxf(0.0f, fmaxf(blo.y - pb.y, pb.y - bhi.y));
+    const float gz = fmaxf(0.0f, fmaxf(blo.z - pb.z, pb.z - bhi.z));
+    return gx * gx + gy * gy + gz * gz > lim * lim * 1.001f;
+}
+
+// chunk boxes of sequence k for round parity par: two float4 per chunk
+__device__ __forceinline__ float4* huge_cbox(const HugeBuf& H, int par, int k) {
+    const int64_t nch = (H.cap + kHugeChunk - 1) / kHugeChunk;
+    return H.cbox + 2 * (((int64_t)par * kBsRows + k) * nch);
+}
+
+// Box of the float positions held by each 64 consecutive threads of the
+// block (one chunk: two warps), members with have = false left out; the
+// group's first thread writes it to dst (two float4: lo xyz and the largest
+// rc, hi xyz; an empty chunk gets lo = +3e38, hi = -3e38).  Every thread of
+// the block calls it: it synchronises the block.
+__device__ void chunk_box_store(bool have, float4 p, float4* dst, int (*red)[kHugeThreads / 32]) {
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const float c[3] = {p.x, p.y, p.z};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int lo = __reduce_min_sync(0xffffffffu, have ? ford(c[k]) : 0x7fffffff);
+        const int hi = __reduce_max_sync(0xffffffffu, have ? ford(c[k]) : (int)0x80000000);
+        if (lane == 0) {
+            red[k][wq] = lo;
+            red[3 + k][wq] = hi;
+        }
+    }
+    const int wm = __reduce_max_sync(0xffffffffu, have ? __float_as_int(p.w) : 0);   // rc >= 0
+    if (lane == 0) red[6][wq] = wm;
+    __syncthreads();
+    if ((threadIdx.x & 63) == 0 && dst) {
+        int v[7];
+        for (int k = 0; k < 7; k++)
+            v[k] = (k < 3) ? min(red[k][wq], red[k][wq + 1]) : max(red[k][wq], red[k][wq + 1]);
+        if (v[0] == 0x7fffffff) {
+            dst[0] = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
+            dst[1] = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.0f);
+        } else {
+            dst[0] = make_float4(fordinv(v[0]), fordinv(v[1]), fordinv(v[2]), __int_as_float(v[6]));
+            dst[1] = make_float4(fordinv(v[3]), fordinv(v[4]), fordinv(v[5]), 0.0f);
+        }
+    }
+    __syncthreads();
+}
+
+// 2D Morton key of a point quantised to 16 bits an axis
+__device__ __forceinline__ unsigned int spread16(unsigned int v) {
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+// Slots of sequence k: positions, float positions and the pair sums.
+__device__ __forceinline__ const double* huge_pos(const HugeBuf& H, int k) { return H.pos + (int64_t)k * 3 * H.cap; }
+__device__ __forceinline__ double* huge_part(const HugeBuf& H, int k) {
+    return H.part + (int64_t)k * 3 * H.cap * ((H.cap + kHugeChunk - 1) / kHugeChunk);
+}
+
+// pair phase of one round: every (sequence, member, chunk) slot of the nact
+// sequences k0 .. k0 + nact - 1, from their evaluation points and the chunk
+// boxes of round parity par; chunks are runs of 64 members in spatial order
+__device__ void huge_pairs(const Dev& d, const Params& p, int M, int nch, int k0, int nact, int par) {
     const HugeBuf& H = d.hb;
     const int64_t c = H.cap;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = gw; w < (int64_t)M * nch; w += nw) {
-        const int b = (int)(w / nch), ch = (int)(w % nch);
+    const int64_t per = (int64_t)M * nch;
+    for (int64_t w = gw; w < nact * per; w += nw) {
+        const int k = k0 + (int)(w / per);
+        const int64_t r = w % per;
+        const int b = (int)(r / nch), ch = (int)(r % nch);
+        const double* pos = huge_pos(H, k);
+        const float4* posf = H.posf + (int64_t)k * c;
+        if (!H.alive[b]) continue;   // its slots are never read
+        const float4 pb = posf[b];
+        const float4* bx = huge_cbox(H, par, k) + 2 * ch;
+        if (chunk_culled(pb, bx[0], bx[1])) continue;   // warp-uniform
         double ax = 0.0, ay = 0.0, az = 0.0;
-        if (H.alive[b]) {
-            const double xb = H.pos[b], yb = H.pos[c + b], zb = H.pos[2 * c + b];
-            const float4 pb = H.posf[b];
+        {
+            const double xb = pos[b], yb = pos[c + b], zb = pos[2 * c + b];
             const float slack = 1e-5f * (1.0f + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
             for (int u = 0; u < 2; u++) {
-                const int o = ch * kHugeChunk + u * 32 + lane;
-                if (o >= M || o == b || !H.alive[o]) continue;
-                const float4 po = H.posf[o];
+                const int io = ch * kHugeChunk + u * 32 + lane;
+                if (io >= M) continue;
+                const int o = H.perm[io];
+                if (o == b || !H.alive[o]) continue;
+                const float4 po = posf[o];
                 const float dx = po.x - pb.x, dy = po.y - pb.y, dz = po.z - pb.z;
                 const float lim = fmaxf(pb.w, po.w) + slack;
-                if (dx * dx + dy * dy + dz * dz < lim * lim) huge_pair(d, p, b, o, xb, yb, zb, ax, ay, az);
+                if (dx * dx + dy * dy + dz * dz < lim * lim) huge_pair(d, p, pos, b, o, xb, yb, zb, ax, ay, az);
             }
         }
 #pragma unroll
@@ -117,7 +204,7 @@ __device__ void huge_pairs(const Dev& d, const Params& p, int M, int nch) {
             az += __shfl_xor_sync(0xffffffffu, az, s);
         }
         if (lane == 0) {
-            double* q = H.part + 3 * (int64_t)w;
+            double* q = huge_part(H, k) + 3 * r;
             q[0] = ax;
             q[1] = ay;
             q[2] = az;
@@ -125,13 +212,17 @@ __device__ void huge_pairs(const Dev& d, const Params& p, int M, int nch) {
     }
 }
 
-__device__ __forceinline__ void huge_set_pos(const Dev& d, int b, double x, double y, double z) {
+// sequence k's evaluation point of member b, in double and in float
+__device__ __forceinline__ float4 huge_set_pos(const Dev& d, int k, int b, double x, double y, double z) {
     const HugeBuf& H = d.hb;
     const int64_t c = H.cap;
-    H.pos[b] = x;
-    H.pos[c + b] = y;
-    H.pos[2 * c + b] = z;
-    H.posf[b] = make_float4((float)x, (float)y, (float)z, __double2float_ru(H.rc[b]));
+    double* pos = H.pos + (int64_t)k * 3 * c;
+    pos[b] = x;
+    pos[c + b] = y;
+    pos[2 * c + b] = z;
+    const float4 f = make_float4((float)x, (float)y, (float)z, __double2float_ru(H.rc[b]));
+    H.posf[(int64_t)k * c + b] = f;
+    return f;
 }
 
 // exact contact test of two members (the small-group kernels' comparison);
@@ -189,8 +280,9 @@ __device__ void huge_merge(const Dev& d, const Params& p, double M0, int b, int 
 // lexicographic order of member pairs (the sequential sweep's order)
 __device__ __forceinline__ bool pair_before(int2 a, int2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); }
 
-__global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
+__global__ void __launch_bounds__(kHugeThreads, 1) k_bs_huge(Dev d) {
     __shared__ double red[kHugeThreads / 32];
+    __shared__ int bred[7][kHugeThreads / 32];
     HugeCtl* hc = d.hctl;
     const int nh = d.ctl->nhuge;
     if (nh == 0) return;   // fixed before the launch: the same in every block
@@ -231,13 +323,68 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
             H.pinv[b] = 1.0 / (0.9 * d.rc[gb]);
             H.alive[b] = d.alive[gb];
         }
+        const int Mp = nch * kHugeChunk;   // member slots rounded up to whole chunks
         if (lead) {
             hc->El = 0.0;
             hc->nmerge = 0;
+            hc->bb[0] = hc->bb[2] = 0x7fffffff;
+            hc->bb[1] = hc->bb[3] = (int)0x80000000;
+        }
+        // The members in spatial order, once a step: a 2D Morton key of each
+        // start position over the group's box, ranked (ties by slot), so that
+        // a chunk of 64 consecutive members of the order is compact and its
+        // box culls the pairs it cannot hold.
+        bool ok = huge_sync(hc);
+        if (ok) {
+            int lx = 0x7fffffff, hx = (int)0x80000000, ly = 0x7fffffff, hy = (int)0x80000000;
+            for (int64_t b = gt; b < M; b += nt) {
+                const int fx = ford((float)H.y[b]), fy = ford((float)H.y[c + b]);
+                lx = min(lx, fx);
+                hx = max(hx, fx);
+                ly = min(ly, fy);
+                hy = max(hy, fy);
+            }
+            lx = __reduce_min_sync(0xffffffffu, lx);
+            hx = __reduce_max_sync(0xffffffffu, hx);
+            ly = __reduce_min_sync(0xffffffffu, ly);
+            hy = __reduce_max_sync(0xffffffffu, hy);
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&hc->bb[0], lx);
+                atomicMax(&hc->bb[1], hx);
+                atomicMin(&hc->bb[2], ly);
+                atomicMax(&hc->bb[3], hy);
+            }
+            ok = huge_sync(hc);
+        }
+        if (ok) {
+            const float x0 = fordinv(*(volatile int*)&hc->bb[0]), x1 = fordinv(*(volatile int*)&hc->bb[1]);
+            const float y0 = fordinv(*(volatile int*)&hc->bb[2]), y1 = fordinv(*(volatile int*)&hc->bb[3]);
+            const float sx = 65535.0f / fmaxf(x1 - x0, 1e-30f), sy = 65535.0f / fmaxf(y1 - y0, 1e-30f);
+            for (int64_t b = gt; b < M; b += nt) {
+                const unsigned qx = (unsigned)fminf(65535.0f, fmaxf(0.0f, ((float)H.y[b] - x0) * sx));
+                const unsigned qy = (unsigned)fminf(65535.0f, fmaxf(0.0f, ((float)H.y[c + b] - y0) * sy));
+                H.key[b] = spread16(qx) | (spread16(qy) << 1);
+            }
+            ok = huge_sync(hc);
+        }
+        if (ok) {
+            for (int64_t b = gt; b < M; b += nt) {
+                const unsigned kb = H.key[b];
+                int rank = 0;
+                for (int o = 0; o < M; o++) {
+                    const unsigned ko = H.key[o];
+                    rank += (ko < kb || (ko == kb && o < (int)b)) ? 1 : 0;
+                }
+                H.perm[rank] = (int)b;
+            }
+        }
+        if (!ok) {
+            if (lead) set_status(d.ctl, kEbs, kHugeAbortDetail + 1 + g);
+            return;
         }
         double t = 0.0, Hs = dt;
         int nsub = 0;
-        bool ok = true, failed = false;
+        bool failed = false;
         for (;;) {
             const double rem = dt - t;
             int last = 0;
@@ -246,29 +393,64 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
                 last = 1;
             }
             int kacc = -1;
-            for (int k = 0; k < kBsRows && ok; k++) {
-                const int n = 2 * (k + 1);
-                const double h = Hs / n;
-                for (int64_t b = gt; b < M; b += nt) huge_set_pos(d, (int)b, H.y[b], H.y[c + b], H.y[2 * c + b]);
+            // The sequences advance in lockstep: round r evaluates the derivative
+            // at the r-th point of every sequence k with n_k = 2 (k + 1) >= r
+            // (round 0 at the substep's start, shared by all of them).  Sequence
+            // k ends at round n_k with its tableau row, and row k >= 1 is tested
+            // then: rows are tested in the sequential order, and the first that
+            // passes is the one the sequential method takes, from the same
+            // arithmetic.  Two grid barriers a round.  Members are visited in
+            // spatial order in whole chunks (block-aligned), so that each chunk's
+            // box of the next evaluation points is reduced where they are set.
+            for (int64_t base = (int64_t)blockIdx.x * kHugeThreads; base < Mp; base += nt) {
+                const int i = (int)(base + threadIdx.x);
+                const bool mem = i < M;
+                const int b = mem ? H.perm[i] : 0;
+                float4 pf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (mem) pf = huge_set_pos(d, 0, b, H.y[b], H.y[c + b], H.y[2 * c + b]);
+                chunk_box_store(mem && H.alive[b], pf,
+                                ((i & 63) == 0 && i < Mp) ? huge_cbox(H, 0, 0) + 2 * (i >> 6) : nullptr, bred);
+            }
+            if (!(ok = huge_sync(hc))) break;
+            for (int r = 0; r <= 2 * kBsRows && ok; r++) {
+                const int k0 = r == 0 ? 0 : max(0, (r + 1) / 2 - 1);
+                const int nact = r == 0 ? 1 : kBsRows - k0;
+                const int kf = (r >= 2 && r % 2 == 0) ? r / 2 - 1 : -1;   // the sequence that ends this round
+                huge_pairs(d, p, M, nch, k0, nact, r & 1);
                 if (!(ok = huge_sync(hc))) break;
-                for (int s = 0; s <= n && ok; s++) {
-                    huge_pairs(d, p, M, nch);
-                    if (!(ok = huge_sync(hc))) break;
-                    double emax = 0.0;
-                    for (int64_t b = gt; b < M; b += nt) {
-                        // evaluation point of this pass: the substep's start or z1
-                        const double* base = s == 0 ? H.y : H.z1;
-                        const double P0 = base[b], P1 = base[c + b], P2 = base[2 * c + b];
-                        double f[6] = {0, 0, 0, 0, 0, 0};
+                double emax = 0.0;
+                for (int64_t base = (int64_t)blockIdx.x * kHugeThreads; base < (int64_t)nact * Mp; base += nt) {
+                    const int64_t idx = base + threadIdx.x;
+                    const bool act = idx < (int64_t)nact * Mp;
+                    const int k = k0 + (act ? (int)(idx / Mp) : 0);
+                    const int i = act ? (int)(idx % Mp) : 0;
+                    const bool mem = act && i < M;
+                    const int b = mem ? H.perm[i] : 0;
+                    const int n = 2 * (k + 1);
+                    const double h = Hs / n;
+                    double* z0 = H.z0 + (int64_t)k * 6 * c;
+                    double* z1 = H.z1 + (int64_t)k * 6 * c;
+                    // the next evaluation point of this member (sequence k), for the chunk box
+                    bool moved = false;
+                    float4 pf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    double f[6] = {0, 0, 0, 0, 0, 0};
+                    if (mem) {
+                        // evaluation point of this round: the substep's start or z1
+                        const double* base_pt = r == 0 ? H.y : z1;
+                        const double P0 = base_pt[b], P1 = base_pt[c + b], P2 = base_pt[2 * c + b];
                         if (H.alive[b]) {
-                            f[0] = base[3 * c + b];
-                            f[1] = base[4 * c + b];
-                            f[2] = base[5 * c + b];
+                            f[0] = base_pt[3 * c + b];
+                            f[1] = base_pt[4 * c + b];
+                            f[2] = base_pt[5 * c + b];
                             const double r2 = P0 * P0 + P1 * P1 + P2 * P2, ri = rsqrt(r2);
                             const double sk = -GM0 * (ri * ri * ri);
                             double ax = sk * P0, ay = sk * P1, az = sk * P2;
-                            const double* q = H.part + 3 * (int64_t)b * nch;
+                            // the chunk slots the pair phase wrote: the same culling decision
+                            const double* q = huge_part(H, k) + 3 * (int64_t)b * nch;
+                            const float4 pb = H.posf[(int64_t)k * c + b];
+                            const float4* bx = huge_cbox(H, r & 1, k);
                             for (int ch = 0; ch < nch; ch++) {
+                                if (chunk_culled(pb, bx[2 * ch], bx[2 * ch + 1])) continue;
                                 ax += q[3 * ch];
                                 ay += q[3 * ch + 1];
                                 az += q[3 * ch + 2];
@@ -277,22 +459,30 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
                             f[4] = ay;
                             f[5] = az;
                         }
-                        if (s == 0) {
-                            for (int q = 0; q < 6; q++) {
-                                H.z0[q * c + b] = H.y[q * c + b];
-                                H.z1[q * c + b] = H.y[q * c + b] + h * f[q];
+                        if (r == 0) {
+                            // the first step of every sequence from the shared derivative
+                            for (int kk = 0; kk < kBsRows; kk++) {
+                                const double hk = Hs / (2 * (kk + 1));
+                                double* a0 = H.z0 + (int64_t)kk * 6 * c;
+                                double* a1 = H.z1 + (int64_t)kk * 6 * c;
+                                for (int q = 0; q < 6; q++) {
+                                    a0[q * c + b] = H.y[q * c + b];
+                                    a1[q * c + b] = H.y[q * c + b] + hk * f[q];
+                                }
                             }
-                        } else if (s < n) {
+                        } else if (r < n) {
                             for (int q = 0; q < 6; q++) {
-                                const double znew = H.z0[q * c + b] + 2.0 * h * f[q];
-                                H.z0[q * c + b] = H.z1[q * c + b];
-                                H.z1[q * c + b] = znew;
+                                const double znew = z0[q * c + b] + 2.0 * h * f[q];
+                                z0[q * c + b] = z1[q * c + b];
+                                z1[q * c + b] = znew;
                             }
+                            pf = huge_set_pos(d, k, b, z1[b], z1[c + b], z1[2 * c + b]);
+                            moved = true;
                         } else {
-                            // row k of the tableau (in place) and this member's error
+                            // row k of the tableau (in place; sequences end in order) and this member's error
                             double dsq_x = 0.0, dsq_v = 0.0, nx = 0.0, nv = 0.0;
                             for (int q = 0; q < 6; q++) {
-                                double cv = 0.5 * (H.z1[q * c + b] + H.z0[q * c + b] + h * f[q]), pv = 0.0;
+                                double cv = 0.5 * (z1[q * c + b] + z0[q * c + b] + h * f[q]), pv = 0.0;
                                 for (int j = 1; j <= k; j++) {
                                     double* slot = H.row + ((int64_t)(j - 1) * 6 + q) * c + b;
                                     const double up = *slot;
@@ -313,34 +503,58 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
                             if (k >= 1 && H.alive[b]) {
                                 // |dX|^2 <= tol^2 |X|^2 and the same for V; a NaN fails it
                                 const double e2 =
-                                    (dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308)) ? 0.0
-                                                                                                             : HUGE_VAL;
+                                    (dsq_x <= tol2 * fmax(nx, 2.3e-308) && dsq_v <= tol2 * fmax(nv, 2.3e-308))
+                                        ? 0.0
+                                        : HUGE_VAL;
                                 emax = fmax(emax, e2);
                             }
                         }
-                        if (s < n) huge_set_pos(d, (int)b, H.z1[b], H.z1[c + b], H.z1[2 * c + b]);
                     }
-                    if (s == n) {
-                        // grid-wide maximum of the errors (non-negative: their bits order as they do)
-                        for (int o = 16; o >= 1; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-                        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
-                        __syncthreads();
-                        if (threadIdx.x == 0) {
-                            double m = 0.0;
-                            for (int w = 0; w < kHugeThreads / 32; w++) m = fmax(m, red[w]);
-                            atomicMax(&hc->err[k], (unsigned long long)__double_as_longlong(m));
+                    // the next round's chunk boxes (parity of round r + 1)
+                    if (r == 0) {
+                        for (int kk = 0; kk < kBsRows; kk++) {
+                            float4 pk = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                            if (mem) {
+                                const double* a1 = H.z1 + (int64_t)kk * 6 * c;
+                                pk = huge_set_pos(d, kk, b, a1[b], a1[c + b], a1[2 * c + b]);
+                            }
+                            chunk_box_store(mem && H.alive[b], pk,
+                                            (act && (i & 63) == 0) ? huge_cbox(H, 1, kk) + 2 * (i >> 6) : nullptr,
+                                            bred);
                         }
+                    } else {
+                        const bool cont = act && r < n;   // the same for the 64 threads of a chunk
+                        chunk_box_store(moved && H.alive[b], pf,
+                                        (cont && (i & 63) == 0) ? huge_cbox(H, (r + 1) & 1, k) + 2 * (i >> 6) : nullptr,
+                                        bred);
                     }
-                    if (!(ok = huge_sync(hc))) break;
                 }
-                if (!ok) break;
-                const double e = __longlong_as_double((long long)*(volatile unsigned long long*)&hc->err[k]);
-                if (!(ok = huge_sync(hc))) break;   // everyone has read the maximum
-                if (lead) hc->err[k] = 0ull;
-                if (k >= 1 && e <= tol2) {
-                    kacc = k;
-                    break;
+                if (kf >= 0) {
+                    // grid-wide maximum of the ending sequence's errors (non-negative:
+                    // their bits order as they do)
+                    for (int o = 16; o >= 1; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+                    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        double m = 0.0;
+                        for (int w = 0; w < kHugeThreads / 32; w++) m = fmax(m, red[w]);
+                        atomicMax(&hc->err[kf], (unsigned long long)__double_as_longlong(m));
+                    }
                 }
+                if (!(ok = huge_sync(hc))) break;
+                if (kf >= 1) {
+                    const double e = __longlong_as_double((long long)*(volatile unsigned long long*)&hc->err[kf]);
+                    if (e <= tol2) {
+                        kacc = kf;
+                        break;
+                    }
+                }
+            }
+            if (ok && kacc < 0) {
+                // rejected: everyone has read the last row's maximum before the rows are cleared
+                ok = huge_sync(hc);
+                if (lead)
+                    for (int k = 0; k < kBsRows; k++) hc->err[k] = 0ull;
             }
             if (!ok) break;
             nsub++;
@@ -351,6 +565,9 @@ __global__ void __launch_bounds__(kHugeThreads) k_bs_huge(Dev d) {
                 // contacts: candidates in parallel, then the sequential sweep by one thread
                 if (lead) hc->ncand = 0;
                 if (!(ok = huge_sync(hc))) break;
+                // every block has read the accepted row's maximum: clear the rows' maxima
+                if (lead)
+                    for (int k = 0; k < kBsRows; k++) hc->err[k] = 0ull;
                 for (int64_t w = gt; w < (int64_t)M * nch; w += nt) {
                     const int u = (int)(w / nch), ch = (int)(w % nch);
                     if (!H.alive[u]) continue;

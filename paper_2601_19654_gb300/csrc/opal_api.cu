@@ -463,19 +463,24 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         HugeBuf& H = d.hb;
         H.cap = std::min<int64_t>(N, kHugeMax);
         const int64_t nch = (H.cap + 63) / 64;
+        // the midpoint sequences advance in lockstep: chains, evaluation points
+        // and pair sums for each of the kBsRows sequences
         TRYF(dalloc(s, &H.y, 6 * H.cap));
-        TRYF(dalloc(s, &H.z0, 6 * H.cap));
-        TRYF(dalloc(s, &H.z1, 6 * H.cap));
+        TRYF(dalloc(s, &H.z0, (int64_t)kBsRows * 6 * H.cap));
+        TRYF(dalloc(s, &H.z1, (int64_t)kBsRows * 6 * H.cap));
         TRYF(dalloc(s, &H.row, (int64_t)kBsRows * 6 * H.cap));
-        TRYF(dalloc(s, &H.pos, 3 * H.cap));
-        TRYF(dalloc(s, &H.posf, H.cap));
-        TRYF(dalloc(s, &H.part, 3 * H.cap * nch));
+        TRYF(dalloc(s, &H.pos, (int64_t)kBsRows * 3 * H.cap));
+        TRYF(dalloc(s, &H.posf, (int64_t)kBsRows * H.cap));
+        TRYF(dalloc(s, &H.part, (int64_t)kBsRows * 3 * H.cap * nch));
         TRYF(dalloc(s, &H.m, H.cap));
         TRYF(dalloc(s, &H.R, H.cap));
         TRYF(dalloc(s, &H.rc, H.cap));
         TRYF(dalloc(s, &H.pinv, H.cap));
         TRYF(dalloc(s, &H.alive, H.cap));
         TRYF(dalloc(s, &H.gid, H.cap));
+        TRYF(dalloc(s, &H.perm, H.cap));
+        TRYF(dalloc(s, &H.key, H.cap));
+        TRYF(dalloc(s, &H.cbox, (int64_t)2 * kBsRows * nch * 2));
         TRYF(dalloc(s, &d.hctl, 1));
         CKF(cudaMemsetAsync(d.hctl, 0, sizeof(HugeCtl), s->stream));
     }

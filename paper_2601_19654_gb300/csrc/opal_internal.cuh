@@ -72,22 +72,28 @@ struct Ctl {
 
 // Encounter groups of more than 64 members: working arrays of one group
 // (component-major [q][cap] arrays, cap = the largest such group).
-constexpr int kHugeMax = 16384;   // members of the largest group these buffers take
+constexpr int kHugeMax = 8192;    // members of the largest group these buffers take
 constexpr int kHugeCand = 1024;   // member pairs in contact after one substep
 struct HugeBuf {
     int64_t cap;
-    double *y, *z0, *z1;      // [6][cap]: substep state, midpoint chain
+    double* y;                // [6][cap]: substep state
+    double *z0, *z1;          // [kBsRows][6][cap]: each midpoint sequence's chain
     double* row;              // [kBsRows][6][cap]: extrapolation tableau (in place)
-    double* pos;              // [3][cap]: positions of the current evaluation
-    float4* posf;             // [cap]: the same in float, with rc (rounded up)
-    double* part;             // [cap * chunks][3]: (1 - K) sums of each (member, 64-member chunk)
+    double* pos;              // [kBsRows][3][cap]: each sequence's positions of the current evaluation
+    float4* posf;             // [kBsRows][cap]: the same in float, with rc (rounded up)
+    double* part;             // [kBsRows][cap * chunks][3]: (1 - K) sums of each (member, 64-member chunk)
     double *m, *R, *rc, *pinv;
     int *alive, *gid;
+    int* perm;                // [cap]: members in spatial order; chunk ch is perm[64 ch .. 64 ch + 63]
+    unsigned int* key;        // [cap]: their spatial keys
+    float4* cbox;             // [2][kBsRows][chunks][2]: box of each chunk's evaluation points (lo xyz +
+                              // largest rc, hi xyz), by round parity
 };
 // barrier and bookkeeping of the whole-GPU encounter kernel (zeroed every step)
 struct HugeCtl {
     unsigned int bar_count, bar_gen;
     int abort, skip;
+    int bb[4];                          // the group's box in x and y (order-mapped: min x, max x, min y, max y)
     int ncand, nmerge;
     double El;
     unsigned long long err[kBsRows];   // grid-wide maximum error of each row (bits of a double >= 0)
