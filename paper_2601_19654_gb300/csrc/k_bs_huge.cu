@@ -164,28 +164,50 @@ __device__ __forceinline__ double* huge_part(const HugeBuf& H, int k) {
 
 // pair phase of one round: every (sequence, member, chunk) slot of the nact
 // sequences k0 .. k0 + nact - 1, from their evaluation points and the chunk
-// boxes of round parity par; chunks are runs of 64 members in spatial order
-__device__ void huge_pairs(const Dev& d, const Params& p, int M, int nch, int k0, int nact, int par) {
+// boxes of round parity par; chunks are runs of 64 members in spatial order.
+// A task takes one member and kHugeGroup chunks (its lanes test the chunks'
+// boxes together, then the chunks that can hold a pair run one after
+// another), except for the nwide members of wide critical radius (a giant
+// planet: every pair of its row passes, in FP64), whose rows take one chunk
+// a task so that their terms spread over the GPU.  Culled chunks leave their
+// slots unwritten; the member phase skips them by the same test.
+__device__ void huge_pairs(const Dev& d, const Params& p, int M, int nch, int k0, int nact, int par, int nwide) {
     const HugeBuf& H = d.hb;
     const int64_t c = H.cap;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t per = (int64_t)M * nch;
+    const int ngrp = (nch + kHugeGroup - 1) / kHugeGroup;
+    const int64_t perA = (int64_t)nwide * nch, perB = (int64_t)M * ngrp, per = perA + perB;
     for (int64_t w = gw; w < nact * per; w += nw) {
         const int k = k0 + (int)(w / per);
         const int64_t r = w % per;
-        const int b = (int)(r / nch), ch = (int)(r % nch);
+        int b, ch0, ch1;
+        if (r < perA) {
+            b = d.hctl->wlist[r / nch];
+            ch0 = (int)(r % nch);
+            ch1 = ch0 + 1;
+        } else {
+            b = (int)((r - perA) / ngrp);
+            if (H.wide[b]) continue;   // its row runs a chunk a task
+            ch0 = (int)((r - perA) % ngrp) * kHugeGroup;
+            ch1 = min(nch, ch0 + kHugeGroup);
+        }
+        if (!H.alive[b]) continue;   // its slots are never read
         const double* pos = huge_pos(H, k);
         const float4* posf = H.posf + (int64_t)k * c;
-        if (!H.alive[b]) continue;   // its slots are never read
         const float4 pb = posf[b];
-        const float4* bx = huge_cbox(H, par, k) + 2 * ch;
-        if (chunk_culled(pb, bx[0], bx[1])) continue;   // warp-uniform
-        double ax = 0.0, ay = 0.0, az = 0.0;
-        {
-            const double xb = pos[b], yb = pos[c + b], zb = pos[2 * c + b];
-            const float slack = 1e-5f * (1.0f + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
+        const float4* bx = huge_cbox(H, par, k);
+        // the task's chunks that can hold a pair (lane j tests chunk ch0 + j)
+        unsigned live = __ballot_sync(0xffffffffu, lane < ch1 - ch0 && !chunk_culled(pb, bx[2 * (ch0 + lane)],
+                                                                                     bx[2 * (ch0 + lane) + 1]));
+        if (!live) continue;
+        const double xb = pos[b], yb = pos[c + b], zb = pos[2 * c + b];
+        const float slack = 1e-5f * (1.0f + fabsf(pb.x) + fabsf(pb.y) + fabsf(pb.z));
+        while (live) {
+            const int ch = ch0 + __ffs(live) - 1;
+            live &= live - 1;
+            double ax = 0.0, ay = 0.0, az = 0.0;
             for (int u = 0; u < 2; u++) {
                 const int io = ch * kHugeChunk + u * 32 + lane;
                 if (io >= M) continue;
@@ -196,18 +218,18 @@ __device__ void huge_pairs(const Dev& d, const Params& p, int M, int nch, int k0
                 const float lim = fmaxf(pb.w, po.w) + slack;
                 if (dx * dx + dy * dy + dz * dz < lim * lim) huge_pair(d, p, pos, b, o, xb, yb, zb, ax, ay, az);
             }
-        }
 #pragma unroll
-        for (int s = 16; s >= 1; s >>= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, s);
-            ay += __shfl_xor_sync(0xffffffffu, ay, s);
-            az += __shfl_xor_sync(0xffffffffu, az, s);
-        }
-        if (lane == 0) {
-            double* q = huge_part(H, k) + 3 * r;
-            q[0] = ax;
-            q[1] = ay;
-            q[2] = az;
+            for (int s = 16; s >= 1; s >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, s);
+                ay += __shfl_xor_sync(0xffffffffu, ay, s);
+                az += __shfl_xor_sync(0xffffffffu, az, s);
+            }
+            if (lane == 0) {
+                double* q = huge_part(H, k) + 3 * ((int64_t)b * nch + ch);
+                q[0] = ax;
+                q[1] = ay;
+                q[2] = az;
+            }
         }
     }
 }
@@ -329,6 +351,9 @@ __global__ void __launch_bounds__(kHugeThreads, 1) k_bs_huge(Dev d) {
             hc->nmerge = 0;
             hc->bb[0] = hc->bb[2] = 0x7fffffff;
             hc->bb[1] = hc->bb[3] = (int)0x80000000;
+            hc->rcmm[0] = 0;
+            hc->rcmm[1] = 0x7fffffff;
+            hc->nwide = 0;
         }
         // The members in spatial order, once a step: a 2D Morton key of each
         // start position over the group's box, ranked (ties by slot), so that
@@ -337,22 +362,32 @@ __global__ void __launch_bounds__(kHugeThreads, 1) k_bs_huge(Dev d) {
         bool ok = huge_sync(hc);
         if (ok) {
             int lx = 0x7fffffff, hx = (int)0x80000000, ly = 0x7fffffff, hy = (int)0x80000000;
+            int rmax = 0, rmin = 0x7fffffff;
             for (int64_t b = gt; b < M; b += nt) {
                 const int fx = ford((float)H.y[b]), fy = ford((float)H.y[c + b]);
                 lx = min(lx, fx);
                 hx = max(hx, fx);
                 ly = min(ly, fy);
                 hy = max(hy, fy);
+                if (H.alive[b]) {
+                    const int rb = __float_as_int(__double2float_ru(H.rc[b]));   // rc >= 0: bits order as values
+                    rmax = max(rmax, rb);
+                    rmin = min(rmin, rb);
+                }
             }
             lx = __reduce_min_sync(0xffffffffu, lx);
             hx = __reduce_max_sync(0xffffffffu, hx);
             ly = __reduce_min_sync(0xffffffffu, ly);
             hy = __reduce_max_sync(0xffffffffu, hy);
+            rmax = __reduce_max_sync(0xffffffffu, rmax);
+            rmin = __reduce_min_sync(0xffffffffu, rmin);
             if ((threadIdx.x & 31) == 0) {
                 atomicMin(&hc->bb[0], lx);
                 atomicMax(&hc->bb[1], hx);
                 atomicMin(&hc->bb[2], ly);
                 atomicMax(&hc->bb[3], hy);
+                atomicMax(&hc->rcmm[0], rmax);
+                atomicMin(&hc->rcmm[1], rmin);
             }
             ok = huge_sync(hc);
         }
@@ -360,10 +395,23 @@ __global__ void __launch_bounds__(kHugeThreads, 1) k_bs_huge(Dev d) {
             const float x0 = fordinv(*(volatile int*)&hc->bb[0]), x1 = fordinv(*(volatile int*)&hc->bb[1]);
             const float y0 = fordinv(*(volatile int*)&hc->bb[2]), y1 = fordinv(*(volatile int*)&hc->bb[3]);
             const float sx = 65535.0f / fmaxf(x1 - x0, 1e-30f), sy = 65535.0f / fmaxf(y1 - y0, 1e-30f);
+            // wide members: rc above a quarter of the largest, when that is over 8 times the smallest
+            const float rmx = __int_as_float(*(volatile int*)&hc->rcmm[0]);
+            const float rmn = __int_as_float(*(volatile int*)&hc->rcmm[1]);
+            const bool any_wide = rmx > 8.0f * rmn;
             for (int64_t b = gt; b < M; b += nt) {
                 const unsigned qx = (unsigned)fminf(65535.0f, fmaxf(0.0f, ((float)H.y[b] - x0) * sx));
                 const unsigned qy = (unsigned)fminf(65535.0f, fmaxf(0.0f, ((float)H.y[c + b] - y0) * sy));
                 H.key[b] = spread16(qx) | (spread16(qy) << 1);
+                int wb = 0;
+                if (any_wide && H.alive[b] && __double2float_ru(H.rc[b]) > 0.25f * rmx) {
+                    const int q = atomicAdd(&hc->nwide, 1);
+                    if (q < kHugeWide) {
+                        hc->wlist[q] = (int)b;
+                        wb = 1;
+                    }
+                }
+                H.wide[b] = wb;
             }
             ok = huge_sync(hc);
         }
@@ -377,11 +425,13 @@ __global__ void __launch_bounds__(kHugeThreads, 1) k_bs_huge(Dev d) {
                 }
                 H.perm[rank] = (int)b;
             }
+            ok = huge_sync(hc);   // the order is complete before anyone reads it
         }
         if (!ok) {
             if (lead) set_status(d.ctl, kEbs, kHugeAbortDetail + 1 + g);
             return;
         }
+        const int nwide = min(*(volatile int*)&hc->nwide, kHugeWide);
         double t = 0.0, Hs = dt;
         int nsub = 0;
         bool failed = false;
@@ -416,7 +466,7 @@ __global__ void __launch_bounds__(kHugeThreads, 1) k_bs_huge(Dev d) {
                 const int k0 = r == 0 ? 0 : max(0, (r + 1) / 2 - 1);
                 const int nact = r == 0 ? 1 : kBsRows - k0;
                 const int kf = (r >= 2 && r % 2 == 0) ? r / 2 - 1 : -1;   // the sequence that ends this round
-                huge_pairs(d, p, M, nch, k0, nact, r & 1);
+                huge_pairs(d, p, M, nch, k0, nact, r & 1, nwide);
                 if (!(ok = huge_sync(hc))) break;
                 double emax = 0.0;
                 for (int64_t base = (int64_t)blockIdx.x * kHugeThreads; base < (int64_t)nact * Mp; base += nt) {

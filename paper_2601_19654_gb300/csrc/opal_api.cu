@@ -479,6 +479,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         TRYF(dalloc(s, &H.alive, H.cap));
         TRYF(dalloc(s, &H.gid, H.cap));
         TRYF(dalloc(s, &H.perm, H.cap));
+        TRYF(dalloc(s, &H.wide, H.cap));
         TRYF(dalloc(s, &H.key, H.cap));
         TRYF(dalloc(s, &H.cbox, (int64_t)2 * kBsRows * nch * 2));
         TRYF(dalloc(s, &d.hctl, 1));

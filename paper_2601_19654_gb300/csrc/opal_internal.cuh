@@ -74,6 +74,8 @@ struct Ctl {
 // (component-major [q][cap] arrays, cap = the largest such group).
 constexpr int kHugeMax = 8192;    // members of the largest group these buffers take
 constexpr int kHugeCand = 1024;   // member pairs in contact after one substep
+constexpr int kHugeWide = 16;     // wide-rc members whose rows run one chunk a task (others: kHugeGroup chunks)
+constexpr int kHugeGroup = 8;     // chunks a pair-phase task takes for the other members
 struct HugeBuf {
     int64_t cap;
     double* y;                // [6][cap]: substep state
@@ -85,6 +87,7 @@ struct HugeBuf {
     double *m, *R, *rc, *pinv;
     int *alive, *gid;
     int* perm;                // [cap]: members in spatial order; chunk ch is perm[64 ch .. 64 ch + 63]
+    int* wide;                // [cap]: 1 for a member with a wide critical radius (its row runs a chunk a task)
     unsigned int* key;        // [cap]: their spatial keys
     float4* cbox;             // [2][kBsRows][chunks][2]: box of each chunk's evaluation points (lo xyz +
                               // largest rc, hi xyz), by round parity
@@ -94,6 +97,9 @@ struct HugeCtl {
     unsigned int bar_count, bar_gen;
     int abort, skip;
     int bb[4];                          // the group's box in x and y (order-mapped: min x, max x, min y, max y)
+    int nwide;                          // members with a wide critical radius, listed in wlist
+    int wlist[kHugeWide];
+    int rcmm[2];                        // bits of the members' largest and smallest float rc (>= 0)
     int ncand, nmerge;
     double El;
     unsigned long long err[kBsRows];   // grid-wide maximum error of each row (bits of a double >= 0)
