@@ -216,34 +216,57 @@ def ensemble_rates(seed: int, steps: int, warmup: int):
     """The 256-system ensemble (N log-uniform in 64-4096, each drawn like the
     10-body workload) advanced as one simulation, against the same systems as
     256 simulations of their own: launched one after another (each step
-    waits), and launched all at once on their own streams (then one wait).
-    All rates are ensemble steps/s (every system advanced one step)."""
+    waits for its system), and launched all at once on their own streams.
+    All rates are ensemble steps/s (every system advanced one step).  The
+    ensemble and the 256 streams are timed with CUDA events (the streams
+    start from one event and a final event waits for all of them); the
+    one-after-another arm, whose steps each end in a host wait, by the host
+    clock."""
+    import torch
     from paper_2601_19654_gb300 import opal
     systems = ic.ensemble(seed, 256)
     ens = opal.Simulation.ensemble(systems, precision=1)
     E0 = ens.energy()[0]
     ens.step(warmup)
-    t0 = time.perf_counter()
-    ens.step(steps)
-    t_ens = time.perf_counter() - t0
+    es = torch.cuda.ExternalStream(ens.stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(es)
+    ens.step_async(steps)
+    e1.record(es)
+    ens.wait()
+    e1.synchronize()
+    t_ens = e0.elapsed_time(e1) * 1e-3
     dE = abs(ens.energy()[0] - E0) / abs(E0)
     st = ens.stats()
     ens.close()
     per = [opal.Simulation.from_system(s, precision=1) for s in systems]
     for sim in per:
         sim.step(warmup)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         for sim in per:
             sim.step(1)
     t_serial = time.perf_counter() - t0
-    t0 = time.perf_counter()
+    streams = [torch.cuda.ExternalStream(sim.stream) for sim in per]
+    head = torch.cuda.Stream()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s0.record(head)
+    for sim, st_ in zip(per, streams):
+        st_.wait_event(s0)
     for _ in range(steps):
         for sim in per:
             sim.step_async(1)
+    for st_ in streams:
+        ev = torch.cuda.Event()
+        ev.record(st_)
+        head.wait_event(ev)
+    s1.record(head)
     for sim in per:
         sim.wait()
-    t_async = time.perf_counter() - t0
+    s1.synchronize()
+    t_async = s0.elapsed_time(s1) * 1e-3
     for sim in per:
         sim.close()
     r_ens, r_ser, r_asy = steps / t_ens, steps / t_serial, steps / t_async
@@ -252,7 +275,7 @@ def ensemble_rates(seed: int, steps: int, warmup: int):
             "ensemble_steps_per_s": r_ens, "per_system_serial_steps_per_s": r_ser,
             "per_system_streams_steps_per_s": r_asy, "over_serial": r_ens / r_ser,
             "over_streams": r_ens / r_asy, "dE_over_E": dE, "encounters_last_step": st,
-            "timing": "host clock around opal_step calls (each call ends in a device sync)"}
+            "timing": "CUDA events for the ensemble and the 256 streams; host clock for the steps one after another"}
 
 
 def removal_rates(system, steps: int, warmup: int, flush, plain_ms: float):
