@@ -227,6 +227,11 @@ opal_status opal_time_kick_alone(opal_sim* sim, int32_t reps, double* ms);
 /* Number of kernel launches in one step (kernel nodes of the step graph). */
 int32_t opal_graph_kernels(const opal_sim* sim);
 
+/* The step order the last opal_step or opal_step_async call ran: 1 when the
+ * kick ran beside the encounter integrator (overlap; see opal_step), 0 when
+ * it ran after it, -1 for a NULL sim. */
+int32_t opal_step_overlap(const opal_sim* sim);
+
 /* Reason for the last error on sim (or on the calling thread when sim is NULL). */
 const char* opal_last_error(const opal_sim* sim);
 

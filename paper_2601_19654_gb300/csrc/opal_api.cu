@@ -1039,6 +1039,8 @@ int32_t opal_graph_kernels(const opal_sim* s) {
     return k;
 }
 
+int32_t opal_step_overlap(const opal_sim* s) { return s ? s->d.overlap : -1; }
+
 opal_status opal_time_kick(opal_sim* s, int32_t enable) {
     if (!s) return set_err(g_err, "sim is NULL"), OPAL_EINVAL;
     if (enable && !s->kick_ev[0]) {

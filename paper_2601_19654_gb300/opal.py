@@ -70,6 +70,8 @@ def _declare(L):
     L.opal_time_kick_alone.restype = C.c_int
     L.opal_graph_kernels.argtypes = [_P]
     L.opal_graph_kernels.restype = C.c_int32
+    L.opal_step_overlap.argtypes = [_P]
+    L.opal_step_overlap.restype = C.c_int32
     L.opal_kick_config.argtypes = [_P]
     L.opal_kick_config.restype = C.c_char_p
     L.opal_last_error.argtypes = [_P]
@@ -244,6 +246,11 @@ class Simulation:
     @property
     def graph_kernels(self) -> int:
         return lib().opal_graph_kernels(self.ptr)
+
+    @property
+    def step_overlap(self) -> bool:
+        """True when the last step call ran the kick beside the encounter integrator."""
+        return lib().opal_step_overlap(self.ptr) == 1
 
     @property
     def kick_config(self) -> str:
