@@ -148,7 +148,7 @@ __device__ __forceinline__ void far_tile(const float* sx, const float* sy, const
     const float4* py = reinterpret_cast<const float4*>(sy);
     const float4* pz = reinterpret_cast<const float4*>(sz);
     const float4* pm = reinterpret_cast<const float4*>(sm);
-#pragma unroll 2
+#pragma unroll 4
     for (int jq = 0; jq < kJTile / 4; jq++) {
         const float4 x4 = px[jq], y4 = py[jq], z4 = pz[jq], m4 = pm[jq];
 #pragma unroll

@@ -153,9 +153,9 @@ bool finite_all(const double* a, int64_t n) {
 //    the chunk's partial row.
 //  - j-major: one j-tile (staged once) against a run of i-tiles; the j-tile
 //    index is the partial row.  The (i-tile, j-tile) units are grouped into
-//    runs of 4 while more than three resident blocks' worth of units
-//    remain, then of 2 while more than one remains, then single units, so
-//    that the queue ends on the smallest items.
+//    runs of 4 while more than four grids' worth of units remain (slots =
+//    the blocks of the launch), then of 2 while more than two remain, then
+//    single units, so that the queue ends on the smallest items.
 void build_kick_items(opal_sim* s, int slots, int itile, bool jmajor) {
     double work = 0;
     for (auto& si : s->sys) work += (double)si.cap * (double)si.nb;
@@ -175,7 +175,7 @@ void build_kick_items(opal_sim* s, int slots, int itile, bool jmajor) {
             for (int64_t t = 0; t < jtiles; t++) {
                 const int64_t j0 = si.off + t * kKickJTile, j1 = si.off + std::min(si.nb, (t + 1) * kKickJTile);
                 for (int64_t a = 0; a < itiles;) {
-                    int64_t run = left > 3 * (int64_t)slots ? 4 : (left > slots ? 2 : 1);
+                    int64_t run = left > 4 * (int64_t)slots ? 4 : (left > 2 * (int64_t)slots ? 2 : 1);
                     run = std::min(run, itiles - a);
                     // the run's i-tiles a + u * S (u < run) for a block of run * S tiles,
                     // S = the block's stride: spatial neighbours go to different items
@@ -632,9 +632,10 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
             }
         }
         s->kick_variant = best;
-        s->items = var_items[best];
-        s->sys = var_sys[best];
         s->kick_grid = (int)std::min<int64_t>((int64_t)var_items[best].size(), (int64_t)s->nsm * graph_blocks(best));
+        // the chosen shape's work list, its item sizes scheduled for the blocks it runs with
+        build_kick_items(s, s->kick_grid, kick_itile(p->precision, best), kick_jmajor(p->precision, best));
+        s->kick_grid = (int)std::min<int64_t>((int64_t)s->items.size(), (int64_t)s->nsm * graph_blocks(best));
         snprintf(s->kick_desc, sizeof(s->kick_desc), "%s, grid %d, %zu items, %d j-chunks (system 0)%s",
                  kick_variant_name(p->precision, best), s->kick_grid, s->items.size(), s->sys[0].nchunk,
                  force ? ", forced" : (best_ms >= 0 ? ", autotuned" : ""));
