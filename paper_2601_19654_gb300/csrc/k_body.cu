@@ -193,7 +193,61 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
 }
 
 // ---------------------------------------------------------------------------
-// Closing half: reduce the kick partials into a, jump with the momentum of
+// The kick's partial rows of every body, summed (after each kick, on its
+// stream).  A block takes 32 sorted positions; its warp w adds rows w,
+// w + 8, w + 16, ... in order, its lanes the 32 positions (one coalesced
+// 256-byte load a row), and the eight warps' sums are combined by a fixed
+// tree in shared memory, so the sum does not depend on the schedule.  The
+// mixed kick writes a body's row at its sorted position, the FP64 kick at
+// its index; the sum goes to ksum at the body's index.  Systems start at
+// multiples of kBodyThreads positions, so a block lies in one system.
+constexpr int kRowWarps = 8;
+__global__ void __launch_bounds__(32 * kRowWarps) k_kick_rows(Dev d) {
+    __shared__ double red[kRowWarps][3][32];
+    if (d.ctl->status || (d.gated && !d.ctl->reprime)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * 32 + lane;   // grid: ntot / 32 blocks
+    const int b = d.p.precision == 1 ? d.csorted[p] : (int)p;
+    const SysInfo si = d.sys[d.body_sys[(int64_t)blockIdx.x * 32]];
+    const int64_t local = p - si.off;
+    // four of the warp's rows loaded together (their latencies overlap), then added in order
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int c = w; c < si.nchunk; c += 4 * kRowWarps) {
+        double bx[4], by[4], bz[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int cu = c + u * kRowWarps;
+            const int64_t slot = si.slot0 + (int64_t)cu * si.cap + local;
+            const bool in = cu < si.nchunk;
+            bx[u] = in ? d.pacc_x[slot] : 0.0;
+            by[u] = in ? d.pacc_y[slot] : 0.0;
+            bz[u] = in ? d.pacc_z[slot] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            ax += bx[u];
+            ay += by[u];
+            az += bz[u];
+        }
+    }
+    red[w][0][lane] = ax;
+    red[w][1][lane] = ay;
+    red[w][2][lane] = az;
+    __syncthreads();
+#pragma unroll
+    for (int h = kRowWarps / 2; h >= 1; h >>= 1) {
+        if (w < h)
+            for (int q = 0; q < 3; q++) red[w][q][lane] += red[w + h][q][lane];
+        __syncthreads();
+    }
+    if (w == 0) {
+        d.ksum[3 * (int64_t)b] = red[0][0][lane];
+        d.ksum[3 * (int64_t)b + 1] = red[0][1][lane];
+        d.ksum[3 * (int64_t)b + 2] = red[0][2][lane];
+    }
+}
+
+// Closing half: the summed kick partials into a, jump with the momentum of
 // the post-encounter state, kick, and the momentum partials the next
 // step's jump needs (of V + dt/2 a, the velocities after its opening kick).
 // first != 0 (create time): only a and the partials, no jump or kick.
@@ -204,34 +258,8 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     const SysInfo si = d.sys[s];
     const double* P = d.Ptot + 3 * (d.nsys + s);   // momentum for the closing jump
     const double half = 0.5 * d.p.dt, G = d.p.G;
-    // the kick's partial rows, summed in row order; eight rows' loads are
-    // issued together so their latencies overlap.  The mixed kick writes a
-    // body's partials at its sorted position, the FP64 kick at its index.
-    const int64_t local = (d.p.precision == 1 ? (int64_t)d.cpos[b] : b) - si.off;
-    double ax = 0, ay = 0, az = 0;
-    int c = 0;
-    for (; c + 8 <= si.nchunk; c += 8) {
-        double bx[8], by[8], bz[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int64_t slot = si.slot0 + (int64_t)(c + u) * si.cap + local;
-            bx[u] = d.pacc_x[slot];
-            by[u] = d.pacc_y[slot];
-            bz[u] = d.pacc_z[slot];
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            ax += bx[u];
-            ay += by[u];
-            az += bz[u];
-        }
-    }
-    for (; c < si.nchunk; c++) {
-        const int64_t slot = si.slot0 + (int64_t)c * si.cap + local;
-        ax += d.pacc_x[slot];
-        ay += d.pacc_y[slot];
-        az += d.pacc_z[slot];
-    }
+    // the kick's partial rows, already summed by k_kick_rows
+    double ax = d.ksum[3 * b], ay = d.ksum[3 * b + 1], az = d.ksum[3 * b + 2];
     // after encounters, when the kick ran beside the BS: a member's row was
     // recomputed at its new place; every other body's row gets the members'
     // terms at their new places added (the mixed kick left the members out
@@ -587,6 +615,10 @@ void launch_prime(const Dev& d, cudaStream_t s) {
 void launch_open(const Dev& d, cudaStream_t s) {
     k_open<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d);
     prof_mark("open: kick+jump+drift");
+}
+void launch_kick_rows(const Dev& d, cudaStream_t s) {
+    k_kick_rows<<<(unsigned)(d.ntot / 32), 32 * kRowWarps, 0, s>>>(d);
+    prof_mark("kick: partial rows summed");
 }
 void launch_close(const Dev& d, cudaStream_t s) {
     k_close<<<(unsigned)(d.ntot / kBodyThreads), kBodyThreads, 0, s>>>(d, 0);

@@ -4,7 +4,7 @@
 //
 // Work is a list of items (i-tile of 128 bodies x a j-range of the same
 // system) that the blocks of a persistent grid take from a queue; each item
-// writes its partial sums to its own row of a buffer that the closing kernel
+// writes its partial sums to its own row of a buffer that k_kick_rows
 // reduces in a fixed order, so results do not depend on the schedule.
 // j-bodies are staged through shared memory and read by every thread of the
 // block (broadcast).  Pairs closer than 2 (rc_i + rc_max) take a slow path
@@ -280,7 +280,7 @@ __device__ __forceinline__ void near_tile(const Dev& d, int64_t i0, float rcm, c
 // largest threshold allows cannot hold a near pair and runs the packed loop
 // with no per-pair test.  Records past the item's j-range are parked (kFar,
 // zero mass): they add exact zeros.  Each (i-tile, j-tile) sum goes to the
-// j-tile's partial row, at the i-body's sorted position; k_close adds the
+// j-tile's partial row, at the i-body's sorted position; k_kick_rows adds the
 // rows in order.
 template <int T, int NI, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_kick_mixed(Dev d, const KickItem* __restrict__ items, int64_t nitems) {
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(T, MINB) k_kick_mixed(Dev d, const KickItem* _
             for (int q = 0; q < NI; q++) ax[q] = ay[q] = az[q] = make_float2(0.0f, 0.0f);
             if (near) near_tile<T, NI>(d, ib, rcm, sx, sy, sz, sm, sl, src, s_near, nx, ny, nz, form, ax, ay, az);
             else far_tile<NI>(sx, sy, sz, sm, nx, ny, nz, ax, ay, az);
-            // partial rows by sorted position (coalesced); k_close reads them through cpos
+            // partial rows by sorted position (coalesced); k_kick_rows sums them by position
 #pragma unroll
             for (int q = 0; q < NI; q++) {
                 const int64_t slot = base + ib + q * T + threadIdx.x;

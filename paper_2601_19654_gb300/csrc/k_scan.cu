@@ -232,7 +232,6 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_order(Dev d) {
         out = s + rank;
     }
     d.csorted[out] = b;
-    d.cpos[b] = (int)out;
     d.cen_sorted[out] = d.cen[b];
 }
 

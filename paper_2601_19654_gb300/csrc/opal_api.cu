@@ -424,6 +424,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     float** ksf[] = {&d.ks_x, &d.ks_y, &d.ks_z, &d.ks_m, &d.ks_rc};
     for (auto pp : ksf) TRYF(dalloc(s, pp, N));
     TRYF(dalloc(s, &d.ks_lo, N));
+    TRYF(dalloc(s, &d.ksum, 3 * N));
     TRYF(dalloc(s, &d.kbox, 2 * (N / kKickBox)));
     TRYF(dalloc(s, &d.kbox2, 2 * (N / (2 * kKickBox))));
     d.ncell = (int)(N / kBucketDiv);
@@ -432,7 +433,6 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.cstart, d.ncell));
     TRYF(dalloc(s, &d.ccursor, d.ncell));
     TRYF(dalloc(s, &d.csorted, N));
-    TRYF(dalloc(s, &d.cpos, N));
     TRYF(dalloc(s, &d.cscratch, N));
     TRYF(dalloc(s, &d.cen_sorted, N));
     TRYF(dalloc(s, &d.tbox, 6 * (N / kSeg)));
@@ -644,6 +644,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     }
     launch_kick_stage(d, P.precision, s->stream);
     launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, P.precision, s->kick_variant, s->stream);
+    launch_kick_rows(d, s->stream);
     launch_first_accel_finish(d, s->stream);
     CKF(cudaGetLastError());
     CKF(cudaStreamSynchronize(s->stream));
@@ -703,6 +704,7 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
             if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[0], st, cudaEventRecordExternal);
             launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
             if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[1], st, cudaEventRecordExternal);
+            launch_kick_rows(d, st);
             break;
         case kStageApply: launch_bs_apply(d, s->nsm, st); break;
         case 8: launch_kick_fix(d, s->nsm, st); break;
@@ -716,6 +718,7 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
             launch_prime(g, st);
             launch_kick_stage(g, d.p.precision, st);
             launch_kick(g, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
+            launch_kick_rows(g, st);
             launch_first_accel_finish(g, st);
             prof_mark("accelerations afresh after a removal");
             break;
@@ -1132,6 +1135,7 @@ opal_status opal_debug_accel(opal_sim* s, const double* rc, double* a) {
     launch_sort_bodies(d, s->stream);
     launch_kick_stage(d, d.p.precision, s->stream);
     launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, s->stream);
+    launch_kick_rows(d, s->stream);
     launch_first_accel_finish(d, s->stream);
     CK(cudaGetLastError());
     std::vector<double> ax(N), ay(N), az(N);

@@ -190,6 +190,7 @@ struct Dev {
     float *ks_x, *ks_y, *ks_z, *ks_m;
     float4* ks_lo;
     float* ks_rc;
+    double* ksum;    // [3 ntot]: each body's kick partial rows summed (by k_kick_rows), by body index
     float4* kbox;    // per 128 positions
     float4* kbox2;   // per 256 positions
     float4* cen;   // (c_hi, s): midpoint of the body's path over the step and the radius
@@ -213,7 +214,6 @@ struct Dev {
     int* ccursor;                       // [ncell] scatter cursors
     int2* cscratch;                     // (body, bucket or -1 if dead) after the scatter, any order in a bucket
     int* csorted;                       // bodies in sorted order, ascending ids within a cell
-    int* cpos;                          // its inverse: the sorted position of each body
     float4* cen_sorted;                 // their midpoint records, in sorted order
     float* tbox;                        // [ntot / 64][6] tile boxes of c +- s
     int ncell;                          // buckets: one per kBucketDiv body slots
@@ -594,6 +594,7 @@ int bs_block_regs();
 int kick_itile(int precision, int variant);   // i-bodies per i-tile (a divisor of kPad)
 bool kick_jmajor(int precision, int variant); // items: one j-tile against a run of i-tiles (else an i-tile against j-tiles)
 void launch_kick_stage(const Dev& d, int precision, cudaStream_t s);   // the sorted copies the mixed kick reads
+void launch_kick_rows(const Dev& d, cudaStream_t s);   // after every kick: its partial rows summed a body
 void launch_close(const Dev& d, cudaStream_t s);
 void launch_first_accel_finish(const Dev& d, cudaStream_t s);
 void launch_finish(const Dev& d, cudaStream_t s);
