@@ -194,42 +194,70 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
 
 // ---------------------------------------------------------------------------
 // The kick's partial rows of every body, summed (after each kick, on its
-// stream).  A block takes 32 sorted positions; its warp w adds rows w,
-// w + 8, w + 16, ... in order, its lanes the 32 positions (one coalesced
-// 256-byte load a row), and the eight warps' sums are combined by a fixed
-// tree in shared memory, so the sum does not depend on the schedule.  The
-// mixed kick writes a body's row at its sorted position, the FP64 kick at
-// its index; the sum goes to ksum at the body's index.  Systems start at
-// multiples of kBodyThreads positions, so a block lies in one system.
-constexpr int kRowWarps = 8;
-__global__ void __launch_bounds__(32 * kRowWarps) k_kick_rows(Dev d) {
-    __shared__ double red[kRowWarps][3][32];
-    if (d.ctl->status || (d.gated && !d.ctl->reprime)) return;
+// stream).  A block takes 32 sorted positions; its warp w adds rows 8w ..
+// 8w + 7 (then 8w + 64 .. 8w + 71, and so on) in order, its lanes the 32
+// positions (one coalesced 256-byte load a row, the warp's 24 loads in
+// flight together), and the eight warps' sums are combined by a fixed tree
+// in shared memory, so the sum does not depend on the schedule.  The
+// control word is read beside the rows, not before them.  Mixed form: the
+// rows are exact float pairs and the sums float-float (FP32 pipe; FP64
+// additions would take this chip's FP64 pipe half the kernel), converted to
+// FP64 at the end; FP64 form: FP64 rows and sums.  The mixed kick writes a
+// body's row at its sorted position, the FP64 kick at its index; the sum
+// goes to ksum at the body's index.  Systems start at multiples of
+// kBodyThreads positions, so a block lies in one system.
+constexpr int kRowWarps = 8, kRowsPerWarp = 8;
+template <bool MIXED>
+struct RowAcc;
+template <>
+struct RowAcc<true> {   // float-float
+    using T = float2;
+    static __device__ T zero() { return make_float2(0.0f, 0.0f); }
+    static __device__ T load(const double* a, int64_t i) { return reinterpret_cast<const float2*>(a)[i]; }
+    static __device__ T add(T x, T y) { return ff_add(x, y); }
+    static __device__ double value(T x) { return (double)x.x + (double)x.y; }
+};
+template <>
+struct RowAcc<false> {   // FP64
+    using T = double;
+    static __device__ T zero() { return 0.0; }
+    static __device__ T load(const double* a, int64_t i) { return a[i]; }
+    static __device__ T add(T x, T y) { return x + y; }
+    static __device__ double value(T x) { return x; }
+};
+
+template <bool MIXED>
+__global__ void __launch_bounds__(32 * kRowWarps, 4) k_kick_rows(Dev d) {
+    using A = RowAcc<MIXED>;
+    using T = typename A::T;
+    __shared__ T red[kRowWarps][3][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * 32 + lane;   // grid: ntot / 32 blocks
-    const int b = d.p.precision == 1 ? d.csorted[p] : (int)p;
+    const int status = d.ctl->status, reprime = d.ctl->reprime;
+    const int b = MIXED ? d.csorted[p] : (int)p;
     const SysInfo si = d.sys[d.body_sys[(int64_t)blockIdx.x * 32]];
     const int64_t local = p - si.off;
-    // four of the warp's rows loaded together (their latencies overlap), then added in order
-    double ax = 0.0, ay = 0.0, az = 0.0;
-    for (int c = w; c < si.nchunk; c += 4 * kRowWarps) {
-        double bx[4], by[4], bz[4];
+    T ax = A::zero(), ay = A::zero(), az = A::zero();
+#pragma unroll 1
+    for (int c0 = kRowsPerWarp * w; c0 < si.nchunk; c0 += kRowsPerWarp * kRowWarps) {
+        T bx[kRowsPerWarp], by[kRowsPerWarp], bz[kRowsPerWarp];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int cu = c + u * kRowWarps;
-            const int64_t slot = si.slot0 + (int64_t)cu * si.cap + local;
-            const bool in = cu < si.nchunk;
-            bx[u] = in ? d.pacc_x[slot] : 0.0;
-            by[u] = in ? d.pacc_y[slot] : 0.0;
-            bz[u] = in ? d.pacc_z[slot] : 0.0;
+        for (int u = 0; u < kRowsPerWarp; u++) {
+            const int c = c0 + u;
+            const int64_t slot = si.slot0 + (int64_t)c * si.cap + local;
+            const bool in = c < si.nchunk;
+            bx[u] = in ? A::load(d.pacc_x, slot) : A::zero();
+            by[u] = in ? A::load(d.pacc_y, slot) : A::zero();
+            bz[u] = in ? A::load(d.pacc_z, slot) : A::zero();
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            ax += bx[u];
-            ay += by[u];
-            az += bz[u];
+        for (int u = 0; u < kRowsPerWarp; u++) {
+            ax = A::add(ax, bx[u]);
+            ay = A::add(ay, by[u]);
+            az = A::add(az, bz[u]);
         }
     }
+    if (status || (d.gated && !reprime)) return;   // the same for every thread of the block
     red[w][0][lane] = ax;
     red[w][1][lane] = ay;
     red[w][2][lane] = az;
@@ -237,14 +265,37 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_kick_rows(Dev d) {
 #pragma unroll
     for (int h = kRowWarps / 2; h >= 1; h >>= 1) {
         if (w < h)
-            for (int q = 0; q < 3; q++) red[w][q][lane] += red[w + h][q][lane];
+            for (int q = 0; q < 3; q++) red[w][q][lane] = A::add(red[w][q][lane], red[w + h][q][lane]);
         __syncthreads();
     }
     if (w == 0) {
-        d.ksum[3 * (int64_t)b] = red[0][0][lane];
-        d.ksum[3 * (int64_t)b + 1] = red[0][1][lane];
-        d.ksum[3 * (int64_t)b + 2] = red[0][2][lane];
+        d.ksum[3 * (int64_t)b] = A::value(red[0][0][lane]);
+        d.ksum[3 * (int64_t)b + 1] = A::value(red[0][1][lane]);
+        d.ksum[3 * (int64_t)b + 2] = A::value(red[0][2][lane]);
     }
+}
+
+// The first group g in [a, ng) whose lowest member is at least body, for a
+// whole warp: groups ascend by their lowest member, and each round the 32
+// lanes test 32 evenly spaced groups of the remaining range and keep the
+// stretch between the last one below and the first one not below (a range
+// of ng groups takes about log32(ng) rounds, each one pair of dependent
+// loads, where a one-thread bisection takes log2(ng)).
+__device__ int warp_first_group_from(const Dev& d, int ng, int a, int64_t body) {
+    const int lane = threadIdx.x & 31;
+    int b = ng;   // the answer lies in [a, b]
+    while (a < b) {
+        const int step = (b - a + 31) / 32;
+        const int g = a + lane * step;
+        const bool below = g < b && d.members[d.goff[g]] < body;
+        const int nb = __popc(__ballot_sync(0xffffffffu, below));   // the lanes below are 0 .. nb - 1
+        if (nb == 0) return a;
+        const int last = a + (nb - 1) * step;
+        const int next = a + nb * step;
+        a = last + 1;
+        if (next < b) b = next;
+    }
+    return a;
 }
 
 // Closing half: the summed kick partials into a, jump with the momentum of
@@ -319,28 +370,11 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     if (!first && (int64_t)blockIdx.x * kBodyThreads == si.off && threadIdx.x < 32) {
         // energy removed by this step's mergers in this system: groups come in
         // ascending order of their lowest member, so the system's groups are the
-        // run whose lowest member lies in [off, off + cap); one warp sums them in
-        // a fixed order
+        // run whose lowest member lies in [off, off + cap), found by two 32-way
+        // searches; one warp sums them in a fixed order
         const int ng = d.ctl->ngroups;
-        int lo = 0, hi = 0;
-        if (threadIdx.x == 0 && ng > 0) {
-            int a = 0, b = ng;
-            while (a < b) {
-                const int mid = (a + b) >> 1;
-                if (d.members[d.goff[mid]] < si.off) a = mid + 1;
-                else b = mid;
-            }
-            lo = a;
-            b = ng;
-            while (a < b) {
-                const int mid = (a + b) >> 1;
-                if (d.members[d.goff[mid]] < si.off + si.cap) a = mid + 1;
-                else b = mid;
-            }
-            hi = a;
-        }
-        lo = __shfl_sync(0xffffffffu, lo, 0);
-        hi = __shfl_sync(0xffffffffu, hi, 0);
+        const int lo = warp_first_group_from(d, ng, 0, si.off);
+        const int hi = warp_first_group_from(d, ng, lo, si.off + si.cap);
         double e = 0.0;
         for (int g = lo + (int)threadIdx.x; g < hi; g += 32) e += d.glost[g];
         for (int o = 16; o >= 1; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -617,7 +651,8 @@ void launch_open(const Dev& d, cudaStream_t s) {
     prof_mark("open: kick+jump+drift");
 }
 void launch_kick_rows(const Dev& d, cudaStream_t s) {
-    k_kick_rows<<<(unsigned)(d.ntot / 32), 32 * kRowWarps, 0, s>>>(d);
+    if (d.p.precision == 1) k_kick_rows<true><<<(unsigned)(d.ntot / 32), 32 * kRowWarps, 0, s>>>(d);
+    else k_kick_rows<false><<<(unsigned)(d.ntot / 32), 32 * kRowWarps, 0, s>>>(d);
     prof_mark("kick: partial rows summed");
 }
 void launch_close(const Dev& d, cudaStream_t s) {

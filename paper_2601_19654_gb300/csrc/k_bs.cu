@@ -748,8 +748,10 @@ __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
 }
 
 // ---------------------------------------------------------------------------
-// Groups of up to four members (nearly every encounter): the four attempts
-// (step sizes H, H/2, H/4, H/8) are the four blocks of a cluster.  Inside a
+// Groups of up to four members (nearly every encounter): the attempts (step
+// sizes H, H/2, H/4, H/8, or H and H/2) are the blocks of a cluster; when
+// every one is rejected the next round tries the following halvings, so the
+// sizes tried and accepted are those of the sequential scheme.  Inside a
 // block, three warps, which the SM issues from three of its schedulers, each
 // with its own FP64 unit (on this chip a warp pays about the same for an FP64
 // instruction whatever its dependences, so what shortens a round is fewer
@@ -801,10 +803,19 @@ constexpr int kBarAcc0 = 3, kBarAcc1 = 4;   // accelerations written (warp 1 or 
 __device__ __forceinline__ void ws_bar_sync(int id) { asm volatile("bar.sync %0, 96;" ::"r"(id) : "memory"); }
 __device__ __forceinline__ void ws_bar_arrive(int id) { asm volatile("bar.arrive %0, 96;" ::"r"(id) : "memory"); }
 
+// Attempts a cluster: four when the encounter integrator has the GPU to
+// itself (a rejected substep costs no extra round unless all four fail);
+// two beside the kick, whose blocks then get the registers the other two
+// would hold (measured on the 16384-body disk: the kick and the encounter
+// branch end together, and the step is 2-3% shorter than with four).
+constexpr int kWsAttemptsAlone = 4, kWsAttemptsBeside = 2;
+
+template <int CA>
 __global__ void __launch_bounds__(kWsThreads, 6) k_bs_ws(Dev d) {
     __shared__ WsSh S;
     __shared__ int s_gi;
-    constexpr int CA = 4, M = WsSh::M;
+    constexpr int M = WsSh::M;
+    static_assert(CA >= 1 && CA <= 4, "one to four attempts a cluster");
     cg::cluster_group cl = cg::this_cluster();
     const int arank = (int)cl.block_rank();
     // (no status check: every block of a cluster must take the same path, and
@@ -1121,7 +1132,7 @@ cudaError_t bs_setup() {
 // registers one small-group block holds (the kick leaves room for one per SM)
 int bs_block_regs() {
     cudaFuncAttributes a{};
-    if (cudaFuncGetAttributes(&a, k_bs_ws) != cudaSuccess) return 65536;
+    if (cudaFuncGetAttributes(&a, k_bs_ws<4>) != cudaSuccess) return 65536;
     return ((a.numRegs + 7) / 8 * 8) * kWsThreads;
 }
 
@@ -1140,7 +1151,8 @@ void launch_bs_packed(const Dev& d, int nsm, cudaStream_t s) {
 // small-group kernel goes first, since beside the kick's blocks only its
 // blocks fit (a larger-group block takes half an SM's registers or more).
 // Otherwise the larger-group kernels go first, on a branch of the same
-// priority, and the small-group blocks fill the room they leave.
+// priority, and the small-group blocks fill the room they leave.  The
+// small-group clusters hold two attempts beside the kick, four otherwise.
 cudaError_t launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork,
                                cudaEvent_t join, bool small_first) {
     cudaError_t err = cudaSuccess;   // the first failed launch, if any (the cluster and cooperative ones)
@@ -1158,20 +1170,22 @@ cudaError_t launch_bs_lockstep(const Dev& d, int nsm, cudaStream_t s, cudaStream
     };
     if (!small_first) larger();
     {
-        // groups of up to 4 members: clusters of four three-warp blocks, one attempt each
+        // groups of up to 4 members: clusters of two or four blocks, one attempt each
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(4 * 2 * nsm));
+        const int ca = small_first ? kWsAttemptsBeside : kWsAttemptsAlone;
+        cfg.gridDim = dim3((unsigned)(ca * 2 * nsm));
         cfg.blockDim = dim3(kWsThreads);
         cfg.dynamicSmemBytes = 0;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 4;
+        at[0].val.clusterDim.x = ca;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_bs_ws, d);
+        const cudaError_t e = ca == kWsAttemptsBeside ? cudaLaunchKernelEx(&cfg, k_bs_ws<kWsAttemptsBeside>, d)
+                                                      : cudaLaunchKernelEx(&cfg, k_bs_ws<kWsAttemptsAlone>, d);
         if (err == cudaSuccess) err = e;
     }
     prof_mark("bs: groups <= 4");

@@ -13,8 +13,12 @@
 //
 // Mixed form: FP32 separations of the hi parts of a hi/lo float split of the
 // FP64 positions (the lo parts are added on the slow path), MUFU rsqrt, FP32
-// sums over each 128-body j-tile folded into a float hi/lo pair with Knuth's
-// TwoSum, converted to FP64 at the end.  FP64 form: the same in doubles.
+// sums over each 256-body j-tile (the even and the odd j in the two lanes of
+// a packed accumulator), written to the tile's partial row as the float pair
+// (hi, lo) that TwoSum makes of the two lanes, which holds their sum
+// exactly; k_kick_rows adds a body's rows in float-float arithmetic and
+// converts the total to FP64.  FP64 form: the same in doubles, rows summed
+// in FP64.
 #include "opal_internal.cuh"
 
 namespace opal {
@@ -412,13 +416,14 @@ __global__ void __launch_bounds__(T, MINB) k_kick_mixed(Dev d, const KickItem* _
             for (int q = 0; q < NI; q++) ax[q] = ay[q] = az[q] = make_float2(0.0f, 0.0f);
             if (near) near_tile<T, NI>(d, ib, rcm, sx, sy, sz, sm, sl, src, s_near, nx, ny, nz, form, ax, ay, az);
             else far_tile<NI>(sx, sy, sz, sm, nx, ny, nz, ax, ay, az);
-            // partial rows by sorted position (coalesced); k_kick_rows sums them by position
+            // partial rows by sorted position (coalesced), each the exact float
+            // pair of the two lanes' sums; k_kick_rows sums them by position
 #pragma unroll
             for (int q = 0; q < NI; q++) {
                 const int64_t slot = base + ib + q * T + threadIdx.x;
-                d.pacc_x[slot] = (double)ax[q].x + (double)ax[q].y;
-                d.pacc_y[slot] = (double)ay[q].x + (double)ay[q].y;
-                d.pacc_z[slot] = (double)az[q].x + (double)az[q].y;
+                reinterpret_cast<float2*>(d.pacc_x)[slot] = two_sum(ax[q].x, ax[q].y);
+                reinterpret_cast<float2*>(d.pacc_y)[slot] = two_sum(ay[q].x, ay[q].y);
+                reinterpret_cast<float2*>(d.pacc_z)[slot] = two_sum(az[q].x, az[q].y);
             }
         }
     }

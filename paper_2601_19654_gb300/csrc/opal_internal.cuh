@@ -252,6 +252,24 @@ __device__ __forceinline__ void set_status(Ctl* c, int code, int detail) {
     if (atomicCAS(&c->status, 0, code) == 0) c->detail = detail;
 }
 
+// Float-float arithmetic (a value held as hi + lo, two floats) for the
+// mixed kick's row totals: Knuth's TwoSum gives a + b exactly as a rounded
+// sum and its error; ff_add adds two such pairs (the hi parts by TwoSum, the
+// lo parts and that error in float, then renormalised), within a few units
+// of 2^-48 (|a| + |b|), on the FP32 pipe.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float2 t = two_sum(a.x, b.x);
+    const float e = __fadd_rn(t.y, __fadd_rn(a.y, b.y));
+    const float hi = __fadd_rn(t.x, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, t.x)));
+}
+
 // Two members of an encounter group can collide unless both are small bodies
 // (zero mass), which never interact (Sec. 2.1).
 __device__ __forceinline__ bool bs_can_touch(double mu, double mw) { return mu > 0.0 || mw > 0.0; }
