@@ -269,62 +269,83 @@ __device__ __forceinline__ bool boxes_overlap(const float* a, const float* b) {
     return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
 }
 
-// tile pairs (A, B >= A) of the sorted order whose boxes overlap: pairs that
-// pass |c_j - c_i| < s_i + s_j go to a list for stage 2.  The tile list has a
-// big tile as A (the big bodies sort first); pairs of two small bodies in it
-// are dropped here.
-__global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
+// The tile pairs whose boxes overlap, listed (one thread a tile pair, one
+// atomic a warp); the list's order is the schedule's, and nothing after it
+// depends on that order.
+__global__ void __launch_bounds__(256) k_tile_cull(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
+    if (d.ctl->status) return;
+    const int lane = threadIdx.x & 31;
+    for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x; it0 < ntiles; it0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t it = it0 + threadIdx.x;
+        bool ov = false;
+        if (it < ntiles) {
+            const PairTile tl = tiles[it];
+            ov = boxes_overlap(d.tbox + 6 * (tl.i0 / kSeg), d.tbox + 6 * (tl.j0 / kSeg));
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ov);
+        if (m == 0) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&d.ctl->ntov, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ov) d.tov[base + __popc(m & ((1u << lane) - 1u))] = (int)it;
+    }
+}
+
+// The listed tile pairs (A, B >= A): pairs that pass |c_j - c_i| < s_i + s_j
+// go to a list for stage 2.  The tile list has a big tile as A (the big
+// bodies sort first); pairs of two small bodies in it are dropped here.
+__global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __restrict__ tiles) {
     __shared__ float4 sj[kSeg];
     __shared__ int gj[kSeg];
     __shared__ unsigned smask[kSeg / 32][kSeg];
     if (d.ctl->status) return;
     const int lane = threadIdx.x & 31;
-    for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
-        const PairTile tl = tiles[it];
-        const float* ba = d.tbox + 6 * (tl.i0 / kSeg);
-        const float* bb = d.tbox + 6 * (tl.j0 / kSeg);
-        if (!boxes_overlap(ba, bb)) continue;       // the same for the whole block
-        const int64_t pi = tl.i0 + threadIdx.x;
-        const float4 ci = d.cen_sorted[pi];
-        const int gi = d.csorted[pi];
-        const int64_t big_end = d.sys[tl.sys].off + d.sys[tl.sys].nb;   // ids below are big bodies
-        const bool ibig = gi < big_end;
-        __syncthreads();
-        sj[threadIdx.x] = d.cen_sorted[tl.j0 + threadIdx.x];
-        gj[threadIdx.x] = d.csorted[tl.j0 + threadIdx.x];
-        __syncthreads();
-        const bool diag = tl.i0 == tl.j0;
-        // pass 1: each warp's ballots of the tile pair, and their total; pass 2:
-        // one atomic reserves the warp's room in the list, then every passing
-        // lane writes its pair (one atomic per warp and tile pair, not per column)
-        const int warp = threadIdx.x >> 5;
-        int cnt = 0;
+    const int warp = threadIdx.x >> 5;
+    const int nov = d.ctl->ntov;
+    for (int q = blockIdx.x; q < nov; q += gridDim.x) {
+        {
+            const PairTile tl = tiles[d.tov[q]];
+            const int64_t pi = tl.i0 + threadIdx.x;
+            const float4 ci = d.cen_sorted[pi];
+            const int gi = d.csorted[pi];
+            const int64_t big_end = d.sys[tl.sys].off + d.sys[tl.sys].nb;   // ids below are big bodies
+            const bool ibig = gi < big_end;
+            __syncthreads();
+            sj[threadIdx.x] = d.cen_sorted[tl.j0 + threadIdx.x];
+            gj[threadIdx.x] = d.csorted[tl.j0 + threadIdx.x];
+            __syncthreads();
+            const bool diag = tl.i0 == tl.j0;
+            // pass 1: each warp's ballots of the tile pair, and their total; pass 2:
+            // one atomic reserves the warp's room in the list, then every passing
+            // lane writes its pair (one atomic per warp and tile pair, not per column)
+            int cnt = 0;
 #pragma unroll 4
-        for (int jj = 0; jj < kSeg; jj++) {
-            const float4 cj = sj[jj];
-            float dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
-            float r2 = dx * dx + dy * dy + dz * dz;
-            float Ts = ci.w + cj.w;
-            // two small bodies never interact
-            bool pass = (!diag || jj > (int)threadIdx.x) && (r2 < Ts * Ts) && (ibig || gj[jj] < big_end);
-            const unsigned mask = __ballot_sync(0xffffffffu, pass);
-            if (lane == 0) smask[warp][jj] = mask;
-            cnt += __popc(mask);
-        }
-        if (cnt == 0) continue;                     // the same for the whole warp
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&d.ctl->nnear, cnt);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        __syncwarp();
-        const unsigned below = (1u << lane) - 1u;
-        for (int jj = 0; jj < kSeg; jj++) {
-            const unsigned mask = smask[warp][jj];
-            if ((mask >> lane) & 1u) {
-                const int idx = base + __popc(mask & below);
-                const int b2 = gj[jj];
-                if (idx < d.near_cap) d.near[idx] = make_int2(min(gi, b2), max(gi, b2));
+            for (int jj = 0; jj < kSeg; jj++) {
+                const float4 cj = sj[jj];
+                float dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
+                float r2 = dx * dx + dy * dy + dz * dz;
+                float Ts = ci.w + cj.w;
+                // two small bodies never interact
+                bool pass = (!diag || jj > (int)threadIdx.x) && (r2 < Ts * Ts) && (ibig || gj[jj] < big_end);
+                const unsigned mask = __ballot_sync(0xffffffffu, pass);
+                if (lane == 0) smask[warp][jj] = mask;
+                cnt += __popc(mask);
             }
-            base += __popc(mask);
+            if (cnt == 0) continue;                     // the same for the whole warp
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&d.ctl->nnear, cnt);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            __syncwarp();
+            const unsigned below = (1u << lane) - 1u;
+            for (int jj = 0; jj < kSeg; jj++) {
+                const unsigned mask = smask[warp][jj];
+                if ((mask >> lane) & 1u) {
+                    const int idx = base + __popc(mask & below);
+                    const int b2 = gj[jj];
+                    if (idx < d.near_cap) d.near[idx] = make_int2(min(gi, b2), max(gi, b2));
+                }
+                base += __popc(mask);
+            }
         }
     }
 }
@@ -748,7 +769,10 @@ void launch_scan(const Dev& d, const PairTile* tiles, int64_t ntiles, int grid, 
     launch_sort_bodies(d, s);
     k_tile_box<<<(unsigned)(d.ntot / kSeg), kSeg, 0, s>>>(d);
     prof_mark("scan: tile boxes");
-    k_scan_tiles<<<grid, kSeg, 0, s>>>(d, tiles, ntiles);
+    const int64_t cb = (ntiles + 255) / 256;
+    k_tile_cull<<<(unsigned)(cb < 152 * 8 ? cb : 152 * 8), 256, 0, s>>>(d, tiles, ntiles);
+    prof_mark("scan: tile boxes culled");
+    k_scan_tiles<<<grid, kSeg, 0, s>>>(d, tiles);
     prof_mark("scan: tile pairs");
     k_chord<<<152 * 4, 256, 0, s>>>(d);
     prof_mark("scan: chord bound");

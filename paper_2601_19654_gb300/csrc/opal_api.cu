@@ -405,8 +405,9 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         max_slots = std::max(max_slots, sl);
     }
     build_pair_tiles(s);
-    s->scan_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (int64_t)s->tiles.size()), (int64_t)s->nsm * 16);
-    s->energy_grid = s->scan_grid;
+    const int64_t nt = std::max<int64_t>(1, (int64_t)s->tiles.size());
+    s->scan_grid = (int)std::min<int64_t>(nt, (int64_t)s->nsm * 16);
+    s->energy_grid = (int)std::min<int64_t>(nt, (int64_t)s->nsm * 16);
     s->confirm_grid = s->nsm * 2;
     s->bs_grid = s->nsm * 4;
     const int64_t slots = max_slots;
@@ -516,6 +517,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     for (auto& it : var_items) max_items = std::max(max_items, it.size());
     TRYF(dalloc(s, &s->d_items, max_items));
     TRYF(dalloc(s, &s->d_tiles, s->tiles.size()));
+    TRYF(dalloc(s, &d.tov, std::max<size_t>(1, s->tiles.size())));
     TRYF(dalloc(s, &s->d_tile_off, s->tile_off.size()));
     {
         int64_t maxcap = 0;

@@ -60,6 +60,7 @@ struct Ctl {
     int nhard;           // groups left to the lockstep kernels when groups are many (this step)
     int qlock[3];        // queues of the lockstep kernels: up to 4, 32, 64 members (this step)
     int nhuge;           // groups of more than 64 members (this step)
+    int ntov;            // tile pairs whose boxes overlap (this step)
     unsigned long long nsub;  // BS substeps (this step)
     long long steps_done;
     int cand_overflow;   // candidates lost to a full candidate list (forces a status)
@@ -218,6 +219,7 @@ struct Dev {
     float* tbox;                        // [ntot / 64][6] tile boxes of c +- s
     int ncell;                          // buckets: one per kBucketDiv body slots
     // encounter pipeline
+    int* tov;                           // tile pairs whose boxes overlap (indices into the tile list)
     int2* near;  int64_t near_cap;      // pairs passing the midpoint test
     int2* cand;  int64_t cand_cap;      // FP32-bound candidates
     int2* flag;  int64_t flag_cap;      // flagged pairs
