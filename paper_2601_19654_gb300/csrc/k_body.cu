@@ -44,9 +44,15 @@ __device__ void note_box(const Dev& d, int s, int64_t b) {
 }
 
 __device__ __forceinline__ void note_rcmax(const Dev& d, int s, double rc) {
-    // rc >= 0: the order of non-negative floats matches the order of their bits
-    atomicMax(reinterpret_cast<int*>(d.rcmax) + s, __float_as_int(__double2float_ru(rc)));
+    // rc >= 0: the order of non-negative floats matches the order of their
+    // bits.  One atomic a warp (the lanes of a warp lie in one system): the
+    // largest over the lanes here, then the lowest of them stores it
+    const unsigned act = __activemask();
+    const unsigned v = __reduce_max_sync(act, (unsigned)__float_as_int(__double2float_ru(rc)));
+    if ((int)(threadIdx.x & 31) == __ffs(act) - 1) atomicMax(reinterpret_cast<int*>(d.rcmax) + s, (int)v);
 }
+
+__device__ __forceinline__ float norm3f(float x, float y, float z) { return sqrtf(fmaf(z, z, fmaf(y, y, x * x))); }
 
 // scan inputs of a live body: start-of-drift hi/lo, velocities, and the
 // midpoint c = (x0 + x1)/2 + dt (V0 - V1)/8 of its Hermite path over the
@@ -62,20 +68,24 @@ __device__ __forceinline__ void scan_floats(const Dev& d, int64_t b, double ox, 
     double dvx = ovx - vx, dvy = ovy - vy, dvz = ovz - vz;
     double cx = 0.5 * (ox + x) + 0.125 * T * dvx, cy = 0.5 * (oy + y) + 0.125 * T * dvy,
            cz = 0.5 * (oz + z) + 0.125 * T * dvz;
-    double rho = 0.5 * sqrt(dot3(wx, wy, wz, wx, wy, wz)) + 0.09622504486493763 * sqrt(dot3(ex, ey, ez, ex, ey, ez)) +
-                 (4.0 / 27.0 + 0.125) * fabs(T) * sqrt(dot3(dvx, dvy, dvz, dvx, dvy, dvz));
-    double sr = (rho + rc) * (1.0 + 1e-5) + 1e-6 * sqrt(dot3(cx, cy, cz, cx, cy, cz));
-    float srf = __double2float_ru(sr);
-    d.cen[b] = make_float4((float)cx, (float)cy, (float)cz, srf);
-    double v0n = sqrt(dot3(ovx, ovy, ovz, ovx, ovy, ovz)), v1n = sqrt(dot3(vx, vy, vz, vx, vy, vz));
+    // the norms in FP32 (the FP64 pipe is this kernel's bound): their relative
+    // error, a few 1e-7, is far inside the 1e-5 margin, and the differences
+    // they are taken of are formed in FP64
+    const float fcx = (float)cx, fcy = (float)cy, fcz = (float)cz;
+    const float nw = norm3f((float)wx, (float)wy, (float)wz), ne = norm3f((float)ex, (float)ey, (float)ez),
+                ndv = norm3f((float)dvx, (float)dvy, (float)dvz);
+    const float rho = 0.5f * nw + 0.0962251f * ne + 0.2731482f * fabsf((float)T) * ndv;   // sqrt 3/18, 4/27 + 1/8 rounded up
+    const float srf = (rho + __double2float_ru(rc)) * 1.00001f + 1e-6f * norm3f(fcx, fcy, fcz);
+    d.cen[b] = make_float4(fcx, fcy, fcz, srf);
+    const float v0n = norm3f((float)ovx, (float)ovy, (float)ovz), v1n = norm3f((float)vx, (float)vy, (float)vz);
     float hx, lx, hy, ly, hz, lz;
     split_hl(ox, hx, lx);
     split_hl(oy, hy, ly);
     split_hl(oz, hz, lz);
     d.sc0[b] = make_float4(hx, hy, hz, srf);
     d.sc1[b] = make_float4(lx, ly, lz, 0.0f);
-    d.sv0[b] = make_float4((float)ovx, (float)ovy, (float)ovz, __double2float_ru(v0n));
-    d.sv1[b] = make_float4((float)vx, (float)vy, (float)vz, __double2float_ru(v1n));
+    d.sv0[b] = make_float4((float)ovx, (float)ovy, (float)ovz, v0n);
+    d.sv1[b] = make_float4((float)vx, (float)vy, (float)vz, v1n);
 }
 
 // ---------------------------------------------------------------------------
@@ -140,7 +150,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
     const SysInfo si = d.sys[s];
-    const double* P = d.Ptot + 3 * s;   // momentum for the opening jump (summed by the last close)
+    const double* J = d.Pjump + 3 * s;   // the opening jump dt/2 P / M0 (summed by the last close)
     if (blockIdx.x == 0 && threadIdx.x == 0) d.ctl->reprime = 0;   // any re-evaluation has run
     const double half = 0.5 * d.p.dt, M0 = d.M0s[s];
     // undo copy of the start of the step
@@ -154,9 +164,9 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
         vx += half * d.ax[b];
         vy += half * d.ay[b];
         vz += half * d.az[b];
-        x += half * P[0] / M0;
-        y += half * P[1] / M0;
-        z += half * P[2] / M0;
+        x += J[0];
+        y += J[1];
+        z += J[2];
         d.x0[b] = x; d.y0[b] = y; d.z0[b] = z;
         d.vx0[b] = vx; d.vy0[b] = vy; d.vz0[b] = vz;
         const double ox = x, oy = y, oz = z, ovx = vx, ovy = vy, ovz = vz;
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
     const SysInfo si = d.sys[s];
-    const double* P = d.Ptot + 3 * (d.nsys + s);   // momentum for the closing jump
+    const double* J = d.Pjump + 3 * (d.nsys + s);   // the closing jump dt/2 P / M0
     const double half = 0.5 * d.p.dt, G = d.p.G;
     // the kick's partial rows, already summed by k_kick_rows
     double ax = d.ksum[3 * b], ay = d.ksum[3 * b + 1], az = d.ksum[3 * b + 2];
@@ -345,9 +355,9 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     if (d.alive[b]) {
         double x = d.x[b], y = d.y[b], z = d.z[b], vx = d.vx[b], vy = d.vy[b], vz = d.vz[b];
         if (!first) {
-            x += half * P[0] / d.M0s[s];
-            y += half * P[1] / d.M0s[s];
-            z += half * P[2] / d.M0s[s];
+            x += J[0];
+            y += J[1];
+            z += J[2];
             vx += half * ax;
             vy += half * ay;
             vz += half * az;
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
         d.ax[b] = 0.0; d.ay[b] = 0.0; d.az[b] = 0.0;
     }
     segment_sums(d, (int64_t)blockIdx.x * kBodyThreads, px, py, pz, d.pP_open);
-    system_total(d, d.pP_open, si, s, d.pcnt, d.Ptot + 3 * s);
+    system_total(d, d.pP_open, si, s, d.pcnt, d.Ptot + 3 * s, d.Pjump + 3 * s);
     if (!first && (int64_t)blockIdx.x * kBodyThreads == si.off && threadIdx.x < 32) {
         // energy removed by this step's mergers in this system: groups come in
         // ascending order of their lowest member, so the system's groups are the
@@ -424,7 +434,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_export_sum(Dev d, int s, doubl
         pz = m * d.vz[b];
     }
     segment_sums(d, first, px, py, pz, d.pP_close);
-    system_total(d, d.pP_close, si, s, counter, P);
+    system_total(d, d.pP_close, si, s, counter, P, nullptr);
 }
 
 // second pass: one record a body for the host, (x, y, z, heliocentric v =

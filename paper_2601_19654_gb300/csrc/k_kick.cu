@@ -587,7 +587,8 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
         if (q == 0) {
             const double m = al ? d.m[b] : 0.0;
             segment_sums(d, (int64_t)bb * kFixThreads, m * d.vx[b], m * d.vy[b], m * d.vz[b], d.pP_close);
-            system_total(d, d.pP_close, d.sys[s], s, d.pcnt + d.nsys, d.Ptot + 3 * (d.nsys + s));
+            system_total(d, d.pP_close, d.sys[s], s, d.pcnt + d.nsys, d.Ptot + 3 * (d.nsys + s),
+                         d.Pjump + 3 * (d.nsys + s));
         }
         if (nm == 0 || !d.overlap) return;
         const int ka = d.mlo[s], kz = d.mhi[s];

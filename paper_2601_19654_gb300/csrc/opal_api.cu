@@ -444,6 +444,7 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     TRYF(dalloc(s, &d.pP_close, 3 * d.nseg_tot));
     TRYF(dalloc(s, &d.pP_open, 3 * d.nseg_tot));
     TRYF(dalloc(s, &d.Ptot, 6 * (int64_t)nsys));
+    TRYF(dalloc(s, &d.Pjump, 6 * (int64_t)nsys));
     TRYF(dalloc(s, &d.pcnt, 2 * (int64_t)nsys));
     CKF(cudaMemsetAsync(d.pcnt, 0, 2 * nsys * sizeof(int), s->stream));
     d.flag_cap = P.encounter_capacity;

@@ -205,6 +205,7 @@ struct Dev {
     double *pP_close;                   // [3][nseg_tot] momentum before the closing jump
     double *pP_open;                    // [3][nseg_tot] momentum before the opening jump
     double* Ptot;                       // [2][nsys][3] those momenta summed: 0 opening, 1 closing jump
+    double* Pjump;                      // [2][nsys][3] each jump's displacement dt/2 P / M0, with its total
     int* pcnt;                          // [2][nsys] blocks done with their segments (see system_total)
     int64_t nseg_tot;
     // spatial order of the scan: each system's bodies counting-sorted by the
@@ -308,11 +309,12 @@ __device__ __forceinline__ void segment_sums(const Dev& d, int64_t first_body, d
 
 // After segment_sums into part: the last block of system s to get here sums
 // all the system's segments in a fixed order (each thread a strided set, then
-// a tree over the block) and stores the total in out[0..2], so the kernel
-// that needs it reads three numbers.  counter[s] is back at zero afterwards
+// a tree over the block) and stores the total in out[0..2] and, when jump is
+// given, the jump's displacement dt/2 P / M0 in jump[0..2], so the kernel
+// that needs them reads three numbers.  counter[s] is back at zero afterwards
 // (the step's memsets clear it too, in case a failing step left it behind).
 __device__ __forceinline__ void system_total(const Dev& d, const double* part, const SysInfo& si, int s,
-                                             int* counter, double* out) {
+                                             int* counter, double* out, double* jump) {
     __shared__ int last;
     __shared__ double red[3][kBodyThreads];
     __syncthreads();   // this block's segment partials are written
@@ -339,7 +341,11 @@ __device__ __forceinline__ void system_total(const Dev& d, const double* part, c
             for (int c = 0; c < 3; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x < 3) out[threadIdx.x] = red[threadIdx.x][0];
+    if (threadIdx.x < 3) {
+        out[threadIdx.x] = red[threadIdx.x][0];
+        // the jump's displacement, once for the system (every body's jump adds it)
+        if (jump) jump[threadIdx.x] = 0.5 * d.p.dt * red[threadIdx.x][0] / d.M0s[s];
+    }
     if (threadIdx.x == 0) counter[s] = 0;
 }
 
