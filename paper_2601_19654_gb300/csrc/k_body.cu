@@ -322,8 +322,8 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
     // the kick's partial rows, already summed by k_kick_rows
     double ax = d.ksum[3 * b], ay = d.ksum[3 * b + 1], az = d.ksum[3 * b + 2];
     // after encounters, when the kick ran beside the BS: a member's row was
-    // recomputed at its new place; every other body's row gets the members'
-    // terms at their new places added (the mixed kick left the members out
+    // recomputed at its new place (in parts, added here in order); every
+    // other body's row gets the members' terms at their new places added (the mixed kick left the members out
     // as sources: mass 0 in its float copy), or in the FP64 form, which never
     // runs beside the BS, their old terms swapped for new ones
     if (!first && d.ctl->ninvolved > 0) {
@@ -334,6 +334,12 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
                 ax = d.cfx[b];
                 ay = d.cfy[b];
                 az = d.cfz[b];
+#pragma unroll
+                for (int q = 1; q < kFixParts; q++) {
+                    ax += d.cfx[q * d.ntot + b];
+                    ay += d.cfy[q * d.ntot + b];
+                    az += d.cfz[q * d.ntot + b];
+                }
             } else {
                 double cx = d.cfx[b], cy = d.cfy[b], cz = d.cfz[b];
 #pragma unroll

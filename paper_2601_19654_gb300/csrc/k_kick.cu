@@ -493,7 +493,8 @@ __global__ void __launch_bounds__(T) k_kick_fp64(Dev d, const KickItem* __restri
 // leave the group members out as sources (k_group_place set their mass to 0
 // in the kick's float copy; overlap runs in the mixed form only), and
 // k_kick_fix then
-//   - recomputes the full row of each member at its new place,
+//   - recomputes the full row of each member at its new place, in kFixParts
+//     runs of the sources (one block a run; k_close adds them in order),
 //   - adds the members' new terms to every other body's row,
 //   - sums m V per 64-body segment for the closing jump (after the mergers;
 //     this part runs in both orders).
@@ -641,17 +642,42 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
             __syncthreads();
             if (!want || n == 0) continue;
             if (mixed) {
-                // the kick left the members out as sources: their new terms only
-                float tx = 0.0f, ty = 0.0f, tz = 0.0f;
-                for (int q = 0; q < n; q++) {
-                    const float3 tn = term_f(hi, li, rci, thrf, snh[q], snl[q], snr[q], form);
-                    tx += tn.x;
-                    ty += tn.y;
-                    tz += tn.z;
+                // the kick left the members out as sources: their new terms
+                // only, two members a packed instruction in the kick's far-path
+                // arithmetic; when either pair is nearer than the threshold,
+                // both take term_f, each in its own lane
+                const float2 nx2 = make_float2(-hi.x, -hi.x), ny2 = make_float2(-hi.y, -hi.y),
+                             nz2 = make_float2(-hi.z, -hi.z);
+                float2 tx2 = make_float2(0.0f, 0.0f), ty2 = tx2, tz2 = tx2;
+                int q = 0;
+                for (; q + 1 < n; q += 2) {
+                    const float4 a = snh[q], c = snh[q + 1];
+                    const float2 dx = __fadd2_rn(make_float2(a.x, c.x), nx2), dy = __fadd2_rn(make_float2(a.y, c.y), ny2),
+                                 dz = __fadd2_rn(make_float2(a.z, c.z), nz2);
+                    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                    if (r2.x < thrf || r2.y < thrf) {
+                        const float3 ta = term_f(hi, li, rci, thrf, a, snl[q], snr[q], form);
+                        const float3 tc = term_f(hi, li, rci, thrf, c, snl[q + 1], snr[q + 1], form);
+                        tx2.x += ta.x; ty2.x += ta.y; tz2.x += ta.z;
+                        tx2.y += tc.x; ty2.y += tc.y; tz2.y += tc.z;
+                    } else {
+                        const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                        const float2 sv = __fmul2_rn(__fmul2_rn(make_float2(a.w, c.w), ri), __fmul2_rn(ri, ri));
+                        tx2 = __ffma2_rn(sv, dx, tx2);
+                        ty2 = __ffma2_rn(sv, dy, ty2);
+                        tz2 = __ffma2_rn(sv, dz, tz2);
+                    }
                 }
-                fold(hx, lx, tx);
-                fold(hy, ly, ty);
-                fold(hz, lz, tz);
+                if (q < n) {
+                    const float3 t = term_f(hi, li, rci, thrf, snh[q], snl[q], snr[q], form);
+                    tx2.x += t.x; ty2.x += t.y; tz2.x += t.z;
+                }
+                fold(hx, lx, tx2.x);
+                fold(hx, lx, tx2.y);
+                fold(hy, ly, ty2.x);
+                fold(hy, ly, ty2.y);
+                fold(hz, lz, tz2.x);
+                fold(hz, lz, tz2.y);
                 continue;
             }
             for (int q = 0; q < n; q++) {
@@ -678,13 +704,18 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
         }
         return;
     }
-    // member rows, one block per member at a time
+    // member rows, a block per (member, part) task at a time: part q takes
+    // the q-th of kFixParts runs of the sources and its sum goes to part q
     if (!d.overlap) return;
     const int first = nbody_blocks * kFixParts;
-    for (int k = (int)blockIdx.x - first; k < nm; k += (int)gridDim.x - first) {
+    for (int task = (int)blockIdx.x - first; task < nm * kFixParts; task += (int)gridDim.x - first) {
+        const int k = task / kFixParts, part = task % kFixParts;
         const int g = d.members[k];
         const int s = d.body_sys[g];
         const SysInfo si = d.sys[s];
+        const int64_t span = (si.nb + kFixParts - 1) / kFixParts;
+        const int64_t jlo = si.off + part * span;
+        const int64_t jhi = si.off + (si.nb < (part + 1) * span ? si.nb : (part + 1) * span);
         double ax = 0.0, ay = 0.0, az = 0.0;
         if (d.alive[g]) {
             const float rcm = d.rcmax[s];
@@ -696,10 +727,12 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
             const double td = 2.0 * (rcid + (double)rcm);
             const double thrd = fmax(td * td, 1e-300);
             if (mixed) {
-                // float sums of 16 terms at a time, folded into hi/lo pairs
+                // float sums of 8 terms at a time, folded into hi/lo pairs
                 float hx = 0.0f, hy = 0.0f, hz = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
-                const int64_t jend = si.off + si.nb;   // sources: the big bodies
-                for (int64_t j0 = si.off + threadIdx.x; j0 < jend; j0 += 8 * kFixThreads) {
+                const float2 nx2 = make_float2(-hi.x, -hi.x), ny2 = make_float2(-hi.y, -hi.y),
+                             nz2 = make_float2(-hi.z, -hi.z);
+                const int64_t jend = jhi;   // sources: this part's run of the big bodies
+                for (int64_t j0 = jlo + threadIdx.x; j0 < jend; j0 += 8 * kFixThreads) {
                     // eight records loaded together (their latencies overlap); lo parts
                     // and rc only for the rare pair that takes the slow path
                     float4 hj[8];
@@ -708,35 +741,60 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
                         const int64_t j = j0 + (int64_t)u * kFixThreads;
                         hj[u] = (j < jend && j != g) ? d.kh[j] : make_float4(kFar, kFar, kFar, 0.0f);
                     }
-                    float tx = 0.0f, ty = 0.0f, tz = 0.0f;
+                    // two sources a packed instruction (the kick's far-path
+                    // arithmetic); a pair of sources with either one near takes
+                    // the scalar path, each in its own lane
+                    float2 tx2 = make_float2(0.0f, 0.0f), ty2 = tx2, tz2 = tx2;
 #pragma unroll
-                    for (int u = 0; u < 8; u++) {
-                        const int64_t j = j0 + (int64_t)u * kFixThreads;
-                        float dx = hj[u].x - hi.x, dy = hj[u].y - hi.y, dz = hj[u].z - hi.z;
-                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        float sv;
-                        if (r2 < thrf) {
-                            const float4 r = slow_pair_f(li, d.kl[j], dx, dy, dz, hj[u].w, rci, d.rcf[j], form);
-                            sv = r.x;
-                            dx = r.y;
-                            dy = r.z;
-                            dz = r.w;
+                    for (int u = 0; u < 8; u += 2) {
+                        const float2 dx = __fadd2_rn(make_float2(hj[u].x, hj[u + 1].x), nx2),
+                                     dy = __fadd2_rn(make_float2(hj[u].y, hj[u + 1].y), ny2),
+                                     dz = __fadd2_rn(make_float2(hj[u].z, hj[u + 1].z), nz2);
+                        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                        if (r2.x < thrf || r2.y < thrf) {
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                const int64_t j = j0 + (int64_t)(u + h) * kFixThreads;
+                                const float4 hh = hj[u + h];
+                                float ex = hh.x - hi.x, ey = hh.y - hi.y, ez = hh.z - hi.z;
+                                const float rs = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                                float sv;
+                                if (rs < thrf) {
+                                    const float4 r = slow_pair_f(li, d.kl[j], ex, ey, ez, hh.w, rci, d.rcf[j], form);
+                                    sv = r.x;
+                                    ex = r.y;
+                                    ey = r.z;
+                                    ez = r.w;
+                                } else {
+                                    const float ri = rsqrt_approx(rs);
+                                    sv = (hh.w * ri) * (ri * ri);
+                                }
+                                if (h == 0) {
+                                    tx2.x += sv * ex; ty2.x += sv * ey; tz2.x += sv * ez;
+                                } else {
+                                    tx2.y += sv * ex; ty2.y += sv * ey; tz2.y += sv * ez;
+                                }
+                            }
                         } else {
-                            const float ri = rsqrt_approx(r2);
-                            sv = (hj[u].w * ri) * (ri * ri);
+                            const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                            const float2 sv = __fmul2_rn(__fmul2_rn(make_float2(hj[u].w, hj[u + 1].w), ri),
+                                                         __fmul2_rn(ri, ri));
+                            tx2 = __ffma2_rn(sv, dx, tx2);
+                            ty2 = __ffma2_rn(sv, dy, ty2);
+                            tz2 = __ffma2_rn(sv, dz, tz2);
                         }
-                        tx += sv * dx;
-                        ty += sv * dy;
-                        tz += sv * dz;
                     }
-                    fold(hx, lx, tx);
-                    fold(hy, ly, ty);
-                    fold(hz, lz, tz);
+                    fold(hx, lx, tx2.x);
+                    fold(hx, lx, tx2.y);
+                    fold(hy, ly, ty2.x);
+                    fold(hy, ly, ty2.y);
+                    fold(hz, lz, tz2.x);
+                    fold(hz, lz, tz2.y);
                 }
                 ax = (double)hx + (double)lx;
                 ay = (double)hy + (double)ly;
                 az = (double)hz + (double)lz;
-            } else for (int64_t j = si.off + threadIdx.x; j < si.off + si.nb; j += kFixThreads) {
+            } else for (int64_t j = jlo + threadIdx.x; j < jhi; j += kFixThreads) {
                 if (j == g) continue;
                 {
                     double tx, ty, tz;
@@ -761,9 +819,10 @@ __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_block
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            d.cfx[g] = red[0][0];
-            d.cfy[g] = red[1][0];
-            d.cfz[g] = red[2][0];
+            const int64_t o = (int64_t)part * d.ntot + g;
+            d.cfx[o] = red[0][0];
+            d.cfy[o] = red[1][0];
+            d.cfz[o] = red[2][0];
         }
     }
 }
@@ -775,7 +834,7 @@ void launch_bs_apply(const Dev& d, int nsm, cudaStream_t s) {
 
 void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s) {
     const int nb = (int)(d.ntot / kFixThreads);
-    k_kick_fix<<<nb * kFixParts + 2 * nsm, kFixThreads, 0, s>>>(d, nb);
+    k_kick_fix<<<nb * kFixParts + 4 * nsm, kFixThreads, 0, s>>>(d, nb);
     prof_mark("kick fix: member rows and corrections");
 }
 

@@ -243,7 +243,7 @@ struct Dev {
     D4* okx;                            // per member slot: x, y, z, m before it
     int* mlo;                           // [nsys] first member slot of the system (or a large value)
     int* mhi;                           // [nsys] one past its last member slot (or 0)
-    double *cfx, *cfy, *cfz;            // [kFixParts][ntot]: kick correction parts (others), full row in part 0 (members)
+    double *cfx, *cfy, *cfz;            // [kFixParts][ntot]: kick correction parts (others), row parts (members)
     double* E_lost;                     // per system running sum
     Ctl* ctl;
 };
