@@ -116,13 +116,7 @@ __device__ __forceinline__ void bs_pair(const Params& p, double xb, double yb, d
     if (ge_nonneg(dr2, rc2)) return;   // 1 - K = 0 at or beyond rc
     const double dri = rsqrt(dr2), dr = dr2 * dri;
     if (ge_nonneg(dr, rc)) return;
-    double K;
-    const double y = (dr - c01) * inv;
-    if (le_zero(y)) K = 0.0;
-    else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
-    else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
-    const double wgt = 1.0 - K;
-    const double t = p.G * mo * wgt * (dri * dri * dri);
+    const double t = mutual_factor(p.G * mo * (dri * dri * dri), (dr - c01) * inv, p.changeover);
     ax += t * dx;
     ay += t * dy;
     az += t * dz;

@@ -76,13 +76,7 @@ __device__ __forceinline__ void huge_pair(const Dev& d, const Params& p, const d
     if (ge_nonneg(dr2, rc * rc)) return;   // 1 - K = 0 at or beyond rc
     const double dri = rsqrt(dr2), dr = dr2 * dri;
     if (ge_nonneg(dr, rc)) return;
-    double K;
-    const double y = (dr - 0.1 * rc) * H.pinv[w];
-    if (le_zero(y)) K = 0.0;
-    else if (p.changeover == 0) K = y * y / (2.0 * y * y - 2.0 * y + 1.0);
-    else K = y * y * y * (10.0 - 15.0 * y + 6.0 * y * y);
-    const double wgt = 1.0 - K;
-    const double t = p.G * H.m[o] * wgt * (dri * dri * dri);
+    const double t = mutual_factor(p.G * H.m[o] * (dri * dri * dri), (dr - 0.1 * rc) * H.pinv[w], p.changeover);
     ax += t * dx;
     ay += t * dy;
     az += t * dz;

@@ -362,6 +362,20 @@ __device__ __forceinline__ bool gt_nonneg(double a, double b) {   // a > b, both
 }
 __device__ __forceinline__ bool le_zero(double a) { return __double_as_longlong(a) <= 0; }
 
+// The mutual term's factor G m_o (1 - K) / r^3 inside rc, given G m_o / r^3
+// and y = (r - 0.1 rc) / (0.9 rc) < 1: for the rational form 1 - K is
+// (1 - y)^2 / (2y^2 - 2y + 1), formed with its one division last, so that
+// the division waits on the fewest operations before it (the encounter
+// integrator's chains are FP64 latency); the quintic's 1 - K as written.
+__device__ __forceinline__ double mutual_factor(double gm_ri3, double y, int form) {
+    if (__double_as_longlong(y) <= 0) return gm_ri3;   // y <= 0: K = 0
+    if (form == 0) {
+        const double u = 1.0 - y;
+        return (gm_ri3 * (u * u)) / fma(2.0 * y, -u, 1.0);   // 2y^2 - 2y + 1 = 1 - 2y(1 - y)
+    }
+    return gm_ri3 * (1.0 - y * y * y * (10.0 - 15.0 * y + 6.0 * y * y));
+}
+
 // Changeover weight K(r; rc): the rational form y^2/(2y^2-2y+1) or the
 // quintic 10y^3-15y^4+6y^5, y = (r - 0.1 rc)/(0.9 rc); 1 beyond rc, 0 below 0.1 rc.
 __device__ __forceinline__ double changeover(double r, double rc, int form) {
