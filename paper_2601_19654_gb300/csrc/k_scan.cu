@@ -63,13 +63,17 @@ __device__ __noinline__ bool chord_bound_passes(const Dev& d, int64_t i, int64_t
 
 struct SortGrid {
     float lo[3];
-    double inv_h;
+    float inv_h;
     int nx, ny, nz;
 };
 
 // a grid over the system's box of midpoints: cells of side h, about 8 of the
-// nbody bodies per cell in the two widest directions, at most nbuck cells
-__device__ void sort_grid(const Dev& d, int sys, double nbody, int64_t nbuck, SortGrid& g) {
+// nbody bodies per cell in the two widest directions, at most nbuck cells.
+// FP32 throughout: the grid only orders the bodies (any grid gives a valid
+// sorted order, and the same inputs give the same grid on every run), and
+// one thread's chain of FP64 operations here would hold every block of the
+// kernel for microseconds.
+__device__ void sort_grid(const Dev& d, int sys, float nbody, int64_t nbuck, SortGrid& g) {
     float lo[3], hi[3];
     for (int k = 0; k < 3; k++) {
         lo[k] = fordinv(d.sbox[3 * sys + k]);
@@ -77,25 +81,25 @@ __device__ void sort_grid(const Dev& d, int sys, double nbody, int64_t nbuck, So
         if (!(hi[k] >= lo[k])) lo[k] = hi[k] = 0.0f;   // no live body
         g.lo[k] = lo[k];
     }
-    double W[3];
-    for (int k = 0; k < 3; k++) W[k] = fmax((double)hi[k] - (double)lo[k], 1e-30);
-    double a = fmax(W[0], W[1]), b = fmin(W[0], W[1]);
-    double wmax = fmax(a, W[2]), wmid = W[2] > a ? a : (W[2] > b ? W[2] : b);
-    double cells = fmax(1.0, nbody / 8.0);
-    double inv_h = sqrt(cells / (wmax * wmid));
-    const double nb = (double)max((int64_t)1, nbuck);
-    double n[3];
+    float W[3];
+    for (int k = 0; k < 3; k++) W[k] = fmaxf(hi[k] - lo[k], 1e-20f);
+    const float a = fmaxf(W[0], W[1]), b = fminf(W[0], W[1]);
+    const float wmax = fmaxf(a, W[2]), wmid = W[2] > a ? a : (W[2] > b ? W[2] : b);
+    const float cells = fmaxf(1.0f, nbody / 8.0f);
+    float inv_h = sqrtf(cells) * rsqrtf(wmax) * rsqrtf(wmid);   // finite down to W = 1e-20
+    const float nb = (float)max((int64_t)1, nbuck);
+    float n[3];
     for (int it = 0; it < 400; it++) {
-        for (int k = 0; k < 3; k++) n[k] = fmin(floor(W[k] * inv_h) + 1.0, 1.0e6);
+        for (int k = 0; k < 3; k++) n[k] = fminf(floorf(W[k] * inv_h) + 1.0f, 1.0e6f);
         if (n[0] * n[1] * n[2] <= nb) break;
-        inv_h *= 0.8;
+        inv_h *= 0.8f;
     }
     // grid_index clamps to these counts, so every key stays in the grid's buckets
     g.inv_h = inv_h;
     g.nx = (int)n[0];
     g.ny = (int)n[1];
     g.nz = (int)n[2];
-    while ((double)g.nx * g.ny * g.nz > nb) {   // only if 400 shrinks were not enough
+    while ((double)g.nx * g.ny * g.nz > (double)nb) {   // only if 400 shrinks were not enough
         if (g.nx >= g.ny && g.nx >= g.nz) g.nx = max(1, g.nx / 2);
         else if (g.ny >= g.nz) g.ny = max(1, g.ny / 2);
         else g.nz = max(1, g.nz / 2);
@@ -114,9 +118,9 @@ __device__ __forceinline__ int64_t big_buckets(const SysInfo& si) {
     return min(nbk - 1, max((int64_t)1, (si.nb * nbk + si.n - 1) / si.n));
 }
 
-__device__ __forceinline__ int grid_index(float c, float lo, double inv_h, int n) {
-    double q = floor(((double)c - (double)lo) * inv_h);
-    q = fmin(fmax(q, 0.0), (double)(n - 1));
+__device__ __forceinline__ int grid_index(float c, float lo, float inv_h, int n) {
+    float q = floorf((c - lo) * inv_h);
+    q = fminf(fmaxf(q, 0.0f), (float)(n - 1));
     return (int)q;
 }
 
@@ -127,8 +131,8 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_count(Dev d) {
     const SysInfo si = d.sys[sys];
     __shared__ SortGrid grid[2];                   // big bodies, small bodies
     const int64_t nbb = big_buckets(si);
-    if (threadIdx.x == 0) sort_grid(d, sys, (double)si.nb, nbb, grid[0]);
-    if (threadIdx.x == 32) sort_grid(d, sys, (double)(si.n - si.nb), si.cap / kBucketDiv - 1 - nbb, grid[1]);
+    if (threadIdx.x == 0) sort_grid(d, sys, (float)si.nb, nbb, grid[0]);
+    if (threadIdx.x == 32) sort_grid(d, sys, (float)(si.n - si.nb), si.cap / kBucketDiv - 1 - nbb, grid[1]);
     __syncthreads();
     const int64_t base = si.off / kBucketDiv;      // the system's buckets: cap / 4 from off / 4
     int key;
