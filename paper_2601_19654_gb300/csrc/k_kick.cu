@@ -556,8 +556,8 @@ __global__ void __launch_bounds__(256) k_kick_apply(Dev d) {
         }
         d.x[g] = o[0]; d.y[g] = o[1]; d.z[g] = o[2];
         d.vx[g] = o[3]; d.vy[g] = o[4]; d.vz[g] = o[5];
+        if (o[6] != d.m[g]) d.hcb[g] = cbrt(o[6] / (3.0 * d.M0s[s]));   // a merger changed the mass
         d.m[g] = o[6];
-        d.hcb[g] = cbrt(o[6] / (3.0 * d.M0s[s]));
         d.R[g] = o[7];
         const int al = (int)o[8];
         d.alive[g] = al;
