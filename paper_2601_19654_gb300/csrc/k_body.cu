@@ -204,18 +204,20 @@ __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
 
 // ---------------------------------------------------------------------------
 // The kick's partial rows of every body, summed (after each kick, on its
-// stream).  A block takes 32 sorted positions; its warp w adds rows 8w ..
-// 8w + 7 (then 8w + 64 .. 8w + 71, and so on) in order, its lanes the 32
-// positions (one coalesced 256-byte load a row, the warp's 24 loads in
-// flight together), and the eight warps' sums are combined by a fixed tree
-// in shared memory, so the sum does not depend on the schedule.  The
-// control word is read beside the rows, not before them.  Mixed form: the
-// rows are exact float pairs and the sums float-float (FP32 pipe; FP64
-// additions would take this chip's FP64 pipe half the kernel), converted to
-// FP64 at the end; FP64 form: FP64 rows and sums.  The mixed kick writes a
-// body's row at its sorted position, the FP64 kick at its index; the sum
-// goes to ksum at the body's index.  Systems start at multiples of
-// kBodyThreads positions, so a block lies in one system.
+// stream).  A group of G warps (G = rows_g: enough for eight rows a warp of
+// the largest system's rows, at most eight) takes 32 sorted positions, its
+// lanes one position each; warp w of the group adds rows 8w .. 8w + 7 (then
+// 8w + 8G .., and so on) in order, one coalesced 256-byte load a row and the
+// warp's 24 loads in flight together, and the group's warps are combined by
+// a fixed tree in shared memory, so the sum does not depend on the schedule.
+// A block of eight warps so takes 32 (8 / G) positions.  The control word is
+// read beside the rows, not before them.  Mixed form: the rows are exact
+// float pairs and the sums float-float (FP32 pipe; FP64 additions would take
+// this chip's FP64 pipe half the kernel), converted to FP64 at the end; FP64
+// form: FP64 rows and sums.  The mixed kick writes a body's row at its
+// sorted position, the FP64 kick at its index; the sum goes to ksum at the
+// body's index.  Systems start at multiples of 256 positions, so a block
+// lies in one system.
 constexpr int kRowWarps = 8, kRowsPerWarp = 8;
 template <bool MIXED>
 struct RowAcc;
@@ -242,14 +244,16 @@ __global__ void __launch_bounds__(32 * kRowWarps, 4) k_kick_rows(Dev d) {
     using T = typename A::T;
     __shared__ T red[kRowWarps][3][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t p = (int64_t)blockIdx.x * 32 + lane;   // grid: ntot / 32 blocks
+    const int G = d.rows_g, gw = w % G;   // the warp's place in its group of G
+    const int64_t p0 = (int64_t)blockIdx.x * 32 * (kRowWarps / G);   // grid: ntot / (32 (8 / G)) blocks
+    const int64_t p = p0 + (w / G) * 32 + lane;
     const int status = d.ctl->status, reprime = d.ctl->reprime;
     const int b = MIXED ? d.csorted[p] : (int)p;
-    const SysInfo si = d.sys[d.body_sys[(int64_t)blockIdx.x * 32]];
+    const SysInfo si = d.sys[d.body_sys[p0]];
     const int64_t local = p - si.off;
     T ax = A::zero(), ay = A::zero(), az = A::zero();
 #pragma unroll 1
-    for (int c0 = kRowsPerWarp * w; c0 < si.nchunk; c0 += kRowsPerWarp * kRowWarps) {
+    for (int c0 = kRowsPerWarp * gw; c0 < si.nchunk; c0 += kRowsPerWarp * G) {
         T bx[kRowsPerWarp], by[kRowsPerWarp], bz[kRowsPerWarp];
 #pragma unroll
         for (int u = 0; u < kRowsPerWarp; u++) {
@@ -272,16 +276,15 @@ __global__ void __launch_bounds__(32 * kRowWarps, 4) k_kick_rows(Dev d) {
     red[w][1][lane] = ay;
     red[w][2][lane] = az;
     __syncthreads();
-#pragma unroll
-    for (int h = kRowWarps / 2; h >= 1; h >>= 1) {
-        if (w < h)
+    for (int h = G / 2; h >= 1; h >>= 1) {
+        if (gw < h)
             for (int q = 0; q < 3; q++) red[w][q][lane] = A::add(red[w][q][lane], red[w + h][q][lane]);
         __syncthreads();
     }
-    if (w == 0) {
-        d.ksum[3 * (int64_t)b] = A::value(red[0][0][lane]);
-        d.ksum[3 * (int64_t)b + 1] = A::value(red[0][1][lane]);
-        d.ksum[3 * (int64_t)b + 2] = A::value(red[0][2][lane]);
+    if (gw == 0) {
+        d.ksum[3 * (int64_t)b] = A::value(red[w][0][lane]);
+        d.ksum[3 * (int64_t)b + 1] = A::value(red[w][1][lane]);
+        d.ksum[3 * (int64_t)b + 2] = A::value(red[w][2][lane]);
     }
 }
 
@@ -667,8 +670,9 @@ void launch_open(const Dev& d, cudaStream_t s) {
     prof_mark("open: kick+jump+drift");
 }
 void launch_kick_rows(const Dev& d, cudaStream_t s) {
-    if (d.p.precision == 1) k_kick_rows<true><<<(unsigned)(d.ntot / 32), 32 * kRowWarps, 0, s>>>(d);
-    else k_kick_rows<false><<<(unsigned)(d.ntot / 32), 32 * kRowWarps, 0, s>>>(d);
+    const unsigned grid = (unsigned)(d.ntot / (32 * (kRowWarps / d.rows_g)));
+    if (d.p.precision == 1) k_kick_rows<true><<<grid, 32 * kRowWarps, 0, s>>>(d);
+    else k_kick_rows<false><<<grid, 32 * kRowWarps, 0, s>>>(d);
     prof_mark("kick: partial rows summed");
 }
 void launch_close(const Dev& d, cudaStream_t s) {

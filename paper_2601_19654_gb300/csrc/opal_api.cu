@@ -645,6 +645,13 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
         CKF(up(d.sys, s->sys.data(), nsys * sizeof(SysInfo)));
         CKF(up(s->d_items, s->items.data(), s->items.size() * sizeof(KickItem)));
     }
+    {
+        // warps a position takes in the row sums: eight rows a warp, at most eight warps
+        int32_t maxc = 1;
+        for (auto& si : s->sys) maxc = std::max(maxc, si.nchunk);
+        d.rows_g = 1;
+        while (d.rows_g < 8 && d.rows_g * 8 < maxc) d.rows_g *= 2;
+    }
     launch_kick_stage(d, P.precision, s->stream);
     launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, P.precision, s->kick_variant, s->stream);
     launch_kick_rows(d, s->stream);

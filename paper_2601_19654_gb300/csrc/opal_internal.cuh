@@ -191,6 +191,7 @@ struct Dev {
     float *ks_x, *ks_y, *ks_z, *ks_m;
     float4* ks_lo;
     float* ks_rc;
+    int rows_g = 8;  // warps a position takes in k_kick_rows (1, 2, 4 or 8: eight rows a warp)
     double* ksum;    // [3 ntot]: each body's kick partial rows summed (by k_kick_rows), by body index
     float4* kbox;    // per 128 positions
     float4* kbox2;   // per 256 positions
