@@ -74,6 +74,23 @@ opal_status opal_debug_barrier(opal_sim* sim, int64_t wait_ns, int32_t hold);
  * for the call.  OPAL_EINVAL for a NULL out, OPAL_ECUDA if a launch fails. */
 opal_status opal_probe_alu_peaks(double out[3]);
 
+/* Device timeline of a step, for measurement.  In a library built with
+ * OPAL_TIMELINE defined (paper_2601_19654_gb300/build.py, timeline=True, into
+ * its own directory), thread 0 of every block of the step's kernels reads the
+ * device's global nanosecond timer when the block starts and when it leaves,
+ * and each kernel keeps the earliest start and the latest end.
+ * opal_timeline_kernels() is the number of kernel slots (0 in the normal
+ * build, which compiles none of it); opal_timeline_name(id) the kernel of slot
+ * id (a static string; NULL out of range).  opal_timeline(sim, 1, NULL)
+ * resets the slots (after the simulation's stream is idle); opal_timeline(sim,
+ * 0, out) copies them to out[2 * opal_timeline_kernels()], start and end of
+ * slot id at out[2 id] and out[2 id + 1] in ns (a start of ~0 means the kernel
+ * did not run since the reset).  Errors: OPAL_EINVAL for a NULL sim or out, or
+ * in the normal build; OPAL_ECUDA if a copy fails. */
+int32_t opal_timeline_kernels(void);
+const char* opal_timeline_name(int32_t id);
+opal_status opal_timeline(opal_sim* sim, int32_t reset, uint64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

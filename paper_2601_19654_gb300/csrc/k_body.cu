@@ -146,6 +146,7 @@ __global__ void k_prime(Dev d) {
 // ---------------------------------------------------------------------------
 // Opening half of a step, one thread per body.
 __global__ void __launch_bounds__(kBodyThreads) k_open(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlOpen);
     if (d.ctl->status) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
@@ -240,6 +241,7 @@ struct RowAcc<false> {   // FP64
 
 template <bool MIXED>
 __global__ void __launch_bounds__(32 * kRowWarps, 4) k_kick_rows(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlKickRows);
     using A = RowAcc<MIXED>;
     using T = typename A::T;
     __shared__ T red[kRowWarps][3][32];
@@ -316,6 +318,7 @@ __device__ int warp_first_group_from(const Dev& d, int ng, int a, int64_t body) 
 // step's jump needs (of V + dt/2 a, the velocities after its opening kick).
 // first != 0 (create time): only a and the partials, no jump or kick.
 __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
+    OPAL_TIMELINE_SCOPE(kTlClose);
     if (d.ctl->status || (d.gated && !d.ctl->reprime)) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int s = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
@@ -403,6 +406,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_close(Dev d, int first) {
 
 // Undo of a failed step (runs every step; returns at once when all is well).
 __global__ void k_finish(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlFinish);
     const Ctl* c = d.ctl;
     if (!c->status) {
         if (blockIdx.x == 0 && threadIdx.x == 0) d.ctl->steps_done++;
@@ -618,6 +622,7 @@ __global__ void __launch_bounds__(kRemThreads) k_remove(Dev d) {
 // Start of a step: the counters, bounds and scratch the step's kernels
 // accumulate into, zeroed or preset in one launch (rather than ten memsets).
 __global__ void __launch_bounds__(256) k_step_reset(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlReset);
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
     int* c = reinterpret_cast<int*>(reinterpret_cast<char*>(d.ctl) + offsetof(Ctl, ncand));
     constexpr int nc = (int)((offsetof(Ctl, steps_done) - offsetof(Ctl, ncand)) / sizeof(int));

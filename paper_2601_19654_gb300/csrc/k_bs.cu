@@ -156,6 +156,7 @@ __device__ __forceinline__ void bs_accel(const BsSh<NT, A>& S, const Params& p, 
 // barriers are always met.
 template <int NT, int A, int CA>
 __global__ void __launch_bounds__(NT, NT == 32 ? 4 : 512 / NT) k_bs(Dev d, int kind) {
+    OPAL_TIMELINE_SCOPE((NT == 256 ? kTlBs256 : kTlBs512));
     using Sh = BsSh<NT, A>;
     constexpr int M = Sh::M;
     constexpr int TA = NT / A;            // threads per attempt
@@ -510,6 +511,7 @@ struct PkWarp {
 };
 
 __global__ void __launch_bounds__(32 * kPkWarps) k_bs_packed(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlBsPacked);
     extern __shared__ __align__(16) unsigned char pk_smem[];
     const int lane = threadIdx.x & 31;
     PkWarp& W = reinterpret_cast<PkWarp*>(pk_smem)[threadIdx.x >> 5];
@@ -806,6 +808,7 @@ constexpr int kWsAttemptsAlone = 4, kWsAttemptsBeside = 2;
 
 template <int CA>
 __global__ void __launch_bounds__(kWsThreads, 6) k_bs_ws(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlBsWs);
     __shared__ WsSh S;
     __shared__ int s_gi;
     constexpr int M = WsSh::M;

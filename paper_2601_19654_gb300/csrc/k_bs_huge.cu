@@ -297,6 +297,7 @@ __device__ void huge_merge(const Dev& d, const Params& p, double M0, int b, int 
 __device__ __forceinline__ bool pair_before(int2 a, int2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); }
 
 __global__ void __launch_bounds__(kHugeThreads, 2) k_bs_huge(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlBsHuge);
     __shared__ double red[kHugeThreads / 32];
     __shared__ int bred[7][kHugeThreads / 32];
     HugeCtl* hc = d.hctl;

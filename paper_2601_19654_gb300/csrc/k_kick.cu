@@ -90,6 +90,7 @@ __device__ __forceinline__ void queue_done(const Dev& d) {
 // i-tiles).  Parked bodies (dead or padding, at kFar) stay out of the boxes;
 // an empty tile gets lo > hi.
 __global__ void __launch_bounds__(2 * kKickBox) k_kick_stage(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlKickStage);
     if (d.gated && !d.ctl->reprime) return;   // the re-evaluation after a removal, with none
     if (d.ctl->status) return;
     constexpr int W = 2 * kKickBox / 32;      // warps of the block (8)
@@ -288,6 +289,7 @@ __device__ __forceinline__ void near_tile(const Dev& d, int64_t i0, float rcm, c
 // rows in order.
 template <int T, int NI, int MINB>
 __global__ void __launch_bounds__(T, MINB) k_kick_mixed(Dev d, const KickItem* __restrict__ items, int64_t nitems) {
+    OPAL_TIMELINE_SCOPE(kTlKick);
     if (d.gated && !d.ctl->reprime) return;   // the re-evaluation after a removal, with none
     constexpr int JPT = kJTile / T;           // j records each thread stages (2 or 4)
     constexpr int IT = T * NI;                // bodies of an i-tile: 128 or 256, one staged box
@@ -432,6 +434,7 @@ __global__ void __launch_bounds__(T, MINB) k_kick_mixed(Dev d, const KickItem* _
 
 template <int T>
 __global__ void __launch_bounds__(T) k_kick_fp64(Dev d, const KickItem* __restrict__ items, int64_t nitems) {
+    OPAL_TIMELINE_SCOPE(kTlKick);
     if (d.gated && !d.ctl->reprime) return;   // the re-evaluation after a removal, with none
     __shared__ D4 sj[kJTile];
     __shared__ int s_item;
@@ -538,6 +541,7 @@ __device__ __forceinline__ void term_d(double xi, double yi, double zi, double r
 }
 
 __global__ void __launch_bounds__(256) k_kick_apply(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlApply);
     if (d.ctl->status) return;
     const int nm = d.ctl->ninvolved;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nm; k += gridDim.x * blockDim.x) {
@@ -569,6 +573,7 @@ __global__ void __launch_bounds__(256) k_kick_apply(Dev d) {
 constexpr int kFixThreads = kBodyThreads;
 
 __global__ void __launch_bounds__(kFixThreads) k_kick_fix(Dev d, int nbody_blocks) {
+    OPAL_TIMELINE_SCOPE(kTlFix);
     __shared__ float4 snh[kFixThreads], snl[kFixThreads];
     __shared__ float snr[kFixThreads];
     __shared__ D4 snx[kFixThreads], sox[kFixThreads];

@@ -125,6 +125,7 @@ __device__ __forceinline__ int grid_index(float c, float lo, float inv_h, int n)
 }
 
 __global__ void __launch_bounds__(kBodyThreads) k_sort_count(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlSortCount);
     if (d.ctl->status) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int sys = d.body_sys[(int64_t)blockIdx.x * kBodyThreads];
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_count(Dev d) {
 // thread loads 16 consecutive counts at once (vector loads), the block scans
 // the per-thread sums, and a carry runs from pass to pass
 __global__ void __launch_bounds__(1024) k_sort_prefix(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlSortPrefix);
     constexpr int PER = 16;
     __shared__ int warp_sum[32];
     __shared__ int carry;
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(1024) k_sort_prefix(Dev d) {
 
 // scatter into the buckets (in whatever order the atomics give)
 __global__ void __launch_bounds__(kBodyThreads) k_sort_scatter(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlSortScatter);
     if (d.ctl->status) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int key = d.ckey[b];
@@ -223,6 +226,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_scatter(Dev d) {
 // with smaller ids.  The dead bodies' bucket (last of each system) keeps its
 // order: it follows every live body, and dead bodies add nothing to any sum.
 __global__ void __launch_bounds__(kBodyThreads) k_sort_order(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlSortOrder);
     if (d.ctl->status) return;
     const int64_t p = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int2 bk = d.cscratch[p];   // (body, bucket; -1 for a dead body)
@@ -241,6 +245,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_sort_order(Dev d) {
 
 // box of c +- s over the live bodies of each 64-body tile of the sorted order
 __global__ void __launch_bounds__(kSeg) k_tile_box(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlTileBox);
     if (d.ctl->status) return;
     const int64_t t = blockIdx.x;
     const int64_t pos = t * kSeg + threadIdx.x;
@@ -277,6 +282,7 @@ __device__ __forceinline__ bool boxes_overlap(const float* a, const float* b) {
 // atomic a warp); the list's order is the schedule's, and nothing after it
 // depends on that order.
 __global__ void __launch_bounds__(256) k_tile_cull(Dev d, const PairTile* __restrict__ tiles, int64_t ntiles) {
+    OPAL_TIMELINE_SCOPE(kTlTileCull);
     if (d.ctl->status) return;
     const int lane = threadIdx.x & 31;
     for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x; it0 < ntiles; it0 += (int64_t)gridDim.x * blockDim.x) {
@@ -299,6 +305,7 @@ __global__ void __launch_bounds__(256) k_tile_cull(Dev d, const PairTile* __rest
 // go to a list for stage 2.  The tile list has a big tile as A (the big
 // bodies sort first); pairs of two small bodies in it are dropped here.
 __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __restrict__ tiles) {
+    OPAL_TIMELINE_SCOPE(kTlScanTiles);
     __shared__ float4 sj[kSeg];
     __shared__ int gj[kSeg];
     __shared__ unsigned smask[kSeg / 32][kSeg];
@@ -356,6 +363,7 @@ __global__ void __launch_bounds__(kSeg) k_scan_tiles(Dev d, const PairTile* __re
 
 // stage 2 on the stage-1 list, one thread per pair
 __global__ void __launch_bounds__(256) k_chord(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlChord);
     if (d.ctl->status) return;
     const int nn = d.ctl->nnear;
     if (nn > d.near_cap) {
@@ -485,6 +493,7 @@ __device__ double interval_min2(double T, int k, const double* d0, const double*
 }
 
 __global__ void __launch_bounds__(256) k_confirm(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlConfirm);
     if (d.ctl->status) return;
     const int ncand = d.ctl->ncand;
     if (ncand > d.cand_cap) {
@@ -559,6 +568,7 @@ __device__ __forceinline__ int uf_root(int* parent, int x) {
 }
 
 __global__ void __launch_bounds__(256) k_group_link(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlGroupLink);
     if (d.ctl->status) return;
     const int nf = d.ctl->nflag;
     if (nf > d.flag_cap) {
@@ -587,6 +597,7 @@ __global__ void __launch_bounds__(256) k_group_link(Dev d) {
 }
 
 __global__ void __launch_bounds__(kBodyThreads) k_group_count(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlGroupCount);
     if (d.ctl->status || d.ctl->nflag == 0) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     if (__ldcg(&d.label[b]) < 0) return;
@@ -602,6 +613,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_group_count(Dev d) {
 // one block: exclusive scans, in body order, of the group sizes (member
 // offsets) and of the root flags (group indices), 16 counts per thread a pass
 __global__ void __launch_bounds__(1024) k_group_offsets(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlGroupOffsets);
     constexpr int PER = 16;
     __shared__ long long warp_sum[32];
     __shared__ long long carry;
@@ -669,6 +681,7 @@ __global__ void __launch_bounds__(1024) k_group_offsets(Dev d) {
 }
 
 __global__ void __launch_bounds__(kBodyThreads) k_group_place(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlGroupPlace);
     if (d.ctl->status || d.ctl->nflag == 0) return;
     const int64_t b = (int64_t)blockIdx.x * kBodyThreads + threadIdx.x;
     const int r = d.label[b];
@@ -688,6 +701,7 @@ __global__ void __launch_bounds__(kBodyThreads) k_group_place(Dev d) {
 }
 
 __global__ void __launch_bounds__(256) k_group_order(Dev d) {
+    OPAL_TIMELINE_SCOPE(kTlGroupOrder);
     __shared__ int v[kGroupSortMax];
     if (d.ctl->status || d.ctl->nflag == 0) return;
     const int ng = d.ctl->ngroups;

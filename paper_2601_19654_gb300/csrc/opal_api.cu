@@ -426,6 +426,9 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     for (auto pp : ksf) TRYF(dalloc(s, pp, N));
     TRYF(dalloc(s, &d.ks_lo, N));
     TRYF(dalloc(s, &d.ksum, 3 * N));
+#ifdef OPAL_TIMELINE
+    TRYF(dalloc(s, &d.timeline, 2 * (size_t)kTlCount));
+#endif
     TRYF(dalloc(s, &d.kbox, 2 * (N / kKickBox)));
     TRYF(dalloc(s, &d.kbox2, 2 * (N / (2 * kKickBox))));
     d.ncell = (int)(N / kBucketDiv);
@@ -694,6 +697,16 @@ void note_launch(opal_sim* s, cudaError_t e) {
 }
 
 // stage k of a step on stream st
+// the kick and its row sums; the timing events (when on) bracket the kick
+// kernel alone, not its staging
+void launch_kick_timed(opal_sim* s, cudaStream_t st) {
+    const Dev& d = s->d;
+    if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[0], st, cudaEventRecordExternal);
+    launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
+    if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[1], st, cudaEventRecordExternal);
+    launch_kick_rows(d, st);
+}
+
 void launch_stage(opal_sim* s, int k, cudaStream_t st) {
     const Dev& d = s->d;
     switch (k) {
@@ -709,12 +722,8 @@ void launch_stage(opal_sim* s, int k, cudaStream_t st) {
                                               false));
             break;
         case kStageKick:
-            // the timing events (when on) bracket the kick kernel alone, not its staging
             launch_kick_stage(d, d.p.precision, st);
-            if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[0], st, cudaEventRecordExternal);
-            launch_kick(d, s->d_items, (int64_t)s->items.size(), s->kick_grid, d.p.precision, s->kick_variant, st);
-            if (s->time_kick) cudaEventRecordWithFlags(s->kick_ev[1], st, cudaEventRecordExternal);
-            launch_kick_rows(d, st);
+            launch_kick_timed(s, st);
             break;
         case kStageApply: launch_bs_apply(d, s->nsm, st); break;
         case 8: launch_kick_fix(d, s->nsm, st); break;
@@ -1334,6 +1343,49 @@ opal_status opal_debug_bs_group(opal_sim* s, const double* x0, const double* V0,
     }
     if (E_lost) *E_lost = gl[0];
     return OPAL_OK;
+}
+
+// Device timeline (timeline builds; the normal build reports none)
+int32_t opal_timeline_kernels(void) {
+#ifdef OPAL_TIMELINE
+    return kTlCount;
+#else
+    return 0;
+#endif
+}
+
+const char* opal_timeline_name(int32_t id) {
+    static const char* names[kTlCount] = {
+        "k_step_reset", "k_open", "k_sort_count", "k_sort_prefix", "k_sort_scatter", "k_sort_order",
+        "k_tile_box", "k_tile_cull", "k_scan_tiles", "k_chord", "k_confirm", "k_group_link", "k_group_count",
+        "k_group_offsets", "k_group_place", "k_group_order", "k_bs_packed", "k_bs_ws", "k_bs<256>", "k_bs<512>",
+        "k_bs_huge", "k_kick_stage", "k_kick", "k_kick_rows", "k_kick_apply", "k_kick_fix", "k_close",
+        "k_finish"};
+    return id >= 0 && id < kTlCount ? names[id] : nullptr;
+}
+
+opal_status opal_timeline(opal_sim* s, int32_t reset, uint64_t* out) {
+    if (!s) return OPAL_EINVAL;
+#ifdef OPAL_TIMELINE
+    CK(cudaStreamSynchronize(s->stream));
+    if (reset) {
+        unsigned long long h[2 * kTlCount];
+        for (int i = 0; i < kTlCount; i++) {
+            h[2 * i] = ~0ull;   // the earliest start comes down from here
+            h[2 * i + 1] = 0ull;
+        }
+        CK(cudaMemcpy(s->d.timeline, h, sizeof(h), cudaMemcpyHostToDevice));
+        return OPAL_OK;
+    }
+    if (!out) return set_err(s->err, "opal_timeline: out is NULL"), OPAL_EINVAL;
+    CK(cudaMemcpy(out, s->d.timeline, 2 * kTlCount * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    return OPAL_OK;
+#else
+    (void)reset;
+    (void)out;
+    set_err(s->err, "opal_timeline: the library was built without OPAL_TIMELINE");
+    return OPAL_EINVAL;
+#endif
 }
 
 }  // extern "C"

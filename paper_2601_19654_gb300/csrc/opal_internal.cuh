@@ -192,6 +192,7 @@ struct Dev {
     float4* ks_lo;
     float* ks_rc;
     int rows_g = 8;  // warps a position takes in k_kick_rows (1, 2, 4 or 8: eight rows a warp)
+    unsigned long long* timeline = nullptr;   // [kTlCount][2] (timeline builds only)
     double* ksum;    // [3 ntot]: each body's kick partial rows summed (by k_kick_rows), by body index
     float4* kbox;    // per 128 positions
     float4* kbox2;   // per 256 positions
@@ -600,6 +601,40 @@ inline void prof_mark(const char* name) {
         g_prof->names[g_prof->n++] = name;
     }
 }
+
+// ---------------------------------------------------------------------------
+// Device timeline, for measurement: in a build with OPAL_TIMELINE defined,
+// thread 0 of every block of the step's kernels reads the global timer when
+// the block starts and when it leaves, and each kernel keeps its earliest
+// start and latest end (atomic min and max on the pair [2 id], [2 id + 1]),
+// so that a step's launches, concurrent branches included, can be read back
+// as they ran.  The normal build compiles none of it.
+enum TimelineId {
+    kTlReset, kTlOpen, kTlSortCount, kTlSortPrefix, kTlSortScatter, kTlSortOrder, kTlTileBox, kTlTileCull,
+    kTlScanTiles, kTlChord, kTlConfirm, kTlGroupLink, kTlGroupCount, kTlGroupOffsets, kTlGroupPlace,
+    kTlGroupOrder, kTlBsPacked, kTlBsWs, kTlBs256, kTlBs512, kTlBsHuge, kTlKickStage, kTlKick, kTlKickRows,
+    kTlApply, kTlFix, kTlClose, kTlFinish, kTlCount
+};
+#ifdef OPAL_TIMELINE
+struct TimelineScope {
+    unsigned long long* t;
+    int id;
+    __device__ static unsigned long long now() {
+        unsigned long long v;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+        return v;
+    }
+    __device__ TimelineScope(unsigned long long* tl, int i) : t(tl), id(i) {
+        if (t && threadIdx.x == 0) atomicMin(t + 2 * id, now());
+    }
+    __device__ ~TimelineScope() {
+        if (t && threadIdx.x == 0) atomicMax(t + 2 * id + 1, now());
+    }
+};
+#define OPAL_TIMELINE_SCOPE(id) TimelineScope opal_timeline_scope_(d.timeline, (id))
+#else
+#define OPAL_TIMELINE_SCOPE(id)
+#endif
 
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the kernel translation units)

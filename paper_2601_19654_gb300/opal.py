@@ -12,7 +12,7 @@ import threading
 
 import numpy as np
 
-from .build import LIB, build
+from .build import LIB, LIB_TIMELINE, build
 
 OK, EINVAL, ENOMEM, ECUDA, EKEPLER, EBS, EOVERFLOW, ENONFINITE = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EKEPLER", 5: "EBS", 6: "EOVERFLOW",
@@ -87,6 +87,12 @@ def _declare(L):
     L.opal_debug_barrier.argtypes = [_P, C.c_int64, C.c_int32]
     L.opal_energy_momentum_noalloc.argtypes = [C.c_int64, C.c_double, C.c_double, _P, _P, _P, _P, _P]
     L.opal_probe_alu_peaks.argtypes = [_D]
+    L.opal_timeline_kernels.argtypes = []
+    L.opal_timeline_kernels.restype = C.c_int32
+    L.opal_timeline_name.argtypes = [C.c_int32]
+    L.opal_timeline_name.restype = C.c_char_p
+    L.opal_timeline.argtypes = [_P, C.c_int32, _P]
+    L.opal_timeline.restype = C.c_int
     for name in ("opal_probe_alu_peaks", "opal_create", "opal_ensemble_create", "opal_step", "opal_step_async", "opal_wait", "opal_get_state", "opal_energy_momentum",
                  "opal_last_step_stats", "opal_profile_steps", "opal_debug_accel", "opal_debug_drift",
                  "opal_debug_scan", "opal_debug_bs_group", "opal_debug_barrier", "opal_energy_momentum_noalloc",
@@ -95,15 +101,19 @@ def _declare(L):
 
 
 def lib(auto_build: bool = False):
-    """The loaded CUDA library (builds it first when asked and out of date)."""
+    """The loaded CUDA library (builds it first when asked and out of date).
+    With OPAL_TIMELINE_BUILD=1 in the environment when it is first loaded,
+    the measurement build with the device timeline is loaded instead."""
     global _lib
     with _lock:
         if _lib is None:
+            timeline = os.environ.get("OPAL_TIMELINE_BUILD") == "1"
+            path = LIB_TIMELINE if timeline else LIB
             if auto_build:
-                build()
-            if not os.path.exists(LIB):
-                raise OpalError(ECUDA, f"CUDA library not built ({LIB}); run paper_2601_19654_gb300.build.build()")
-            L = C.CDLL(LIB)
+                build(timeline=timeline)
+            if not os.path.exists(path):
+                raise OpalError(ECUDA, f"CUDA library not built ({path}); run paper_2601_19654_gb300.build.build()")
+            L = C.CDLL(path)
             _declare(L)
             _lib = L
     return _lib
@@ -267,6 +277,22 @@ class Simulation:
         ms = C.c_double(0.0)
         _check(lib().opal_time_kick_alone(self.ptr, int(reps), C.byref(ms)), self.ptr)
         return ms.value
+
+    def timeline_reset(self):
+        """Clear the device timeline (a timeline build: OPAL_TIMELINE_BUILD=1)."""
+        _check(lib().opal_timeline(self.ptr, 1, None), self.ptr)
+
+    def timeline(self) -> dict:
+        """Kernel name -> (first block start, last block end) in ns of the
+        global timer, for the kernels that ran since timeline_reset()."""
+        n = int(lib().opal_timeline_kernels())
+        buf = np.zeros(2 * max(n, 1), dtype=np.uint64)
+        _check(lib().opal_timeline(self.ptr, 0, buf.ctypes.data), self.ptr)
+        out = {}
+        for k in range(n):
+            if buf[2 * k] != np.uint64(0xFFFFFFFFFFFFFFFF):
+                out[lib().opal_timeline_name(k).decode()] = (int(buf[2 * k]), int(buf[2 * k + 1]))
+        return out
 
     def profile(self, nsteps: int) -> dict:
         cap = 64

@@ -6,12 +6,15 @@ Workloads (opal_ic): tiny (10 bodies), planetesimals (1000 + Jupiter),
 disk (16384 equal masses), heavy (131072 + Jupiter and Saturn), embryos
 (1023 embryos and Jupiter with 262144 massless planetesimals; --n sets the
 planetesimal count), ensemble (256 systems of 64-4096 bodies).  Prints steps/s, the encounter counters of
-the last step, |dE/E| and, with --profile, the device time of every kernel.
+the last step, |dE/E| and, with --profile, the device time of every kernel
+(each launched alone); with --timeline K, the step graph's kernels as they
+ran on the device (a separate build with the device timeline).
 """
 from __future__ import annotations
 
 import argparse
 import os
+import statistics
 import sys
 import time
 
@@ -39,11 +42,16 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile", action="store_true")
+    ap.add_argument("--timeline", type=int, default=0, metavar="K",
+                    help="K more steps one at a time in the timeline build: each kernel's first block start "
+                         "and last block end on the device, medians over the K steps, from the step's start")
     args = ap.parse_args(argv)
 
+    if args.timeline:
+        os.environ["OPAL_TIMELINE_BUILD"] = "1"   # before the library is first loaded
     from paper_2601_19654_gb300 import opal
     from paper_2601_19654_gb300.build import build
-    build()
+    build(timeline=bool(args.timeline))
     if args.workload == "ensemble":
         systems = ic.ensemble(args.seed, nsys=args.nsys)
         sim = opal.Simulation.ensemble(systems, precision=args.precision)
@@ -65,6 +73,20 @@ def main(argv=None):
         prof = sim.profile(max(1, min(args.steps, 10)))
         for name, ms in prof.items():
             print(f"  {name:28s} {ms * 1e3:10.1f} us")
+    if args.timeline:
+        spans = {}
+        for _ in range(args.timeline):
+            sim.timeline_reset()
+            sim.step(1)
+            tl = sim.timeline()
+            t0 = min(a for a, _ in tl.values())
+            for name, (a, b) in tl.items():
+                spans.setdefault(name, []).append(((a - t0) * 1e-3, (b - t0) * 1e-3))
+        print(f"  device timeline, medians over {args.timeline} steps one at a time (us from the step's start):")
+        rows = sorted(((statistics.median(a for a, _ in v), statistics.median(b for _, b in v), k)
+                       for k, v in spans.items()))
+        for a, b, name in rows:
+            print(f"  {name:16s} {a:8.1f} {b:8.1f}  ({b - a:6.1f})")
     sim.close()
 
 

@@ -123,3 +123,19 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 def test_barrier_hook_rejects_a_null_simulation(lib):
     """The barrier test hook validates on the host: no simulation, no call."""
     assert lib.lib().opal_debug_barrier(None, 1000, 1) == lib.EINVAL
+
+
+def test_normal_build_has_no_device_timeline(lib):
+    """The device timeline is compiled only into the measurement build: the
+    normal library reports no kernel slots and refuses the readout, while the
+    slot names (shared by both builds) cover the step's kernels."""
+    L = lib.lib()
+    assert L.opal_timeline_kernels() == 0
+    assert L.opal_timeline(None, 1, None) == lib.EINVAL
+    names = []
+    k = 0
+    while L.opal_timeline_name(k) is not None:
+        names.append(L.opal_timeline_name(k).decode())
+        k += 1
+    assert {"k_open", "k_kick", "k_bs_ws", "k_kick_rows", "k_close", "k_finish"} <= set(names)
+    assert L.opal_timeline_name(-1) is None
