@@ -800,7 +800,7 @@ opal_status capture_graph(opal_sim* s) {
     }
     cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
     if (s->launch_err != cudaSuccess) {
-        set_err(s->err, "launch of an encounter kernel (cluster of four blocks, or the cooperative whole-GPU "
+        set_err(s->err, "launch of an encounter kernel (a cluster of attempt blocks, or the cooperative whole-GPU "
                         "kernel) refused: %s", cudaGetErrorString(s->launch_err));
         if (s->graph) {
             cudaGraphDestroy(s->graph);
