@@ -1126,13 +1126,6 @@ cudaError_t bs_setup() {
                                 (int)sizeof(BsSh<kBsLargerThreads, 1>));
 }
 
-// registers one small-group block holds (the kick leaves room for one per SM)
-int bs_block_regs() {
-    cudaFuncAttributes a{};
-    if (cudaFuncGetAttributes(&a, k_bs_ws<4>) != cudaSuccess) return 65536;
-    return ((a.numRegs + 7) / 8 * 8) * kWsThreads;
-}
-
 void launch_bs_packed(const Dev& d, int nsm, cudaStream_t s) {
     // two warps an SM: FP64 issues about one warp instruction per 17 cycles an
     // SM, so fewer warps sharing it finish their groups' chains sooner

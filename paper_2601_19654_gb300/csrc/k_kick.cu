@@ -853,7 +853,6 @@ struct KickVariant {
     bool jmajor;      // items: a j-tile against a run of i-tiles (else an i-tile against a j-chunk)
     void (*launch)(const Dev&, const KickItem*, int64_t, int, cudaStream_t);
     int (*occupancy)();
-    int (*regs)();
 };
 
 template <int T, int NI, int MINB>
@@ -865,18 +864,6 @@ int occ_mixed() {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kick_mixed<T, NI, MINB>, T, 0);
     return nb;
-}
-template <int T, int NI, int MINB>
-int regs_mixed() {
-    cudaFuncAttributes a{};
-    cudaFuncGetAttributes(&a, k_kick_mixed<T, NI, MINB>);
-    return a.numRegs;
-}
-template <int T>
-int regs_fp64() {
-    cudaFuncAttributes a{};
-    cudaFuncGetAttributes(&a, k_kick_fp64<T>);
-    return a.numRegs;
 }
 template <int T>
 void launch_fp64(const Dev& d, const KickItem* items, int64_t nitems, int grid, cudaStream_t s) {
@@ -890,14 +877,14 @@ int occ_fp64() {
 }
 
 static const KickVariant kMixed[] = {
-    {"mixed t128 i1", 128, 1, true, launch_mixed<128, 1, 7>, occ_mixed<128, 1, 7>, regs_mixed<128, 1, 7>},
-    {"mixed t128 i1 6", 128, 1, true, launch_mixed<128, 1, 6>, occ_mixed<128, 1, 6>, regs_mixed<128, 1, 6>},
-    {"mixed t128 i1 8", 128, 1, true, launch_mixed<128, 1, 8>, occ_mixed<128, 1, 8>, regs_mixed<128, 1, 8>},
-    {"mixed t64 i2", 64, 2, true, launch_mixed<64, 2, 8>, occ_mixed<64, 2, 8>, regs_mixed<64, 2, 8>},
-    {"mixed t128 i2", 128, 2, true, launch_mixed<128, 2, 5>, occ_mixed<128, 2, 5>, regs_mixed<128, 2, 5>},
+    {"mixed t128 i1", 128, 1, true, launch_mixed<128, 1, 7>, occ_mixed<128, 1, 7>},
+    {"mixed t128 i1 6", 128, 1, true, launch_mixed<128, 1, 6>, occ_mixed<128, 1, 6>},
+    {"mixed t128 i1 8", 128, 1, true, launch_mixed<128, 1, 8>, occ_mixed<128, 1, 8>},
+    {"mixed t64 i2", 64, 2, true, launch_mixed<64, 2, 8>, occ_mixed<64, 2, 8>},
+    {"mixed t128 i2", 128, 2, true, launch_mixed<128, 2, 5>, occ_mixed<128, 2, 5>},
 };
 static const KickVariant kFp64[] = {
-    {"fp64 t128", 128, 1, false, launch_fp64<128>, occ_fp64<128>, regs_fp64<128>},
+    {"fp64 t128", 128, 1, false, launch_fp64<128>, occ_fp64<128>},
 };
 
 int kick_num_variants(int precision) {
@@ -908,12 +895,6 @@ bool kick_jmajor(int precision, int v) { return precision == 1 ? kMixed[v].jmajo
 int kick_itile(int precision, int v) {
     const KickVariant& k = precision == 1 ? kMixed[v] : kFp64[v];
     return k.threads * k.ni;
-}
-// registers one block holds as the SM allocates them (per warp, in units of
-// 8 per thread)
-int kick_block_regs(int precision, int v) {
-    const KickVariant& k = precision == 1 ? kMixed[v] : kFp64[v];
-    return k.threads * ((k.regs() + 7) / 8 * 8);
 }
 int kick_occupancy(int precision, int v) { return precision == 1 ? kMixed[v].occupancy() : kFp64[v].occupancy(); }
 int kick_threads(int precision, int v) { return precision == 1 ? kMixed[v].threads : kFp64[v].threads; }

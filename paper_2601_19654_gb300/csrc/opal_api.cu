@@ -583,13 +583,12 @@ opal_status create_impl(const opal_params* p, int32_t nsys, const int64_t* nps, 
     launch_sort_bodies(d, s->stream);
     // pick the kick variant: timed on this simulation's own positions
     {
-        // blocks of variant v an SM in the step graph: as many as leave the
-        // registers of one encounter block free
-        auto graph_blocks = [&](int v) {
-            const int occ = std::max(1, kick_occupancy(p->precision, v));
-            const int kr = std::max(1, kick_block_regs(p->precision, v));
-            return std::max(1, std::min(occ, (65536 - bs_block_regs()) / kr));
-        };
+        // blocks of variant v an SM in the step graph: as many as fit.  Beside
+        // the encounter integrator some of them wait for room, and take it as
+        // the encounter blocks finish (measured on the 16384-body disk: with
+        // room left for one encounter block an SM the kick took 162 us in the
+        // graph, with every block it fits 144 us, the encounter kernel the same)
+        auto graph_blocks = [&](int v) { return std::max(1, kick_occupancy(p->precision, v)); };
         int best = 0;
         const char* force = getenv("OPAL_KICK_VARIANT");
         double work = 0;

@@ -664,9 +664,7 @@ void launch_kick_fix(const Dev& d, int nsm, cudaStream_t s);
 int kick_num_variants(int precision);
 const char* kick_variant_name(int precision, int variant);
 int kick_occupancy(int precision, int variant);
-int kick_block_regs(int precision, int variant);   // registers one block of variant v holds
 int kick_threads(int precision, int variant);      // threads a block of variant v
-int bs_block_regs();
 int kick_itile(int precision, int variant);   // i-bodies per i-tile (a divisor of kPad)
 bool kick_jmajor(int precision, int variant); // items: one j-tile against a run of i-tiles (else an i-tile against j-tiles)
 void launch_kick_stage(const Dev& d, int precision, cudaStream_t s);   // the sorted copies the mixed kick reads
