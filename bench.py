@@ -46,9 +46,10 @@ SM_MAX_MHZ = 2070.0
 FLOPS_PER_INTERACTION = 18
 # DRAM bytes (read + written) of one launch of the mixed kick, from the ncu
 # capture summarised in profiles/kick_mixed_disk16384.md (launch shape
-# "mixed t128 i1 6"); the other one-i-body shapes run the same code with
-# another register cap, so they move the same bytes.  Other shapes report none.
-_KICK_I1_TRAFFIC = 0.802048e6 + 0.0
+# "mixed t128 i1 6" with the step graph's 912 blocks); the other one-i-body
+# shapes run the same code with another register cap, so they move the same
+# bytes.  Other shapes report none.
+_KICK_I1_TRAFFIC = 0.821248e6 + 0.0
 KICK_TRAFFIC = {"mixed t128 i1": _KICK_I1_TRAFFIC, "mixed t128 i1 6": _KICK_I1_TRAFFIC,
                 "mixed t128 i1 8": _KICK_I1_TRAFFIC}
 
